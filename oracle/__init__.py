@@ -1,0 +1,233 @@
+"""FP64 CPU oracle for CS-WGS (test infrastructure only).
+
+This package is the slow, plain reference that the CUDA library is checked
+against.  Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg
+of ``bench.py`` may import it; the product path never does.  It shares no code
+with the CUDA library.  The arithmetic lives in ``cswgs_oracle.c`` (plain C,
+double precision, optional OpenMP); this module compiles it with gcc on first
+use and wraps it with ctypes and numpy.
+
+Each wrapper names the passage of the paper the C function follows:
+Eq. 1 (back-propagation), Eq. 2 (lens-and-prism phase), Eq. 3 (forward
+projection), Eqs. 4-6 (weighted update), Eq. 7 (uniformity), Section 2
+(CS-WGS schedule) and Section 3 "Compressed sensing" (random pixel order).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cswgs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no -ffast-math); returns the .so path."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        d = ctypes.POINTER(ctypes.c_double)
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        u64 = ctypes.c_uint64
+        lib.oracle_splitmix64.argtypes = [u64, u64]
+        lib.oracle_splitmix64.restype = u64
+        lib.oracle_fmix32.argtypes = [ctypes.c_uint32]
+        lib.oracle_fmix32.restype = ctypes.c_uint32
+        lib.oracle_theta0.argtypes = [ctypes.c_int, u64, d]
+        lib.oracle_permute.argtypes = [ctypes.c_int, u64, ctypes.c_int, ctypes.c_int64]
+        lib.oracle_permute.restype = ctypes.c_int64
+        lib.oracle_subset.argtypes = [ctypes.c_int, ctypes.c_int64, u64, ctypes.c_int, i64]
+        lib.oracle_spot_phase.argtypes = [ctypes.c_int, d, ctypes.c_int, ctypes.c_int64]
+        lib.oracle_spot_phase.restype = ctypes.c_double
+        lib.oracle_back.argtypes = [ctypes.c_int, ctypes.c_int, d, d, d, ctypes.c_int64, i64, d]
+        lib.oracle_forward.argtypes = [ctypes.c_int, ctypes.c_int, d, ctypes.c_int64, i64, d, d]
+        lib.oracle_update.argtypes = [ctypes.c_int, d, d, d]
+        lib.oracle_metrics.argtypes = [ctypes.c_int, ctypes.c_int, d, d, d, d, d, d]
+        lib.oracle_solve.argtypes = [ctypes.c_int, ctypes.c_int, d, d, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int, u64, d, d, ctypes.c_int, ctypes.c_int, d, d, d, d, d, d]
+        lib.oracle_solve.restype = ctypes.c_int
+        lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        _lib = lib
+        return lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def threads() -> int:
+    return _load().oracle_threads()
+
+
+def set_threads(t: int) -> None:
+    _load().oracle_set_threads(int(t))
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Output k of SplitMix64 started from `seed` (counter-based form)."""
+    return int(_load().oracle_splitmix64(seed & (2**64 - 1), k & (2**64 - 1)))
+
+
+def fmix32(h: int) -> int:
+    """MurmurHash3 32-bit finaliser."""
+    return int(_load().oracle_fmix32(h & 0xFFFFFFFF))
+
+
+def theta0(N: int, seed: int) -> np.ndarray:
+    """theta_n^0 ~ U[0, 2 pi) drawn from the seed (Eq. 1, random superposition)."""
+    out = np.empty(N)
+    _load().oracle_theta0(N, seed & (2**64 - 1), _dp(out))
+    return out
+
+
+def permute(P: int, seed: int, j: int, k: int) -> int:
+    """pi_{seed,j}(k): keyed bijection on [0, P^2) (Section 3, compressed sensing)."""
+    return int(_load().oracle_permute(P, seed & (2**64 - 1), j, k))
+
+
+def subset(P: int, Mp: int, seed: int, j: int) -> np.ndarray:
+    """S_j: the Mp pixel indices of iteration j (Section 2, CS-WGS)."""
+    out = np.empty(Mp, dtype=np.int64)
+    _load().oracle_subset(P, Mp, seed & (2**64 - 1), j, _ip(out))
+    return out
+
+
+def spot_phase(P: int, xyz, n: int, m: int) -> float:
+    """phi_n at pixel m (Eq. 2, normalised units), radians."""
+    xyz = _f64(xyz, (-1, 3))
+    return float(_load().oracle_spot_phase(P, _dp(xyz), n, m))
+
+
+def back(P: int, xyz, amp, theta, pix=None) -> np.ndarray:
+    """Eq. 1: Phi at the listed pixels (all pixels when pix is None), in (-pi, pi]."""
+    xyz = _f64(xyz, (-1, 3))
+    N = xyz.shape[0]
+    amp = _f64(amp)
+    theta = _f64(theta)
+    if pix is None:
+        cnt = P * P
+    else:
+        pix = np.ascontiguousarray(pix, dtype=np.int64)
+        cnt = pix.shape[0]
+    out = np.empty(cnt)
+    _load().oracle_back(P, N, _dp(xyz), _dp(amp), _dp(theta), cnt, _ip(pix), _dp(out))
+    return out
+
+
+def forward(P: int, xyz, phi, pix=None) -> np.ndarray:
+    """Eq. 3 (sign reading +i): complex V_n over the listed pixels, normalised 1/count."""
+    xyz = _f64(xyz, (-1, 3))
+    N = xyz.shape[0]
+    phi = _f64(phi)
+    if pix is None:
+        cnt = P * P
+    else:
+        pix = np.ascontiguousarray(pix, dtype=np.int64)
+        cnt = pix.shape[0]
+    assert phi.shape[0] == cnt
+    V = np.empty(2 * N)
+    _load().oracle_forward(P, N, _dp(xyz), cnt, _ip(pix), _dp(phi), _dp(V))
+    return V[0::2] + 1j * V[1::2]
+
+
+def update(V, w, theta):
+    """Eqs. 4-6: returns the updated (w, theta)."""
+    V = np.asarray(V, dtype=np.complex128)
+    Vi = np.empty(2 * V.shape[0])
+    Vi[0::2] = V.real
+    Vi[1::2] = V.imag
+    w = _f64(w).copy()
+    theta = _f64(theta).copy()
+    _load().oracle_update(V.shape[0], _dp(Vi), _dp(w), _dp(theta))
+    return w, theta
+
+
+def metrics(P: int, xyz, phi_full):
+    """Efficiency e, uniformity u (Eq. 7), spot intensities I_n and fields V_n."""
+    xyz = _f64(xyz, (-1, 3))
+    N = xyz.shape[0]
+    phi_full = _f64(phi_full)
+    assert phi_full.shape[0] == P * P
+    V = np.empty(2 * N)
+    In = np.empty(N)
+    e = ctypes.c_double()
+    u = ctypes.c_double()
+    _load().oracle_metrics(P, N, _dp(xyz), _dp(phi_full), _dp(V), _dp(In), ctypes.byref(e), ctypes.byref(u))
+    return e.value, u.value, In, V[0::2] + 1j * V[1::2]
+
+
+def solve(P: int, xyz, amp=None, c: float = 1.0, iterations: int = 0, seed: int = 0,
+          theta_in=None, w_in=None, first_j: int = 1, final_pass: bool = True,
+          full_iterations: int = 2):
+    """The whole CS-WGS method (Section 2).
+
+    The last `full_iterations` of the `iterations` run over all pixels (the
+    paper ends with two such iterations); the others over the subsets S_j.
+
+    Returns a dict with phase (P*P, [0, 2 pi), or None without the final pass),
+    e, u, w, theta (final state) and I (spot intensities)."""
+    xyz = _f64(xyz, (-1, 3))
+    N = xyz.shape[0]
+    amp = _f64(amp)
+    theta_in = _f64(theta_in)
+    w_in = _f64(w_in)
+    M = P * P
+    phase = np.empty(M) if final_pass else None
+    w = np.empty(N)
+    th = np.empty(N)
+    In = np.empty(N) if final_pass else None
+    e = ctypes.c_double(float("nan"))
+    u = ctypes.c_double(float("nan"))
+    rc = _load().oracle_solve(P, N, _dp(xyz), _dp(amp), float(c), int(iterations),
+                              int(full_iterations), seed & (2**64 - 1), _dp(theta_in), _dp(w_in), int(first_j),
+                              1 if final_pass else 0, _dp(phase), ctypes.byref(e),
+                              ctypes.byref(u), _dp(w), _dp(th), _dp(In))
+    if rc != 0:
+        raise ValueError("oracle_solve rejected its arguments")
+    return {"phase": phase, "e": e.value, "u": u.value, "w": w, "theta": th, "I": In}
+
+
+def subset_size(P: int, c: float) -> int:
+    """Mp = floor(c M), the size of every subset (Section 2, CS-WGS)."""
+    import math
+    return int(math.floor(c * P * P))
