@@ -1,0 +1,307 @@
+"""Benchmark: CS-WGS point-cloud holograms on GB300.
+
+One step = the whole hot path for a batch of holograms resident in HBM: spot
+preparation, 30 iterations (28 over random pixel subsets of 1/8 of the
+pupil, 2 over all pixels), the final full back-propagation writing each phase
+map and the full forward projection giving e and u; one persistent launch
+per iteration for the whole batch, replayed from a CUDA graph.
+
+Workload: 64 holograms of P = 1152 (M = 1152^2), N = 100 spots, alpha, beta
+~ U[-P/4, P/4] cycles, gamma ~ U[-10, 10] waves, theta^0 ~ U[0, 2 pi), one
+seed per hologram.  Prints one JSON line (see README of the keys in
+the design doc): holograms/s, p50/p99 latency, the roofline of the iteration
+kernel against the SFU (sine/cosine) pipe, the FP64 GPU baseline, the FP64
+CPU oracle on a bounded sample, and an end-to-end number through the C ABI
+with host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "holograms/s and p50/p99 latency at M=1152^2, N=100, e,u>=0.9 vs FP64 GPU baseline"
+SFU_PER_CLK_PER_SM = 16       # sine/cosine results per clock per SM (CUDA arithmetic throughput table)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--P", type=int, default=1152)
+    ap.add_argument("--N", type=int, default=100)
+    ap.add_argument("--c", type=float, default=0.125)
+    ap.add_argument("--iters", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def problems(args, rank):
+    return [workloads.problem(args.P, args.N, 10.0, args.c, args.iters, seed=rank * 100000 + h)
+            for h in range(args.batch)]
+
+
+def workload_config(args, extra=None):
+    cfg = {"workload": "CS-WGS batch of %d point-cloud holograms, P=%d (M=%d), N=%d, c=%g, %d iterations "
+                       "(%d compressed + 2 full) + final pass" % (args.batch, args.P, args.P * args.P, args.N,
+                                                                args.c, args.iters, args.iters - 2),
+           "P": args.P, "M": args.P * args.P, "N": args.N, "subset_fraction": args.c,
+           "iterations": args.iters, "full_iterations": 2, "batch": args.batch,
+           "spots": "alpha,beta~U[-P/4,P/4] cycles, gamma~U[-10,10] waves, a=1, theta0~U[0,2pi)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def pairs_per_hologram(args):
+    Mp = math.floor(args.c * args.P * args.P)
+    M = args.P * args.P
+    F = min(2, args.iters)
+    return args.N * (2 * (args.iters - F) * Mp + 2 * F * M + 2 * M)
+
+
+# ---------------------------------------------------------------- clocks --
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------- reference arm --
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the host cores, one hologram of the workload per step."""
+    if rank != 0:
+        return
+    import oracle
+    pbs = problems(args, 0)
+    cores = oracle.threads()
+    times = []
+    for s in range(args.warmup + args.steps):
+        pb = pbs[s % len(pbs)]
+        t0 = time.perf_counter()
+        oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = len(times) / total
+    sample = "one hologram of the workload per step (P=%d, N=%d, c=%g, %d iterations), FP64" % (
+        args.P, args.N, args.c, args.iters)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, {"batch": 1}),
+            "cpu_baseline": {"value": value, "unit": "holograms/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "holograms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- our arm --
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2003_05293_gb300 import Plan
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    pbs = problems(args, rank)
+    B = len(pbs)
+    stream = torch.cuda.current_stream()
+    plan = Plan(device=local, precision="fp32", max_batch=max(64, B), max_N=max(1024, args.N),
+                stream=stream.cuda_stream)
+    outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+    batch = plan.batch(pbs, outs)
+    total_pairs, iter_pairs = batch.pairs()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+
+    for _ in range(args.warmup):
+        batch.run()
+        batch.results()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms, iter_ms, iter_n = [], 0.0, 0
+    ev0.record(stream)
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)                       # evict L2 between steps
+        batch.run()                          # graph launch on the same stream
+        res = batch.results()                # waits for the step
+        kt = batch.kernel_times()            # prep, then one entry per persistent launch
+        step_ms.append(sum(kt))
+        iter_ms += sum(kt[1:])
+        iter_n += len(kt) - 1
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = B * world * args.steps / (total_ms * 1e-3)
+
+    # roofline of the iteration kernel: algorithmic sine+cosine per pair
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    max_mhz = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        max_mhz = float(mp.get("sm_max_mhz", max_mhz))
+    except (OSError, ValueError):
+        pass
+    peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9        # G sincos-op/s
+    achieved = 2.0 * total_pairs / (iter_ms / args.steps * 1e-3) / 1e9
+    probe, probe_mhz = plan.sincos_peak()
+
+    eu = [(r["e"], r["u"]) for r in res]
+    line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, {"l2": "flushed between steps (256 MB write), inside the timed region",
+                                             "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "what": "batch step = every hologram of the batch, submit to result"},
+            "quality": {"e_mean": float(np.mean([a for a, _ in eu])), "u_mean": float(np.mean([b for _, b in eu])),
+                        "u_min": float(np.min([b for _, b in eu])), "e_min": float(np.min([a for a, _ in eu]))},
+            "roofline": {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": achieved, "peak": peak,
+                         "unit": "G sincos/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "iter_kernel (all %d persistent launches of a step)" % iter_n_per_step(iter_n, args),
+                         "peak_basis": "%d SMs x %d/clk x %.0f MHz" % (sm_count, SFU_PER_CLK_PER_SM, max_mhz),
+                         "probe_measured": probe / 1e9, "probe_sm_mhz": probe_mhz,
+                         "algorithmic_pairs_per_step": total_pairs},
+            "gpu_launches": args.steps * (1 + iter_n_per_step(iter_n, args)),
+            "clocks": clk}
+
+    # FP64 GPU baseline (plain double-precision kernels), one hologram at a time
+    if not args.no_fp64:
+        with Plan(device=local, precision="fp64") as p64:
+            pb = pbs[0]
+            o = torch.empty(pb.M, dtype=torch.float32, device="cuda")
+            p64.solve(pb.xyz, pb.P, pb.c, 2, pb.seed, out=o)      # warm-up
+            torch.cuda.synchronize()
+            n64, t0 = 0, time.perf_counter()
+            while n64 < 2:
+                p64.solve(pbs[n64].xyz, pb.P, pb.c, pb.iterations, pbs[n64].seed, out=o)
+                n64 += 1
+            torch.cuda.synchronize()
+            v64 = n64 / (time.perf_counter() - t0)
+        line["fp64_gpu_baseline"] = {"value": v64, "unit": "holograms/s", "holograms": n64,
+                                     "speedup_fp32_batched": value / v64 / world}
+
+    # end to end through the C ABI: host inputs in, host phase maps and e, u out
+    if not args.no_e2e:
+        host_outs = [np.empty(pb.M, dtype=np.float32) for pb in pbs]
+        plan.solve_batch(pbs, host_outs)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.solve_batch(pbs, host_outs)
+        dt = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": B * world * args.e2e_steps / dt, "unit": "holograms/s",
+                       "h2d_bytes_per_step": int(sum(pb.N * 3 * 8 for pb in pbs)),
+                       "d2h_bytes_per_step": int(sum(pb.M * 4 + 16 for pb in pbs)),
+                       "api": "cswgs_solve_batch, pageable host buffers"}
+
+    # the FP64 CPU oracle on a bounded sample (rank 0, single GPU runs only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        pb = pbs[0]
+        t0 = time.perf_counter()
+        oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "holograms/s", "cores": oracle.threads(),
+                                "kind": "oracle",
+                                "sample": "1 hologram of the workload (P=%d, N=%d, c=%g, %d iterations), FP64 C "
+                                          "with OpenMP, %.1f s" % (pb.P, pb.N, pb.c, pb.iterations, dt)}
+    batch.close()
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def iter_n_per_step(iter_n, args):
+    return iter_n // max(1, args.steps)
+
+
+if __name__ == "__main__":
+    main()

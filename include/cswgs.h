@@ -1,0 +1,255 @@
+/*
+ * cswgs.h -- C ABI of the GB300 (sm_103a) CS-WGS hologram library.
+ *
+ * The library computes phase-only holograms for 3D point clouds with the
+ * compressed-sensing weighted Gerchberg-Saxton method (CS-WGS) of Pozzi &
+ * Mapelli: back-propagation of the spot fields to the SLM (Eq. 1) with the
+ * lens-and-prism spot phases of Eq. 2, forward projection onto the spots
+ * (Eq. 3) over a random pixel subset, the weighted update of Eqs. 4-6, a
+ * final pass over all pixels, and the efficiency / uniformity metrics (Eq. 7).
+ *
+ * Conventions for every entry point:
+ *  - All functions return a cswgs_status and never throw or abort.  On
+ *    failure cswgs_last_error() gives a one-line message (per host thread).
+ *  - Input arrays are read during the call only; the caller may free or
+ *    reuse them when it returns.  Outputs go to caller-owned memory.
+ *  - Spot units (Eq. 2, normalised): spots_xyz holds N triples
+ *    (alpha, beta, gamma) of doubles, row-major N x 3.  alpha and beta are the
+ *    tilt in cycles across the P-pixel aperture, gamma the defocus in waves at
+ *    the aperture edge, so that the phase of spot n at pixel (i, r) is
+ *        phi_n = 2 pi [ (alpha x' + beta y') / P + gamma (x'^2 + y'^2) / (P/2)^2 ]
+ *    with x' = i - P/2, y' = r - P/2, pixel index m = r * P + i.
+ *  - amplitudes: N doubles a_n^0 > 0 (NULL = all 1).
+ *  - The phase map is P * P floats, row-major (m = r * P + i), in [0, 2 pi).
+ *  - A plan is not thread-safe: use one plan per host thread, or the
+ *    submit / poll serving calls, which are internally locked.
+ *  - Argument checks (each failing with CSWGS_EINVAL): 2 <= P <= max_P and P
+ *    even; 1 <= N <= max_N; 0 < subset_fraction <= 1 and
+ *    Mp = floor(subset_fraction * P * P) >= 1; iterations >= 0; finite spot
+ *    coordinates; amplitudes finite and > 0.
+ */
+#ifndef CSWGS_H
+#define CSWGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSWGS_ABI_VERSION 1
+
+typedef struct cswgs_plan_s *cswgs_plan;
+typedef struct cswgs_batch_s *cswgs_batch;
+
+typedef enum {
+    CSWGS_OK = 0,
+    CSWGS_EINVAL = 1,      /* bad argument */
+    CSWGS_ENOMEM = 2,      /* device or host allocation failed, or admission refused */
+    CSWGS_ECUDA = 3,       /* a CUDA call failed (message in cswgs_last_error) */
+    CSWGS_ETIMEOUT = 4,    /* a bounded wait ran out */
+    CSWGS_EBUSY = 5,       /* serving: the request is not finished yet */
+    CSWGS_ECANCELLED = 6,  /* serving: the request was cancelled */
+    CSWGS_ENOTFOUND = 7    /* serving: unknown or already collected ticket */
+} cswgs_status;
+
+typedef enum {
+    CSWGS_FP64 = 0,             /* plain double-precision kernels (the baseline solver) */
+    CSWGS_FP32 = 1,             /* fixed-point phase range reduction + FP32 sincos, FP64 metrics */
+    CSWGS_FP32_FP16SINCOS = 2   /* as FP32, with half-precision sincos in the compressed iterations */
+} cswgs_precision;
+
+/* ---------------------------------------------------------------- plan --- */
+
+typedef struct {
+    int device;                 /* CUDA device ordinal */
+    int max_P;                  /* largest grid side accepted */
+    int max_N;                  /* largest spot count accepted */
+    int max_batch;              /* largest batch, and number of serving slots */
+    size_t mem_cap_bytes;       /* device bytes the serving loop may hold (0: half the free memory, at most 16 GiB) */
+    cswgs_precision precision;
+    void *stream;               /* cudaStream_t to run on; NULL: the plan creates its own */
+    const char *tune_cache;     /* autotuner JSON cache file; NULL: keep tunings in memory only */
+} cswgs_plan_desc;
+
+/* Fills d with defaults: device 0, max_P 2048, max_N 1024, max_batch 64,
+ * mem_cap 0, FP32, NULL stream, no tune cache. */
+void cswgs_plan_desc_default(cswgs_plan_desc *d);
+
+/* Creates a plan: binds the device, creates or adopts the stream, reads the
+ * tune cache.  *out receives an opaque handle owned by the library. */
+cswgs_status cswgs_plan_create(cswgs_plan *out, const cswgs_plan_desc *d);
+
+/* Stops the serving loop (cancelling pending requests), frees every device
+ * buffer and graph of the plan.  NULL is accepted. */
+cswgs_status cswgs_plan_destroy(cswgs_plan p);
+
+/* --------------------------------------------------------------- solve --- */
+
+/* One hologram, synchronous.  The method (Section 2): w_n = 1 and theta_n^0
+ * ~ U[0, 2 pi) drawn from `seed` (the random-superposition start, Eq. 1);
+ * `iterations` WGS iterations, each a back-propagation (Eq. 1) and forward
+ * projection (Eq. 3) over the iteration's pixel set followed by the update of
+ * Eqs. 4-6; the pixel set is a random subset S_j of Mp = floor(c P^2)
+ * pixels drawn from (seed, j) for all but the last two iterations, which run
+ * over all pixels as Section 2 prescribes; then a full back-propagation
+ * writes the phase map, and a full forward projection gives
+ *   e = sum_n |V_n|^2 (power fraction at the spots) and u by Eq. 7,
+ * with V_n = (1/P^2) sum_m e^{i(Phi_m - phi_n(m))}.
+ * iterations = 0 gives the random-superposition hologram; c = 1 plain WGS.
+ * phase_out: P*P floats, a device pointer (e.g. a torch tensor's data) or,
+ * when out_on_host != 0, a host pointer.  e, u: host doubles (either may be
+ * NULL).  Blocks until the result is written. */
+cswgs_status cswgs_solve(cswgs_plan p, const double *spots_xyz, const double *amplitudes,
+                         int N, int P, double subset_fraction, int iterations, uint64_t seed,
+                         float *phase_out, int out_on_host, double *e, double *u);
+
+/* Options of cswgs_solve_ex; cswgs_solve_opts_default() gives the
+ * cswgs_solve behaviour. */
+typedef struct {
+    int full_iterations;        /* how many of the last iterations use all pixels (default 2, Section 2) */
+    int first_iteration;        /* index j of the first iteration, keying its subset (default 1) */
+    int final_pass;             /* 1: full back-propagation + metrics (default); 0: state only */
+    const double *init_w;       /* host, N weights to start from, or NULL (all 1) */
+    const double *init_theta;   /* host, N spot phases (radians) to start from, or NULL (drawn from seed) */
+    double *final_w;            /* host, N: the weights after the last iteration, or NULL */
+    double *final_theta;        /* host, N: the spot phases after the last iteration (radians), or NULL */
+    double *spot_intensity;     /* host, N: I_n = |V_n|^2 of the final hologram, or NULL */
+} cswgs_solve_opts;
+
+void cswgs_solve_opts_default(cswgs_solve_opts *o);
+
+/* cswgs_solve with options: resume from or teacher-force a state (init_w,
+ * init_theta, first_iteration), choose the schedule (full_iterations), skip
+ * the final pass, and read back the state.  With final_pass = 0 the phase
+ * map, e and u are not written (phase_out may be NULL). */
+cswgs_status cswgs_solve_ex(cswgs_plan p, const double *spots_xyz, const double *amplitudes,
+                            int N, int P, double subset_fraction, int iterations, uint64_t seed,
+                            const cswgs_solve_opts *opts, float *phase_out, int out_on_host,
+                            double *e, double *u);
+
+/* The pixel subset S_j of iteration j (Section 2, CS-WGS; Section 3,
+ * "Compressed sensing": pixels taken in a random order): out_device[k] =
+ * pi_{seed,j}(k) for 0 <= k < Mp, where pi is the library's keyed
+ * permutation of [0, P^2).  out_device: device int32 array of Mp entries,
+ * caller-owned.  Runs the same device code the solver uses.  Synchronous. */
+cswgs_status cswgs_subset(cswgs_plan p, int P, int64_t Mp, uint64_t seed, int j,
+                          int32_t *out_device);
+
+/* ------------------------------------------------- batches and graphs --- */
+
+/* One hologram of a batch or a serving request. */
+typedef struct {
+    const double *spots_xyz;    /* host, N x 3 (copied at the call) */
+    const double *amplitudes;   /* host, N, or NULL */
+    int N;
+    int P;
+    double subset_fraction;
+    int iterations;
+    uint64_t seed;
+    int full_iterations;        /* < 0: the default 2 */
+    float *phase_out;           /* P*P floats: device pointer, or host when out_on_host; NULL: not written */
+    int out_on_host;
+} cswgs_request;
+
+typedef struct {
+    cswgs_status status;
+    double e;                   /* efficiency */
+    double u;                   /* uniformity, Eq. 7 */
+    double latency_ms;          /* serving: submit -> result ready; batches: the batch's run time */
+    double queue_ms;            /* serving: submit -> admitted */
+} cswgs_result;
+
+/* Prepares a batch of `count` holograms (count <= max_batch) to be run many
+ * times: copies the inputs to the device, allocates their state and
+ * workspace, picks tile shapes (autotuner) and captures the whole hot path
+ * (spot preparation, every iteration of every hologram as one persistent
+ * launch per iteration, final pass, metrics) into one CUDA graph.  Every
+ * request's phase_out must be a device pointer (or NULL).  FP32 plans only. */
+cswgs_status cswgs_batch_create(cswgs_plan p, const cswgs_request *reqs, int count,
+                                cswgs_batch *out);
+
+/* Launches the batch's graph on the plan's stream and returns (asynchronous). */
+cswgs_status cswgs_batch_run(cswgs_batch b);
+
+/* Waits for the last run and copies e, u of each hologram to results[count]. */
+cswgs_status cswgs_batch_results(cswgs_batch b, cswgs_result *results);
+
+/* Device time of each kernel launch of the last run, in milliseconds, in
+ * launch order (spot preparation, then one entry per iteration launch, then
+ * the final pass), measured with CUDA events recorded inside the graph.
+ * *count receives the number of launches; ms may be NULL to query it. */
+cswgs_status cswgs_batch_kernel_times(cswgs_batch b, float *ms, int cap, int *count);
+
+/* Algorithmic sincos evaluations (pixel-spot phasors; each is one sine and one
+ * cosine) of one run of the batch, for throughput accounting: per hologram
+ * N * (2 * (I - F) * Mp + 2 * F * M + 2 * M), F = min(full_iterations, I). */
+cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs_iter_launches);
+
+cswgs_status cswgs_batch_destroy(cswgs_batch b);
+
+/* Runs `count` requests (host or device outputs) as one batch, synchronous:
+ * the convenience form of create + run + results + destroy, reusing a cached
+ * graph when the batch has the same shape as an earlier call. */
+cswgs_status cswgs_solve_batch(cswgs_plan p, const cswgs_request *reqs, int count,
+                               cswgs_result *results);
+
+/* --------------------------------------------------------------- serving --- */
+
+/* Continuous batching: a host thread of the plan admits queued requests as
+ * serving slots and device memory (mem_cap_bytes) allow, keeps each admitted
+ * request's state (w, theta, phase map, workspace) on the device, and advances
+ * every admitted request by one iteration per persistent launch; requests join
+ * and leave between launches.  The serving loop starts on the first submit. */
+
+/* Queues a request (inputs are copied).  *ticket identifies it.  A request
+ * whose footprint can never fit mem_cap_bytes fails with CSWGS_ENOMEM. */
+cswgs_status cswgs_submit(cswgs_plan p, const cswgs_request *r, uint64_t *ticket);
+
+/* CSWGS_EBUSY while pending; CSWGS_OK with *res filled once finished (the
+ * ticket is then released); CSWGS_ECANCELLED / CSWGS_ENOTFOUND otherwise. */
+cswgs_status cswgs_poll(cswgs_plan p, uint64_t ticket, cswgs_result *res);
+
+/* As cswgs_poll, but waits up to timeout_s seconds (CSWGS_ETIMEOUT after). */
+cswgs_status cswgs_wait(cswgs_plan p, uint64_t ticket, double timeout_s, cswgs_result *res);
+
+/* Cancels a queued or running request; its slot is freed before the next launch. */
+cswgs_status cswgs_cancel(cswgs_plan p, uint64_t ticket);
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, rejected;
+    uint64_t launches;          /* persistent launches issued */
+    int active;                 /* requests holding a slot now */
+    int queued;                 /* requests waiting for admission */
+    size_t bytes_in_use;        /* device bytes held by admitted requests */
+    size_t bytes_cap;
+    double busy_ms;             /* summed device time of the serving launches */
+} cswgs_serve_stats;
+
+cswgs_status cswgs_serve_stats_get(cswgs_plan p, cswgs_serve_stats *s);
+
+/* ------------------------------------------------------ tuning, probes --- */
+
+/* Times the candidate tile shapes (threads per block, pixels per thread) of
+ * the FP32 iteration kernel on a synthetic hologram of this size, keeps the
+ * fastest for the (P, N) bucket and writes the tune cache if the plan has one.
+ * *best_ms (may be NULL) receives the best per-iteration time. */
+cswgs_status cswgs_autotune(cswgs_plan p, int P, int N, double subset_fraction, double *best_ms);
+
+/* Measures the device's sincos throughput with a kernel that does nothing but
+ * FP32 sine and cosine approximations: *sincos_per_s receives sine-or-cosine
+ * results per second, *sm_mhz the SM clock seen during the run. */
+cswgs_status cswgs_sincos_peak(cswgs_plan p, double *sincos_per_s, double *sm_mhz);
+
+/* ---------------------------------------------------------------- misc --- */
+
+int cswgs_abi_version(void);
+const char *cswgs_status_string(cswgs_status s);
+const char *cswgs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSWGS_H */

@@ -1,0 +1,265 @@
+"""GB300 (sm_103a) CS-WGS point-cloud hologram library: Python binding.
+
+The work happens in ``lib/libcswgs.so`` (hand-written CUDA kernels behind the
+C ABI of ``include/cswgs.h``).  This package marshals arguments: numpy arrays
+for host data, torch CUDA tensors for device buffers (data pointers only), and
+the torch stream handle when the caller wants the plan on its stream.
+
+    plan = Plan(precision="fp32")
+    out = torch.empty(P * P, device="cuda")
+    r = plan.solve(xyz, P=1152, c=0.125, iterations=30, seed=0, out=out)
+    r["e"], r["u"]
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi
+from .capi import (CSWGS_FP32, CSWGS_FP32_FP16SINCOS, CSWGS_FP64, CswgsError, check,
+                   cswgs_plan_desc, cswgs_request, cswgs_result, cswgs_serve_stats,
+                   cswgs_solve_opts)
+
+__all__ = ["Plan", "Batch", "CswgsError", "PRECISIONS", "capi"]
+
+PRECISIONS = {"fp64": CSWGS_FP64, "fp32": CSWGS_FP32, "fp32_fp16sincos": CSWGS_FP32_FP16SINCOS}
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(capi.c_double_p)
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+def _out_ptr(out):
+    """(float*, on_host) for a torch CUDA tensor, a numpy float32 array or None."""
+    if out is None:
+        return None, 0
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float32 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("host output must be a contiguous float32 array")
+        return out.ctypes.data_as(capi.c_float_p), 1
+    # torch tensor
+    if not out.is_cuda or out.dtype.__str__() != "torch.float32" or not out.is_contiguous():
+        raise ValueError("device output must be a contiguous float32 CUDA tensor")
+    return ctypes.cast(ctypes.c_void_p(out.data_ptr()), capi.c_float_p), 0
+
+
+class Plan:
+    """A cswgs_plan: device, stream, limits, precision, tunings and serving loop."""
+
+    def __init__(self, device: int = 0, max_P: int = 2048, max_N: int = 1024, max_batch: int = 64,
+                 mem_cap_bytes: int = 0, precision: str = "fp32", stream=None, tune_cache=None):
+        self.lib = capi.load()
+        d = cswgs_plan_desc()
+        self.lib.cswgs_plan_desc_default(ctypes.byref(d))
+        d.device, d.max_P, d.max_N, d.max_batch = device, max_P, max_N, max_batch
+        d.mem_cap_bytes = mem_cap_bytes
+        d.precision = PRECISIONS[precision]
+        d.stream = stream
+        self._tune_cache = tune_cache.encode() if tune_cache else None
+        d.tune_cache = self._tune_cache
+        h = ctypes.c_void_p()
+        check(self.lib.cswgs_plan_create(ctypes.byref(h), ctypes.byref(d)), "cswgs_plan_create")
+        self.handle = h
+        self.precision = precision
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.cswgs_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------- solve --
+    def solve(self, xyz, P: int, c: float, iterations: int, seed: int, amp=None, out=None,
+              full_iterations: int = 2, first_iteration: int = 1, final_pass: bool = True,
+              init_w=None, init_theta=None, state: bool = False):
+        """cswgs_solve_ex; returns dict(e, u[, w, theta, I])."""
+        xyz = _f64(xyz, (-1, 3))
+        N = xyz.shape[0]
+        amp = _f64(amp)
+        init_w = _f64(init_w)
+        init_theta = _f64(init_theta)
+        o = cswgs_solve_opts()
+        self.lib.cswgs_solve_opts_default(ctypes.byref(o))
+        o.full_iterations = full_iterations
+        o.first_iteration = first_iteration
+        o.final_pass = 1 if final_pass else 0
+        o.init_w = _dptr(init_w)
+        o.init_theta = _dptr(init_theta)
+        w = np.empty(N) if state else None
+        th = np.empty(N) if state else None
+        In = np.empty(N) if state and final_pass else None
+        o.final_w = _dptr(w)
+        o.final_theta = _dptr(th)
+        o.spot_intensity = _dptr(In)
+        ptr, host = _out_ptr(out)
+        e = ctypes.c_double(float("nan"))
+        u = ctypes.c_double(float("nan"))
+        check(self.lib.cswgs_solve_ex(self.handle, _dptr(xyz), _dptr(amp), N, P, float(c), int(iterations),
+                                      int(seed) & (2**64 - 1), ctypes.byref(o), ptr, host,
+                                      ctypes.byref(e), ctypes.byref(u)), "cswgs_solve_ex")
+        res = {"e": e.value, "u": u.value}
+        if state:
+            res.update(w=w, theta=th, I=In)
+        return res
+
+    def solve_simple(self, xyz, P, c, iterations, seed, amp=None, out=None):
+        """cswgs_solve (the plain entry point)."""
+        xyz = _f64(xyz, (-1, 3))
+        amp = _f64(amp)
+        ptr, host = _out_ptr(out)
+        e = ctypes.c_double()
+        u = ctypes.c_double()
+        check(self.lib.cswgs_solve(self.handle, _dptr(xyz), _dptr(amp), xyz.shape[0], P, float(c),
+                                   int(iterations), int(seed) & (2**64 - 1), ptr, host,
+                                   ctypes.byref(e), ctypes.byref(u)), "cswgs_solve")
+        return {"e": e.value, "u": u.value}
+
+    def subset(self, P: int, Mp: int, seed: int, j: int, out):
+        """cswgs_subset into a CUDA int32 tensor of Mp entries."""
+        ptr = ctypes.cast(ctypes.c_void_p(out.data_ptr()), ctypes.POINTER(ctypes.c_int32))
+        check(self.lib.cswgs_subset(self.handle, P, Mp, int(seed) & (2**64 - 1), j, ptr), "cswgs_subset")
+
+    # ----------------------------------------------------------- batches --
+    def _requests(self, problems, outs):
+        n = len(problems)
+        reqs = (cswgs_request * n)()
+        keep = []
+        for i, pb in enumerate(problems):
+            xyz = _f64(pb.xyz, (-1, 3))
+            amp = _f64(pb.amp)
+            keep += [xyz, amp]
+            r = reqs[i]
+            r.spots_xyz = _dptr(xyz)
+            r.amplitudes = _dptr(amp)
+            r.N = xyz.shape[0]
+            r.P = pb.P
+            r.subset_fraction = pb.c
+            r.iterations = pb.iterations
+            r.seed = int(pb.seed) & (2**64 - 1)
+            r.full_iterations = int(pb.extra.get("full_iterations", 2)) if hasattr(pb, "extra") else 2
+            ptr, host = _out_ptr(outs[i] if outs is not None else None)
+            r.phase_out = ptr
+            r.out_on_host = host
+        return reqs, keep
+
+    def batch(self, problems, outs=None) -> "Batch":
+        reqs, keep = self._requests(problems, outs)
+        h = ctypes.c_void_p()
+        check(self.lib.cswgs_batch_create(self.handle, reqs, len(problems), ctypes.byref(h)),
+              "cswgs_batch_create")
+        return Batch(self, h, len(problems), keep + [outs])
+
+    def solve_batch(self, problems, outs=None):
+        reqs, keep = self._requests(problems, outs)
+        res = (cswgs_result * len(problems))()
+        check(self.lib.cswgs_solve_batch(self.handle, reqs, len(problems), res), "cswgs_solve_batch")
+        return [{"e": r.e, "u": r.u, "latency_ms": r.latency_ms} for r in res]
+
+    # ----------------------------------------------------------- serving --
+    def submit(self, pb, out=None) -> int:
+        reqs, keep = self._requests([pb], [out])
+        t = ctypes.c_uint64()
+        check(self.lib.cswgs_submit(self.handle, reqs, ctypes.byref(t)), "cswgs_submit")
+        self._keep[t.value] = (reqs, keep, out)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else dict(status, e, u, latency_ms, queue_ms)."""
+        r = cswgs_result()
+        st = self.lib.cswgs_poll(self.handle, ticket, ctypes.byref(r))
+        if st == capi.CSWGS_EBUSY:
+            return None
+        self._keep.pop(ticket, None)
+        if st not in (capi.CSWGS_OK, capi.CSWGS_ECANCELLED):
+            check(st, "cswgs_poll")
+        return {"status": st, "e": r.e, "u": r.u, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms}
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        r = cswgs_result()
+        st = self.lib.cswgs_wait(self.handle, ticket, float(timeout_s), ctypes.byref(r))
+        if st not in (capi.CSWGS_OK, capi.CSWGS_ECANCELLED):
+            check(st, "cswgs_wait")
+        self._keep.pop(ticket, None)
+        return {"status": st, "e": r.e, "u": r.u, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms}
+
+    def cancel(self, ticket: int) -> int:
+        return self.lib.cswgs_cancel(self.handle, ticket)
+
+    def serve_stats(self) -> dict:
+        s = cswgs_serve_stats()
+        check(self.lib.cswgs_serve_stats_get(self.handle, ctypes.byref(s)), "cswgs_serve_stats_get")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    # ------------------------------------------------------ tuning/probes --
+    def autotune(self, P: int, N: int, c: float) -> float:
+        ms = ctypes.c_double()
+        check(self.lib.cswgs_autotune(self.handle, P, N, float(c), ctypes.byref(ms)), "cswgs_autotune")
+        return ms.value
+
+    def sincos_peak(self):
+        v = ctypes.c_double()
+        mhz = ctypes.c_double()
+        check(self.lib.cswgs_sincos_peak(self.handle, ctypes.byref(v), ctypes.byref(mhz)), "cswgs_sincos_peak")
+        return v.value, mhz.value
+
+
+class Batch:
+    """A cswgs_batch: device-resident holograms with a captured CUDA graph."""
+
+    def __init__(self, plan: Plan, handle, count: int, keep):
+        self.plan, self.handle, self.count, self._keep = plan, handle, count, keep
+        self.lib = plan.lib
+
+    def run(self):
+        check(self.lib.cswgs_batch_run(self.handle), "cswgs_batch_run")
+
+    def results(self):
+        res = (cswgs_result * self.count)()
+        check(self.lib.cswgs_batch_results(self.handle, res), "cswgs_batch_results")
+        return [{"e": r.e, "u": r.u, "latency_ms": r.latency_ms} for r in res]
+
+    def kernel_times(self):
+        n = ctypes.c_int()
+        check(self.lib.cswgs_batch_kernel_times(self.handle, None, 0, ctypes.byref(n)), "kernel_times")
+        ms = (ctypes.c_float * n.value)()
+        check(self.lib.cswgs_batch_kernel_times(self.handle, ms, n.value, ctypes.byref(n)), "kernel_times")
+        return list(ms)
+
+    def pairs(self):
+        a = ctypes.c_double()
+        b = ctypes.c_double()
+        check(self.lib.cswgs_batch_pairs(self.handle, ctypes.byref(a), ctypes.byref(b)), "cswgs_batch_pairs")
+        return a.value, b.value
+
+    def close(self):
+        if self.handle:
+            self.lib.cswgs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

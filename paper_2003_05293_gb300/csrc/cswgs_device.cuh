@@ -1,0 +1,158 @@
+// Device primitives of the CS-WGS kernels: the seeded draws (theta^0 and the
+// per-iteration pixel subsets), the fixed-point lens-and-prism phase of Eq. 2
+// with its exact range reduction, and sincos of a fixed-point phase.
+#pragma once
+
+#include <stdint.h>
+
+namespace cswgs {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+// ------------------------------------------------------------ seeded draws --
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), counter form: output k of the
+// sequence whose state starts at `seed` and advances by the golden gamma.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// MurmurHash3 32-bit finaliser (Appleby).
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// theta_n^0 in turns, as a 53-bit fraction of [0, 1): the random phases of
+// the random-superposition start (Eq. 1).  Draw n of the seed's sequence.
+__host__ __device__ __forceinline__ double theta0_turns(uint64_t seed, int n)
+{
+    return (double)(splitmix64(seed, (uint64_t)n) >> 11) * 0x1.0p-53;
+}
+
+// Round keys of the subset permutation of iteration j: outputs 2^32 + 4j + r
+// of the seed's sequence, upper 32 bits.
+struct SubsetKeys {
+    uint32_t k0, k1, k2, k3;
+};
+
+__host__ __device__ __forceinline__ SubsetKeys subset_keys(uint64_t seed, int j)
+{
+    uint64_t base = 0x100000000ull + 4ull * (uint64_t)(uint32_t)j;
+    SubsetKeys K;
+    K.k0 = (uint32_t)(splitmix64(seed, base + 0) >> 32);
+    K.k1 = (uint32_t)(splitmix64(seed, base + 1) >> 32);
+    K.k2 = (uint32_t)(splitmix64(seed, base + 2) >> 32);
+    K.k3 = (uint32_t)(splitmix64(seed, base + 3) >> 32);
+    return K;
+}
+
+__device__ __forceinline__ void feistel_round(uint32_t &L, uint32_t &R, uint32_t key, uint32_t P)
+{
+    uint32_t F = __umulhi(fmix32(R ^ key), P);   // in [0, P)
+    uint32_t nr = L + F;
+    nr = nr >= P ? nr - P : nr;                  // (L + F) mod P, both < P
+    L = R;
+    R = nr;
+}
+
+// pi_{seed,j}(k): keyed bijection of [0, P^2).  k = L P + R; four rounds of
+// (L, R) -> (R, (L + F(R)) mod P); result L P + R.  The subset S_j of an
+// iteration is the image of [0, Mp) (Section 2, CS-WGS; Section 3,
+// "Compressed sensing": a random pixel order, c M pixels per iteration).
+__device__ __forceinline__ uint32_t permute(uint32_t k, uint32_t P, const SubsetKeys &K)
+{
+    uint32_t L = k / P;
+    uint32_t R = k - L * P;
+    feistel_round(L, R, K.k0, P);
+    feistel_round(L, R, K.k1, P);
+    feistel_round(L, R, K.k2, P);
+    feistel_round(L, R, K.k3, P);
+    return L * P + R;
+}
+
+// ------------------------------------------------------ fixed-point phase --
+// Phases are carried in turns as 32-bit fixed point (2^32 = one turn), so
+// arithmetic mod 2^32 is arithmetic mod 2 pi with no rounding: the range
+// reduction of the lens-and-prism argument (Eq. 2, up to a few hundred turns
+// at P = 1152) is exact.  The spot coefficients (turns per pixel, FP64 on the
+// host side of the kernel) are split into 32-bit words:
+//   tilt:    A = a * 2^32, B = b * 2^32           (a = alpha/P, b = beta/P)
+//   defocus: g * 2^32 = Gh + Gl * 2^-32           (g = gamma/(P/2)^2)
+// so that phi_n(m) * 2^32 / (2 pi) = A x' + B y' + Gh rho^2 + hi32(Gl rho^2)
+// (mod 2^32) to within 2 units, for integer pixel coordinates x', y' and
+// rho^2 = x'^2 + y'^2 < 2^32.
+struct SpotFix {
+    int32_t A, B, Gh;
+    uint32_t Gl;
+};
+
+// Nearest 32-bit fixed-point turn of a real number of turns (mod 1).
+__device__ __forceinline__ uint32_t turns_to_fix(double t)
+{
+    double f = t - rint(t);                        // [-0.5, 0.5], exact
+    return (uint32_t)(int64_t)llrint(f * 4294967296.0);
+}
+
+__device__ __forceinline__ SpotFix spot_fix(double alpha, double beta, double gamma, int P)
+{
+    SpotFix s;
+    s.A = (int32_t)turns_to_fix(alpha / (double)P);
+    s.B = (int32_t)turns_to_fix(beta / (double)P);
+    double half = 0.5 * (double)P;
+    double g = gamma / (half * half);
+    g = g - rint(g);                               // rho^2 is an integer: g mod 1
+    double gs = g * 4294967296.0;                  // exact scaling
+    double gh = floor(gs);
+    double gl = rint((gs - gh) * 4294967296.0);    // in [0, 2^32]
+    int64_t ghi = (int64_t)gh;
+    if (gl >= 4294967296.0) { gl = 0.0; ghi += 1; }
+    s.Gh = (int32_t)(uint32_t)ghi;
+    s.Gl = (uint32_t)gl;
+    return s;
+}
+
+// Fixed-point phase of spot s at pixel (x', y', rho^2), plus an addend.
+__device__ __forceinline__ uint32_t fix_phase(const SpotFix &s, int32_t xp, int32_t yp,
+                                              uint32_t rho2, uint32_t addend)
+{
+    uint32_t t = addend + (uint32_t)s.A * (uint32_t)xp;
+    t += (uint32_t)s.B * (uint32_t)yp;
+    t += (uint32_t)s.Gh * rho2;
+    t += __umulhi(s.Gl, rho2);
+    return t;
+}
+
+// Rounding bias folded into every addend: the conversion below keeps the top
+// 23 bits of the phase, so adding half of the dropped range rounds to nearest.
+constexpr uint32_t kFixRound = 1u << 8;
+
+// sin and cos of 2 pi T / 2^32, T already carrying kFixRound.  The top 23 bits
+// of T become the mantissa of a float in [1, 2), i.e. 1 + turns; one FMA
+// turns it into radians in [0, 2 pi) with no offset error; the hardware
+// sine/cosine approximations finish.
+__device__ __forceinline__ void sincos_fix(uint32_t T, float &s, float &c)
+{
+    float f = __uint_as_float((T >> 9) | 0x3F800000u);
+    float x = fmaf(f, kTwoPiF, -kTwoPiF);
+    s = __sinf(x);
+    c = __cosf(x);
+}
+
+// Fixed-point turn of an angle in radians, as float (|x| <= pi).
+__device__ __forceinline__ uint32_t rad_to_fix(float x)
+{
+    // 2^32 / (2 pi) = 683565275.58...
+    return (uint32_t)__float2int_rn(x * 683565275.5764316f);
+}
+
+}  // namespace cswgs

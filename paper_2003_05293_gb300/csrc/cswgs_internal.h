@@ -1,0 +1,92 @@
+// Internal declarations shared by the kernels and the host runtime of the
+// CS-WGS library.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/cswgs.h"
+
+namespace cswgs {
+
+// Pass kinds of one persistent launch, per hologram slot.
+enum PassKind : int {
+    kPassSubset = 0,   // one CS iteration over the subset S_j, then the update (Eqs. 1, 3-6)
+    kPassFull = 1,     // one WGS iteration over all pixels, then the update
+    kPassFinal = 2     // full back-propagation -> phase map, full projection -> e, u (Eq. 7)
+};
+
+// Per-spot state of the FP32 solver.
+struct SpotState {
+    uint32_t theta;   // theta_n in fixed-point turns
+    float w;          // weight w_n (Eq. 4)
+    float a0;         // target amplitude a_n^0
+    float pad;
+};
+
+// One hologram's device buffers (FP32 solver).  All pointers are device.
+struct HoloDev {
+    int P, N;
+    int Mp;                 // subset size floor(c M)
+    int pad0;
+    uint64_t seed;
+    const double *xyz;      // N x 3 inputs
+    const double *amp;      // N or nullptr
+    const double *init_w;   // N or nullptr: start weights
+    const double *init_th;  // N or nullptr: start phases (radians)
+    int4 *coef;             // N fixed-point spot coefficients (SpotFix)
+    SpotState *state;       // N
+    float2 *part;           // tiles x N per-tile partial fields (iterations)
+    double2 *part64;        // tiles x N per-tile partial fields (final pass)
+    unsigned *counter;      // tiles finished in the current pass
+    float *phase_out;       // M or nullptr
+    double *metrics;        // 2 + N: e, u, I_0 .. I_{N-1}
+};
+
+// One hologram's share of one persistent launch.
+struct LaunchSlot {
+    int holo;         // index into the HoloDev array
+    int pass;         // PassKind
+    int j;            // iteration index (subset key) for kPassSubset
+    int tile_begin;   // first work item of this slot in the launch
+    int tiles;        // work items of this slot
+    int count;        // pixels of the pass (Mp or M)
+};
+
+// Tile shape of the FP32 iteration kernel.
+struct TileShape {
+    int threads;      // threads per block
+    int ppt;          // pixels per thread
+};
+
+// Kernel launchers (kernels_fp32.cu).
+cudaError_t launch_prep_fp32(const HoloDev *holos, int count, int maxN, cudaStream_t s);
+cudaError_t launch_iter_fp32(TileShape shape, const HoloDev *holos, const LaunchSlot *slots,
+                             int nslots, int total_tiles, int maxN, unsigned *queue,
+                             int grid, cudaStream_t s);
+int iter_fp32_max_grid(TileShape shape, int maxN, int sm_count);
+bool tile_shape_supported(TileShape shape);
+size_t iter_fp32_smem(TileShape shape, int maxN);
+cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_t *out,
+                                 cudaStream_t s);
+cudaError_t launch_sincos_probe(float *sink, long long *cycles, int iters, int blocks,
+                                int threads, cudaStream_t s);
+
+// FP64 baseline solver (kernels_fp64.cu): one hologram, plain kernels.
+struct Fp64Work {
+    double *xyz, *amp, *init_w, *init_th;
+    double *coef;        // N x 3: turns per pixel (a, b, g)
+    double *w, *theta;   // N
+    double *phi;         // M
+    int32_t *pix;        // Mp
+    double2 *part;       // chunks x N
+    double *metrics;     // 2 + N
+    int chunks;
+};
+cudaError_t fp64_solve(const Fp64Work &wk, int P, int N, int Mp, int iterations, int n_full,
+                       int first_j, uint64_t seed, int final_pass, float *phase_out,
+                       cudaStream_t s);
+
+}  // namespace cswgs

@@ -1,0 +1,360 @@
+// Host runtime: validation, FP32 batches (buffers, launch schedule, CUDA
+// graph, kernel timing) and the FP64 baseline driver.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "runtime.h"
+
+namespace cswgs {
+
+static thread_local std::string g_last_error;
+
+cswgs_status set_error(cswgs_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+
+static bool finite_all(const double *a, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+cswgs_status validate_request(const cswgs_plan_desc &d, const double *xyz, const double *amp, int N,
+                              int P, double c, int iterations, int n_full, HoloSpec *out)
+{
+    if (P < 2 || (P & 1) || P > d.max_P)
+        return set_error(CSWGS_EINVAL, "P=%d: need an even grid side in [2, %d]", P, d.max_P);
+    if (N < 1 || N > d.max_N) return set_error(CSWGS_EINVAL, "N=%d: need 1 <= N <= %d", N, d.max_N);
+    if (!(c > 0.0 && c <= 1.0)) return set_error(CSWGS_EINVAL, "subset fraction %g not in (0, 1]", c);
+    const int64_t M = (int64_t)P * P;
+    const int64_t Mp = (int64_t)std::floor(c * (double)M);
+    if (Mp < 1) return set_error(CSWGS_EINVAL, "subset fraction %g gives an empty subset at P=%d", c, P);
+    if (iterations < 0) return set_error(CSWGS_EINVAL, "iterations=%d < 0", iterations);
+    if (!xyz) return set_error(CSWGS_EINVAL, "spots_xyz is NULL");
+    if (!finite_all(xyz, (size_t)N * 3)) return set_error(CSWGS_EINVAL, "non-finite spot coordinate");
+    if (amp) {
+        for (int n = 0; n < N; ++n)
+            if (!std::isfinite(amp[n]) || !(amp[n] > 0.0))
+                return set_error(CSWGS_EINVAL, "amplitude %d is %g: need finite and > 0", n, amp[n]);
+    }
+    out->P = P;
+    out->N = N;
+    out->Mp = (int)Mp;
+    out->iterations = iterations;
+    out->n_full = n_full < 0 ? 2 : n_full;
+    out->xyz.assign(xyz, xyz + (size_t)N * 3);
+    out->has_amp = amp != nullptr;
+    if (amp) out->amp.assign(amp, amp + N);
+    return CSWGS_OK;
+}
+
+int schedule_launches(const HoloSpec &h) { return h.iterations + (h.final_pass ? 1 : 0); }
+
+int pass_of(const HoloSpec &h, int L)
+{
+    if (L < h.iterations) {
+        int F = h.n_full < h.iterations ? h.n_full : h.iterations;
+        return L >= h.iterations - F ? kPassFull : kPassSubset;
+    }
+    if (L == h.iterations && h.final_pass) return kPassFinal;
+    return -1;
+}
+
+static int pass_count(const HoloSpec &h, int pass)
+{
+    return pass == kPassSubset ? h.Mp : h.P * h.P;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Fp32Batch::~Fp32Batch()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto e : events) cudaEventDestroy(e);
+    if (staging) cudaFreeHost(staging);
+}
+
+// Builds the device side of a batch with a given tile shape.
+static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> specs, TileShape shape,
+                                      bool timing, bool host_out, std::unique_ptr<Fp32Batch> *out)
+{
+    auto b = std::make_unique<Fp32Batch>();
+    b->plan = p;
+    b->specs = std::move(specs);
+    b->shape = shape;
+    b->timing = timing;
+    const int count = (int)b->specs.size();
+    const int tp = shape.threads * shape.ppt;
+
+    // inputs block (mirrored in pinned staging)
+    size_t in = 0;
+    b->in_off.resize(count);
+    for (int h = 0; h < count; ++h) {
+        const HoloSpec &s = b->specs[h];
+        b->in_off[h] = in;
+        in += align256(sizeof(double) * 3 * s.N);
+        if (s.has_amp) in += align256(sizeof(double) * s.N);
+        if (s.has_init_w) in += align256(sizeof(double) * s.N);
+        if (s.has_init_th) in += align256(sizeof(double) * s.N);
+    }
+    b->in_bytes = in;
+    // work buffers
+    size_t work = in;
+    std::vector<size_t> w_off(count);
+    b->maxN = 0;
+    for (int h = 0; h < count; ++h) {
+        const HoloSpec &s = b->specs[h];
+        const int M = s.P * s.P;
+        const int tiles_it = (std::max(s.Mp, s.iterations > 0 && s.n_full > 0 ? M : 0) + tp - 1) / tp;
+        const int tiles_full = (M + tp - 1) / tp;
+        w_off[h] = work;
+        work += align256(sizeof(int4) * s.N);                                   // coef
+        work += align256(sizeof(SpotState) * s.N);                              // state
+        work += align256(sizeof(float2) * (size_t)tiles_it * s.N);              // part
+        work += align256(sizeof(double2) * (size_t)(s.final_pass ? tiles_full : 1) * s.N);  // part64
+        work += 256;                                                            // counter
+        work += align256(sizeof(double) * (2 + s.N));                           // metrics
+        if (host_out) work += align256(sizeof(float) * (size_t)M);              // own phase
+        b->maxN = std::max(b->maxN, s.N);
+    }
+    CSWGS_TRY(b->mem.ensure(work));
+    CSWGS_CUDA_TRY(cudaMallocHost(&b->staging, std::max<size_t>(in, 256)));
+
+    char *base = b->mem.as<char>();
+    char *stg = static_cast<char *>(b->staging);
+    b->holos.resize(count);
+    b->own_phase.assign(count, nullptr);
+    for (int h = 0; h < count; ++h) {
+        const HoloSpec &s = b->specs[h];
+        HoloDev &H = b->holos[h];
+        std::memset(&H, 0, sizeof H);
+        H.P = s.P;
+        H.N = s.N;
+        H.Mp = s.Mp;
+        H.seed = s.seed;
+        size_t o = b->in_off[h];
+        H.xyz = reinterpret_cast<const double *>(base + o);
+        std::memcpy(stg + o, s.xyz.data(), sizeof(double) * 3 * s.N);
+        o += align256(sizeof(double) * 3 * s.N);
+        if (s.has_amp) {
+            H.amp = reinterpret_cast<const double *>(base + o);
+            std::memcpy(stg + o, s.amp.data(), sizeof(double) * s.N);
+            o += align256(sizeof(double) * s.N);
+        }
+        if (s.has_init_w) {
+            H.init_w = reinterpret_cast<const double *>(base + o);
+            std::memcpy(stg + o, s.init_w.data(), sizeof(double) * s.N);
+            o += align256(sizeof(double) * s.N);
+        }
+        if (s.has_init_th) {
+            H.init_th = reinterpret_cast<const double *>(base + o);
+            std::memcpy(stg + o, s.init_th.data(), sizeof(double) * s.N);
+            o += align256(sizeof(double) * s.N);
+        }
+        const int M = s.P * s.P;
+        const int tiles_it = (std::max(s.Mp, s.iterations > 0 && s.n_full > 0 ? M : 0) + tp - 1) / tp;
+        const int tiles_full = (M + tp - 1) / tp;
+        size_t w = w_off[h];
+        H.coef = reinterpret_cast<int4 *>(base + w);
+        w += align256(sizeof(int4) * s.N);
+        H.state = reinterpret_cast<SpotState *>(base + w);
+        w += align256(sizeof(SpotState) * s.N);
+        H.part = reinterpret_cast<float2 *>(base + w);
+        w += align256(sizeof(float2) * (size_t)tiles_it * s.N);
+        H.part64 = reinterpret_cast<double2 *>(base + w);
+        w += align256(sizeof(double2) * (size_t)(s.final_pass ? tiles_full : 1) * s.N);
+        H.counter = reinterpret_cast<unsigned *>(base + w);
+        w += 256;
+        H.metrics = reinterpret_cast<double *>(base + w);
+        w += align256(sizeof(double) * (2 + s.N));
+        if (host_out) {
+            b->own_phase[h] = reinterpret_cast<float *>(base + w);
+            w += align256(sizeof(float) * (size_t)M);
+        }
+        H.phase_out = b->own_phase[h];
+    }
+
+    // launch schedule: launch L advances every hologram that still has work
+    int L_max = 0;
+    for (auto &s : b->specs) L_max = std::max(L_max, schedule_launches(s));
+    // heavier tiles first: order holograms by N (tile cost) descending
+    std::vector<int> order(count);
+    for (int h = 0; h < count; ++h) order[h] = h;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return b->specs[a].N > b->specs[c].N; });
+    std::vector<LaunchSlot> slots;
+    double pairs_total = 0.0, pairs_iter = 0.0;
+    for (int L = 0; L < L_max; ++L) {
+        int first = (int)slots.size(), tiles = 0, mN = 0;
+        for (int h : order) {
+            const HoloSpec &s = b->specs[h];
+            int pass = pass_of(s, L);
+            if (pass < 0) continue;
+            LaunchSlot sl;
+            sl.holo = h;
+            sl.pass = pass;
+            sl.j = s.first_j + L;
+            sl.count = pass_count(s, pass);
+            sl.tiles = (sl.count + tp - 1) / tp;
+            sl.tile_begin = tiles;
+            tiles += sl.tiles;
+            mN = std::max(mN, s.N);
+            slots.push_back(sl);
+            double pr = 2.0 * (double)s.N * (double)sl.count;
+            pairs_total += pr;
+            if (pass != kPassFinal) pairs_iter += pr;
+        }
+        b->l_slot0.push_back(first);
+        b->l_nslots.push_back((int)slots.size() - first);
+        b->l_tiles.push_back(tiles);
+        b->l_maxN.push_back(mN);
+    }
+    b->pairs_total = pairs_total;
+    b->pairs_iter = pairs_iter;
+    CSWGS_TRY(b->holos_d.ensure(sizeof(HoloDev) * count));
+    CSWGS_TRY(b->slots_d.ensure(sizeof(LaunchSlot) * std::max<size_t>(1, slots.size())));
+    CSWGS_TRY(b->queue_d.ensure(256));
+    CSWGS_CUDA_TRY(cudaMemcpy(b->holos_d.p, b->holos.data(), sizeof(HoloDev) * count, cudaMemcpyHostToDevice));
+    if (!slots.empty())
+        CSWGS_CUDA_TRY(cudaMemcpy(b->slots_d.p, slots.data(), sizeof(LaunchSlot) * slots.size(),
+                                  cudaMemcpyHostToDevice));
+    CSWGS_CUDA_TRY(cudaMemset(b->queue_d.p, 0, 256));
+    CSWGS_CUDA_TRY(cudaMemset(b->mem.p, 0, work));
+    b->grid = iter_fp32_max_grid(shape, b->maxN, p->sm_count);
+    if (b->grid <= 0) return set_error(CSWGS_ECUDA, "tile shape %dx%d cannot be resident with N=%d",
+                                       shape.threads, shape.ppt, b->maxN);
+    if (timing) {
+        b->events.resize(L_max + 2);
+        for (auto &e : b->events) CSWGS_CUDA_TRY(cudaEventCreate(&e));
+    }
+    *out = std::move(b);
+    return CSWGS_OK;
+}
+
+cswgs_status batch_build(cswgs_plan_s *p, std::vector<HoloSpec> specs, bool timing,
+                         std::unique_ptr<Fp32Batch> *out)
+{
+    TileShape shape = tuned_shape(p, specs);
+    return batch_build_shape(p, std::move(specs), shape, timing, false, out);
+}
+
+cswgs_status batch_build_host(cswgs_plan_s *p, std::vector<HoloSpec> specs, bool timing,
+                              bool host_out, std::unique_ptr<Fp32Batch> *out)
+{
+    TileShape shape = tuned_shape(p, specs);
+    return batch_build_shape(p, std::move(specs), shape, timing, host_out, out);
+}
+
+cswgs_status batch_build_with(cswgs_plan_s *p, std::vector<HoloSpec> specs, TileShape shape,
+                              std::unique_ptr<Fp32Batch> *out)
+{
+    return batch_build_shape(p, std::move(specs), shape, true, false, out);
+}
+
+// Re-stages the inputs of hologram h from its spec (after the spec changed).
+void batch_restage(Fp32Batch *b, int h)
+{
+    const HoloSpec &s = b->specs[h];
+    char *stg = static_cast<char *>(b->staging);
+    size_t o = b->in_off[h];
+    std::memcpy(stg + o, s.xyz.data(), sizeof(double) * 3 * s.N);
+    o += align256(sizeof(double) * 3 * s.N);
+    if (s.has_amp) {
+        std::memcpy(stg + o, s.amp.data(), sizeof(double) * s.N);
+        o += align256(sizeof(double) * s.N);
+    }
+    if (s.has_init_w) {
+        std::memcpy(stg + o, s.init_w.data(), sizeof(double) * s.N);
+        o += align256(sizeof(double) * s.N);
+    }
+    if (s.has_init_th) {
+        std::memcpy(stg + o, s.init_th.data(), sizeof(double) * s.N);
+        o += align256(sizeof(double) * s.N);
+    }
+}
+
+cswgs_status batch_upload_inputs(Fp32Batch *b, cudaStream_t s)
+{
+    if (b->in_bytes)
+        CSWGS_CUDA_TRY(cudaMemcpyAsync(b->mem.p, b->staging, b->in_bytes, cudaMemcpyHostToDevice, s));
+    return CSWGS_OK;
+}
+
+cswgs_status batch_set_outputs(Fp32Batch *b, const std::vector<float *> &dev_phase, cudaStream_t s)
+{
+    bool changed = false;
+    for (size_t h = 0; h < b->holos.size(); ++h) {
+        float *want = h < dev_phase.size() && dev_phase[h] ? dev_phase[h] : b->own_phase[h];
+        if (b->holos[h].phase_out != want) {
+            b->holos[h].phase_out = want;
+            changed = true;
+        }
+    }
+    if (changed)
+        CSWGS_CUDA_TRY(cudaMemcpyAsync(b->holos_d.p, b->holos.data(), sizeof(HoloDev) * b->holos.size(),
+                                       cudaMemcpyHostToDevice, s));
+    return CSWGS_OK;
+}
+
+cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s)
+{
+    const HoloDev *holos = b->holos_d.as<HoloDev>();
+    const LaunchSlot *slots = b->slots_d.as<LaunchSlot>();
+    unsigned *queue = b->queue_d.as<unsigned>();
+    const int count = (int)b->holos.size();
+    CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s));
+    if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, cudaEventRecordExternal));
+    CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
+    for (size_t L = 0; L < b->l_tiles.size(); ++L) {
+        if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[L + 1], s, cudaEventRecordExternal));
+        const int tiles = b->l_tiles[L];
+        if (tiles == 0) continue;
+        const int grid = std::min(b->grid, tiles);
+        CSWGS_CUDA_TRY(launch_iter_fp32(b->shape, holos, slots + b->l_slot0[L], b->l_nslots[L], tiles,
+                                        b->l_maxN[L], queue, grid, s));
+    }
+    if (b->timing)
+        CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[b->l_tiles.size() + 1], s, cudaEventRecordExternal));
+    return CSWGS_OK;
+}
+
+cswgs_status batch_enqueue(Fp32Batch *b, cudaStream_t s)
+{
+    if (!b->exec) {
+        cudaStream_t cap;
+        CSWGS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            CSWGS_CUDA_TRY(e);
+        }
+        cswgs_status st = batch_enqueue_direct(b, cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (st != CSWGS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        CSWGS_CUDA_TRY(e);
+        b->graph = g;
+        CSWGS_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    }
+    CSWGS_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    return CSWGS_OK;
+}
+
+}  // namespace cswgs

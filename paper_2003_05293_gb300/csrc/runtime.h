@@ -1,0 +1,150 @@
+// Host runtime of the CS-WGS library: plans, device buffers, FP32 batches
+// (launch schedule + CUDA graph), the autotuner and the serving loop.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdarg>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "cswgs_internal.h"
+
+namespace cswgs {
+
+cswgs_status set_error(cswgs_status s, const char *fmt, ...);
+
+#define CSWGS_CUDA_TRY(expr)                                                               \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::cswgs::set_error(e_ == cudaErrorMemoryAllocation ? CSWGS_ENOMEM       \
+                                                                      : CSWGS_ECUDA,       \
+                                      "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),     \
+                                      __FILE__, __LINE__);                                 \
+    } while (0)
+
+#define CSWGS_TRY(expr)                              \
+    do {                                             \
+        cswgs_status s_ = (expr);                    \
+        if (s_ != CSWGS_OK) return s_;               \
+    } while (0)
+
+// Owning device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cswgs_status ensure(size_t n)
+    {
+        if (n <= bytes && p) return CSWGS_OK;
+        release();
+        if (n == 0) n = 256;
+        CSWGS_CUDA_TRY(cudaMalloc(&p, n));
+        bytes = n;
+        return CSWGS_OK;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// One hologram as the runtime sees it (validated copy of a request).
+struct HoloSpec {
+    int P = 0, N = 0, Mp = 0;
+    int iterations = 0, n_full = 2, first_j = 1, final_pass = 1;
+    uint64_t seed = 0;
+    bool has_amp = false, has_init_w = false, has_init_th = false;
+    std::vector<double> xyz, amp, init_w, init_th;
+};
+
+cswgs_status validate_request(const cswgs_plan_desc &d, const double *xyz, const double *amp, int N,
+                              int P, double c, int iterations, int n_full, HoloSpec *out);
+
+// Number of launches of the FP32 schedule: one per iteration plus the final pass.
+int schedule_launches(const HoloSpec &h);
+int pass_of(const HoloSpec &h, int L);   // PassKind of launch L, or -1
+
+// An FP32 batch ready to run: device buffers for every hologram, the launch
+// schedule (one persistent launch per iteration), and a CUDA graph of it.
+struct Fp32Batch {
+    cswgs_plan_s *plan = nullptr;
+    std::vector<HoloSpec> specs;
+    std::vector<HoloDev> holos;           // host mirror of holos_d
+    std::vector<size_t> in_off;           // per hologram: offset of its inputs in the staging block
+    size_t in_bytes = 0;                  // size of the input block (device + pinned staging)
+    DevBuf mem;                           // all per-hologram buffers
+    DevBuf holos_d, slots_d, queue_d;
+    void *staging = nullptr;              // pinned host copy of the inputs
+    std::vector<float *> own_phase;       // internal phase buffers (host outputs), per hologram
+    std::vector<int> l_slot0, l_nslots, l_tiles, l_maxN;
+    TileShape shape{256, 4};
+    int grid = 0;
+    int maxN = 0;
+    bool timing = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> events;      // launch boundaries (timing)
+    double pairs_total = 0.0, pairs_iter = 0.0;
+    ~Fp32Batch();
+};
+
+cswgs_status batch_build(cswgs_plan_s *p, std::vector<HoloSpec> specs, bool timing,
+                         std::unique_ptr<Fp32Batch> *out);
+cswgs_status batch_upload_inputs(Fp32Batch *b, cudaStream_t s);
+cswgs_status batch_set_outputs(Fp32Batch *b, const std::vector<float *> &dev_phase, cudaStream_t s);
+cswgs_status batch_enqueue(Fp32Batch *b, cudaStream_t s);   // graph launch (captures on first use)
+cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s);
+
+class Server;
+
+}  // namespace cswgs
+
+struct cswgs_plan_s {
+    cswgs_plan_desc desc{};
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::mutex mu;
+    std::map<std::string, std::unique_ptr<cswgs::Fp32Batch>> solve_cache;
+    std::map<std::string, cswgs::TileShape> tune;
+    std::string tune_path;
+    // FP64 solver workspace
+    cswgs::DevBuf f64_mem;
+    // small device scratch for results
+    cswgs::DevBuf scratch;
+    std::unique_ptr<cswgs::Server> server;
+};
+
+struct cswgs_batch_s {
+    cswgs_plan_s *plan = nullptr;
+    std::unique_ptr<cswgs::Fp32Batch> b;
+    int count = 0;
+    float last_ms = 0.f;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+};
+
+namespace cswgs {
+// autotuner
+TileShape tuned_shape(cswgs_plan_s *p, const std::vector<HoloSpec> &specs);
+cswgs_status tune_batch(cswgs_plan_s *p, Fp32Batch *b, double *best_ms);
+std::string tune_key(const std::vector<HoloSpec> &specs);
+void tune_load(cswgs_plan_s *p);
+void tune_save(cswgs_plan_s *p);
+}  // namespace cswgs

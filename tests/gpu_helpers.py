@@ -1,0 +1,35 @@
+"""Shared helpers of the GPU parity tests."""
+import math
+
+import numpy as np
+
+# Tolerances of the FP32 path against the FP64 oracle: RMS wrapped phase error
+# per iteration and on the final map (radians), and absolute e / u error.
+TOL_PHASE_RMS = 1e-3
+TOL_EU = 1e-3
+# The FP64 GPU baseline computes the same sums as the oracle in another order.
+TOL_FP64_PHASE = 1e-9
+TOL_FP64_EU = 1e-11
+
+
+def wrap(d):
+    return (np.asarray(d, dtype=np.float64) + np.pi) % (2 * np.pi) - np.pi
+
+
+def rms_wrapped(a, b):
+    d = wrap(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64))
+    return float(math.sqrt(np.mean(d * d)))
+
+
+def oracle_states(oracle, pb, iterations, full_iterations=2):
+    """(w, theta) at the start of every iteration j = 1..iterations+1, from the oracle."""
+    w = np.ones(pb.N)
+    th = oracle.theta0(pb.N, pb.seed)
+    states = [(w, th)]
+    for j in range(1, iterations + 1):
+        full = 1 if j > iterations - full_iterations else 0
+        r = oracle.solve(pb.P, pb.xyz, pb.amp, c=pb.c, iterations=1, seed=pb.seed, theta_in=th, w_in=w,
+                         first_j=j, final_pass=False, full_iterations=full)
+        w, th = r["w"], r["theta"]
+        states.append((w, th))
+    return states

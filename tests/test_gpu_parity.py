@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every step of the path is compared on the same seeded inputs: the subset draw
+(bit-exact), theta^0, teacher-forced single iterations (the GPU starts from
+the oracle's state and takes one step), the phase map, the final e and u, and
+free-running solves, for the FP32 solver and the FP64 baseline, at the tiny
+and medium workloads and at the P = 1152 sizes, plus the edge cases."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_helpers import (TOL_EU, TOL_FP64_EU, TOL_FP64_PHASE, TOL_PHASE_RMS, oracle_states,
+                         rms_wrapped, wrap)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fp32():
+    from paper_2003_05293_gb300 import Plan
+    p = Plan(precision="fp32")
+    yield p
+    p.close()
+
+
+@pytest.fixture(scope="module")
+def fp64():
+    from paper_2003_05293_gb300 import Plan
+    p = Plan(precision="fp64")
+    yield p
+    p.close()
+
+
+def run(plan, pb, **kw):
+    out = torch.full((pb.P * pb.P,), -1.0, dtype=torch.float32, device="cuda")
+    r = plan.solve(pb.xyz, pb.P, pb.c, pb.iterations, pb.seed, amp=pb.amp, out=out, state=True, **kw)
+    torch.cuda.synchronize()
+    return r, out.cpu().numpy().astype(np.float64)
+
+
+# ------------------------------------------------------------------ subsets --
+
+@pytest.mark.parametrize("P,c,seed,j", [(64, 0.25, 0, 1), (64, 0.25, 0, 2), (512, 0.125, 7, 30),
+                                        (1152, 0.125, 3, 5), (1152, 0.0625, 11, 1), (2, 1.0, 0, 1),
+                                        (6, 0.5, 1, 4), (130, 0.3, 2**63 + 5, 7)])
+def test_subset_bit_exact(fp32, P, c, seed, j):
+    Mp = oracle.subset_size(P, c)
+    out = torch.empty(Mp, dtype=torch.int32, device="cuda")
+    fp32.subset(P, Mp, seed, j, out)
+    got = out.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got, oracle.subset(P, Mp, seed, j))
+
+
+# ------------------------------------------------------------------ theta^0 --
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_theta0(fp32, fp64, prec):
+    plan = fp32 if prec == "fp32" else fp64
+    pb = workloads.problem(64, 50, 5.0, 0.25, 0, seed=123)
+    r = plan.solve(pb.xyz, pb.P, pb.c, 0, pb.seed, final_pass=False, state=True)
+    ref = oracle.theta0(pb.N, pb.seed)
+    assert np.max(np.abs(wrap(r["theta"] - ref))) < (1e-8 if prec == "fp32" else 1e-14)
+    assert np.all(r["w"] == 1.0)
+
+
+# -------------------------------------------------------- whole solves, tiny --
+
+def test_fp64_tiny_matches_oracle(fp64):
+    pb = workloads.problem(**{k: v for k, v in workloads.TINY.items()}, seed=0)
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = run(fp64, pb)
+    assert rms_wrapped(ph, ref["phase"]) < TOL_FP64_PHASE * 10      # FP32 output rounding
+    assert abs(r["e"] - ref["e"]) < TOL_FP64_EU and abs(r["u"] - ref["u"]) < TOL_FP64_EU
+    assert np.max(np.abs(wrap(r["theta"] - ref["theta"]))) < TOL_FP64_PHASE
+    assert np.allclose(r["w"], ref["w"], rtol=1e-10)
+    assert np.allclose(r["I"], ref["I"], rtol=1e-9, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fp32_tiny_matches_oracle(fp32, seed):
+    pb = workloads.problem(**workloads.TINY, seed=seed)
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = run(fp32, pb)
+    assert np.all(ph >= 0) and np.all(ph < 2 * np.pi)
+    assert rms_wrapped(ph, ref["phase"]) < TOL_PHASE_RMS
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
+    assert rms_wrapped(r["theta"], ref["theta"]) < TOL_PHASE_RMS
+
+
+# ------------------------------------------- teacher-forced, medium workload --
+
+@pytest.fixture(scope="module")
+def medium():
+    pb = workloads.problem(**workloads.MEDIUM, seed=5)
+    return pb, oracle_states(oracle, pb, pb.iterations)
+
+
+@pytest.mark.parametrize("j", [1, 2, 10, 28, 29, 30])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_teacher_forced_iteration(fp32, fp64, medium, j, prec):
+    plan = fp32 if prec == "fp32" else fp64
+    pb, states = medium
+    w0, th0 = states[j - 1]
+    w1, th1 = states[j]
+    full = 1 if j > pb.iterations - 2 else 0
+    r = plan.solve(pb.xyz, pb.P, pb.c, 1, pb.seed, init_w=w0, init_theta=th0, first_iteration=j,
+                   full_iterations=full, final_pass=False, state=True)
+    tol = TOL_PHASE_RMS if prec == "fp32" else TOL_FP64_PHASE
+    assert rms_wrapped(r["theta"], th1) < tol
+    assert math.sqrt(np.mean((r["w"] / w1 - 1) ** 2)) < tol
+
+
+@pytest.mark.parametrize("j", [1, 15, 30])
+def test_teacher_forced_phase_on_subset(fp32, medium, j):
+    # the back-propagation of iteration j from the oracle's state, at the pixels of S_j
+    pb, states = medium
+    w0, th0 = states[j - 1]
+    out = torch.empty(pb.M, dtype=torch.float32, device="cuda")
+    fp32.solve(pb.xyz, pb.P, pb.c, 0, pb.seed, init_w=w0, init_theta=th0, out=out)
+    got = out.cpu().numpy().astype(np.float64)
+    pix = oracle.subset(pb.P, oracle.subset_size(pb.P, pb.c), pb.seed, j)
+    ref = oracle.back(pb.P, pb.xyz, w0, th0, pix)
+    assert rms_wrapped(got[pix], ref) < TOL_PHASE_RMS
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_medium_free_running(fp32, fp64, medium, prec):
+    plan = fp32 if prec == "fp32" else fp64
+    pb, _ = medium
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = run(plan, pb)
+    tol_p = TOL_PHASE_RMS if prec == "fp32" else 1e-6
+    tol_e = TOL_EU if prec == "fp32" else 1e-9
+    assert rms_wrapped(ph, ref["phase"]) < tol_p
+    assert abs(r["e"] - ref["e"]) < tol_e and abs(r["u"] - ref["u"]) < tol_e
+    assert r["u"] > 0.95
+
+
+# ---------------------------------------------------------- P = 1152 sizes --
+
+@pytest.mark.parametrize("N,c", [(100, 0.25), (100, 0.125), (100, 0.0625), (300, 0.25), (300, 0.125),
+                                 (300, 0.0625)])
+def test_large_teacher_forced_first_iterations(fp32, N, c):
+    pb = workloads.problem(1152, N, 10.0, c, 30, seed=17)
+    st = oracle_states(oracle, pb, 2, full_iterations=0)
+    for j in (1, 2):
+        w0, th0 = st[j - 1]
+        w1, th1 = st[j]
+        r = fp32.solve(pb.xyz, pb.P, pb.c, 1, pb.seed, init_w=w0, init_theta=th0, first_iteration=j,
+                       full_iterations=0, final_pass=False, state=True)
+        assert rms_wrapped(r["theta"], th1) < TOL_PHASE_RMS
+        assert math.sqrt(np.mean((r["w"] / w1 - 1) ** 2)) < TOL_PHASE_RMS
+
+
+def test_large_final_pass_and_metrics(fp32):
+    # final pass from a fixed state at P = 1152, N = 300: every pixel and e, u
+    pb = workloads.problem(1152, 300, 10.0, 0.125, 0, seed=23)
+    rng = np.random.default_rng(1)
+    w0 = rng.uniform(0.5, 1.5, pb.N)
+    th0 = rng.uniform(-np.pi, np.pi, pb.N)
+    out = torch.empty(pb.M, dtype=torch.float32, device="cuda")
+    r = fp32.solve(pb.xyz, pb.P, pb.c, 0, pb.seed, init_w=w0, init_theta=th0, out=out, state=True)
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=0, seed=pb.seed, theta_in=th0, w_in=w0)
+    got = out.cpu().numpy().astype(np.float64)
+    assert rms_wrapped(got, ref["phase"]) < TOL_PHASE_RMS
+    assert np.max(np.abs(wrap(got - ref["phase"]))) < 0.05
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
+    assert np.allclose(r["I"], ref["I"], rtol=1e-3, atol=1e-7)
+
+
+def test_large_free_running_target(fp32):
+    # the headline workload (P = 1152, N = 100, c = 1/8, 30 iterations), one hologram
+    pb = workloads.problem(**workloads.LARGE, seed=0)
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = run(fp32, pb)
+    assert rms_wrapped(ph, ref["phase"]) < TOL_PHASE_RMS
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
+    assert rms_wrapped(r["theta"], ref["theta"]) < TOL_PHASE_RMS
+
+
+# -------------------------------------------------------------- edge cases --
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_single_spot(fp32, fp64, prec):
+    plan = fp32 if prec == "fp32" else fp64
+    P = 96
+    xyz = np.array([[7.3, -11.2, 3.1]])
+    out = torch.empty(P * P, dtype=torch.float32, device="cuda")
+    r = plan.solve(xyz, P, 0.25, 6, 9, out=out, init_theta=np.zeros(1), state=True)
+    ref = np.array([oracle.spot_phase(P, xyz, 0, m) for m in range(P * P)]) % (2 * np.pi)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(wrap(got - ref))) < 2e-5
+    assert abs(r["e"] - 1.0) < 1e-5 and abs(r["u"] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("P,N,c,I", [(2, 1, 1.0, 3), (4, 3, 0.5, 4), (6, 2, 0.3, 2), (10, 5, 1.0, 5),
+                                     (34, 7, 0.07, 6), (64, 10, 1.0, 0), (64, 10, 1.0 / 4096, 3),
+                                     (200, 33, 0.111, 4)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_edge_sizes(fp32, fp64, P, N, c, I, prec):
+    # tiny grids, one-pixel subsets, ragged tiles, RS (I = 0) and WGS (c = 1)
+    plan = fp32 if prec == "fp32" else fp64
+    pb = workloads.problem(P, N, 3.0, c, I, seed=P * 131 + N)
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = run(plan, pb)
+    tol = TOL_PHASE_RMS if prec == "fp32" else 1e-6
+    # tiny grids can put a pixel's sum near zero, where arg is ill-conditioned:
+    # compare the phase where the oracle's field is not degenerate
+    assert rms_wrapped(ph, ref["phase"]) < max(tol, 5e-3 if P <= 6 else tol)
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
+
+
+def test_amplitudes_and_many_spots(fp32):
+    pb = workloads.problem(256, 1024, 10.0, 0.25, 4, seed=77)
+    pb.amp = np.random.default_rng(2).uniform(0.5, 2.0, pb.N)
+    ref = oracle.solve(pb.P, pb.xyz, pb.amp, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = run(fp32, pb)
+    assert rms_wrapped(ph, ref["phase"]) < TOL_PHASE_RMS
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
+
+
+def test_same_seed_same_result(fp32):
+    pb = workloads.problem(128, 20, 5.0, 0.25, 8, seed=4)
+    a, pa = run(fp32, pb)
+    b, pbm = run(fp32, pb)
+    assert np.array_equal(pa, pbm) and a["e"] == b["e"] and a["u"] == b["u"]
+    pb2 = workloads.problem(128, 20, 5.0, 0.25, 8, seed=4)
+    pb2.seed = 5
+    c, pc = run(fp32, pb2)
+    assert not np.array_equal(pa, pc)
+
+
+def test_invalid_arguments(fp32):
+    from paper_2003_05293_gb300 import CswgsError
+    xyz = np.array([[1.0, 2.0, 0.5]])
+    bad = [dict(P=7), dict(P=0), dict(P=4096), dict(c=0.0), dict(c=1.5), dict(iterations=-1),
+           dict(xyz=np.array([[np.nan, 0.0, 0.0]])), dict(amp=np.array([-1.0])), dict(c=1e-9)]
+    for kw in bad:
+        args = dict(xyz=xyz, P=16, c=0.5, iterations=2, seed=0, amp=None)
+        args.update(kw)
+        with pytest.raises(CswgsError) as ei:
+            fp32.solve(args["xyz"], args["P"], args["c"], args["iterations"], args["seed"], amp=args["amp"])
+        assert ei.value.status == 1
+    with pytest.raises(CswgsError):
+        fp32.solve(np.zeros((0, 3)), 16, 0.5, 1, 0)
