@@ -185,6 +185,7 @@ def main():
     outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
     batch = plan.batch(pbs, outs)
     total_pairs, iter_pairs = batch.pairs()
+    tile = batch.tile_shape()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
     for _ in range(args.warmup):
@@ -245,7 +246,8 @@ def main():
                          "kernel": "iter_kernel (all %d persistent launches of a step)" % iter_n_per_step(iter_n, args),
                          "peak_basis": "%d SMs x %d/clk x %.0f MHz" % (sm_count, SFU_PER_CLK_PER_SM, max_mhz),
                          "probe_measured": probe / 1e9, "probe_sm_mhz": probe_mhz,
-                         "algorithmic_pairs_per_step": total_pairs},
+                         "algorithmic_pairs_per_step": total_pairs,
+                         "tile": {"threads": tile[0], "pixels_per_thread": tile[1], "blocks": tile[2]}},
             "gpu_launches": args.steps * (1 + iter_n_per_step(iter_n, args)),
             "clocks": clk}
 

@@ -187,6 +187,10 @@ cswgs_status cswgs_batch_kernel_times(cswgs_batch b, float *ms, int cap, int *co
  * N * (2 * (I - F) * Mp + 2 * F * M + 2 * M), F = min(full_iterations, I). */
 cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs_iter_launches);
 
+/* Launch shape of the batch's iteration kernel, as chosen by the autotuner:
+ * threads per block, pixels per thread, and persistent blocks per launch. */
+cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *blocks);
+
 cswgs_status cswgs_batch_destroy(cswgs_batch b);
 
 /* Runs `count` requests (host or device outputs) as one batch, synchronous:

@@ -46,8 +46,12 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        build()
-        lib = ctypes.CDLL(_LIB)
+        # CSWGS_ORACLE_LIB: a deliberately broken build of this file, loaded by
+        # the mutation tests to show that the pins catch each planted mistake
+        path = os.environ.get("CSWGS_ORACLE_LIB")
+        if not path:
+            path = build()
+        lib = ctypes.CDLL(path)
         d = ctypes.POINTER(ctypes.c_double)
         i64 = ctypes.POINTER(ctypes.c_int64)
         u64 = ctypes.c_uint64

@@ -253,6 +253,12 @@ class Batch:
         check(self.lib.cswgs_batch_pairs(self.handle, ctypes.byref(a), ctypes.byref(b)), "cswgs_batch_pairs")
         return a.value, b.value
 
+    def tile_shape(self):
+        t, k, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self.lib.cswgs_batch_tile_shape(self.handle, ctypes.byref(t), ctypes.byref(k), ctypes.byref(g)),
+              "cswgs_batch_tile_shape")
+        return t.value, k.value, g.value
+
     def close(self):
         if self.handle:
             self.lib.cswgs_batch_destroy(self.handle)

@@ -424,6 +424,15 @@ cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs
     return CSWGS_OK;
 }
 
+cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *blocks)
+{
+    if (!b) return set_error(CSWGS_EINVAL, "NULL batch");
+    if (threads) *threads = b->b->shape.threads;
+    if (pixels_per_thread) *pixels_per_thread = b->b->shape.ppt;
+    if (blocks) *blocks = b->b->grid;
+    return CSWGS_OK;
+}
+
 cswgs_status cswgs_batch_destroy(cswgs_batch b)
 {
     if (!b) return CSWGS_OK;
@@ -537,7 +546,7 @@ cswgs_status cswgs_sincos_peak(cswgs_plan p, double *sincos_per_s, double *sm_mh
     std::lock_guard<std::mutex> lk(p->mu);
     CSWGS_TRY(set_device(p));
     const int threads = 256, iters = 4096;
-    const int blocks = p->sm_count * 8;
+    const int blocks = p->sm_count * 4;   // one resident wave
     CSWGS_TRY(p->scratch.ensure(4096));
     float *sink = p->scratch.as<float>();
     long long *cyc = reinterpret_cast<long long *>(p->scratch.as<char>() + 256);
@@ -545,6 +554,7 @@ cswgs_status cswgs_sincos_peak(cswgs_plan p, double *sincos_per_s, double *sm_mh
     CSWGS_CUDA_TRY(cudaEventCreate(&a));
     CSWGS_CUDA_TRY(cudaEventCreate(&c));
     CSWGS_CUDA_TRY(launch_sincos_probe(sink, cyc, iters, blocks, threads, p->stream));  // warm-up
+    CSWGS_CUDA_TRY(cudaMemsetAsync(cyc, 0, sizeof(long long), p->stream));
     CSWGS_CUDA_TRY(cudaEventRecord(a, p->stream));
     CSWGS_CUDA_TRY(launch_sincos_probe(sink, cyc, iters, blocks, threads, p->stream));
     CSWGS_CUDA_TRY(cudaEventRecord(c, p->stream));

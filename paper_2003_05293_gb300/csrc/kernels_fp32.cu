@@ -344,7 +344,8 @@ __global__ void sincos_probe_kernel(float *sink, long long *cycles, int iters)
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc += a[q];
     if (acc == 12345.678f) sink[0] = acc;   // keeps the chains alive
-    if (threadIdx.x == 0 && blockIdx.x == 0) cycles[0] = t1 - t0;
+    if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned long long *>(cycles),
+                                    (unsigned long long)(t1 - t0));
 }
 
 // ------------------------------------------------------------- launchers --
@@ -398,6 +399,7 @@ static cudaError_t launch_impl(const HoloDev *holos, const LaunchSlot *slots, in
 {
     // the smem attribute is set by iter_fp32_max_grid, which every batch calls first
     size_t smem = iter_fp32_smem(TileShape{T, K}, maxN);
+    (void)cudaGetLastError();   // report this launch, not an earlier call's error
     iter_kernel<T, K><<<grid, T, smem, s>>>(holos, slots, nslots, total_tiles, maxN, queue);
     return cudaGetLastError();
 }
@@ -415,6 +417,7 @@ cudaError_t launch_iter_fp32(TileShape shape, const HoloDev *holos, const Launch
 cudaError_t launch_prep_fp32(const HoloDev *holos, int count, int maxN, cudaStream_t s)
 {
     dim3 grid((unsigned)((maxN + 127) / 128), (unsigned)count);
+    (void)cudaGetLastError();
     prep_kernel<<<grid, 128, 0, s>>>(holos);
     return cudaGetLastError();
 }
@@ -424,6 +427,7 @@ cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_
     int64_t blocks = (Mp + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     if (blocks < 1) blocks = 1;
+    (void)cudaGetLastError();
     subset_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, Mp, seed, j, out);
     return cudaGetLastError();
 }
@@ -431,6 +435,7 @@ cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_
 cudaError_t launch_sincos_probe(float *sink, long long *cycles, int iters, int blocks, int threads,
                                 cudaStream_t s)
 {
+    (void)cudaGetLastError();
     sincos_probe_kernel<<<blocks, threads, 0, s>>>(sink, cycles, iters);
     return cudaGetLastError();
 }

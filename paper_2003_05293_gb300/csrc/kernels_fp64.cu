@@ -164,6 +164,7 @@ cudaError_t fp64_solve(const Fp64Work &wk, int P, int N, int Mp, int iterations,
                        int first_j, uint64_t seed, int final_pass, float *phase_out, cudaStream_t s)
 {
     const int64_t M = (int64_t)P * P;
+    (void)cudaGetLastError();   // report these launches, not an earlier call's error
     fp64_prep<<<blocks_for(N, 128), 128, 0, s>>>(wk.xyz, wk.init_w, wk.init_th, N, P, seed, wk.coef,
                                                  wk.w, wk.theta);
     for (int it = 0; it < iterations; ++it) {

@@ -309,17 +309,19 @@ cswgs_status batch_set_outputs(Fp32Batch *b, const std::vector<float *> &dev_pha
     return CSWGS_OK;
 }
 
-cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s)
+cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
 {
+    // inside a stream capture the timing events become event-record nodes
+    const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     const HoloDev *holos = b->holos_d.as<HoloDev>();
     const LaunchSlot *slots = b->slots_d.as<LaunchSlot>();
     unsigned *queue = b->queue_d.as<unsigned>();
     const int count = (int)b->holos.size();
     CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s));
-    if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, cudaEventRecordExternal));
+    if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, evflag));
     CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
     for (size_t L = 0; L < b->l_tiles.size(); ++L) {
-        if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[L + 1], s, cudaEventRecordExternal));
+        if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[L + 1], s, evflag));
         const int tiles = b->l_tiles[L];
         if (tiles == 0) continue;
         const int grid = std::min(b->grid, tiles);
@@ -327,7 +329,7 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s)
                                         b->l_maxN[L], queue, grid, s));
     }
     if (b->timing)
-        CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[b->l_tiles.size() + 1], s, cudaEventRecordExternal));
+        CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[b->l_tiles.size() + 1], s, evflag));
     return CSWGS_OK;
 }
 
@@ -341,7 +343,7 @@ cswgs_status batch_enqueue(Fp32Batch *b, cudaStream_t s)
             cudaStreamDestroy(cap);
             CSWGS_CUDA_TRY(e);
         }
-        cswgs_status st = batch_enqueue_direct(b, cap);
+        cswgs_status st = batch_enqueue_direct(b, cap, true);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);

@@ -109,7 +109,7 @@ cswgs_status batch_build(cswgs_plan_s *p, std::vector<HoloSpec> specs, bool timi
 cswgs_status batch_upload_inputs(Fp32Batch *b, cudaStream_t s);
 cswgs_status batch_set_outputs(Fp32Batch *b, const std::vector<float *> &dev_phase, cudaStream_t s);
 cswgs_status batch_enqueue(Fp32Batch *b, cudaStream_t s);   // graph launch (captures on first use)
-cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s);
+cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing = false);
 
 class Server;
 

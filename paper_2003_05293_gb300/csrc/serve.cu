@@ -303,33 +303,70 @@ void Server::loop()
             active_[slot] = std::move(r);
         }
         int nactive = 0;
-        for (auto &a : active_) nactive += a && !a->cancelled;
+        bool has_work = false;
+        for (auto &a : active_) {
+            if (!a || a->cancelled) continue;
+            ++nactive;
+            has_work |= pass_of(a->spec, a->L) >= 0;
+        }
         st_.active = nactive;
         st_.queued = (int)queue_.size();
         st_.bytes_in_use = arena_.in_use();
-        if (nactive == 0) {
+
+        // results of every launch up to completed_serial_
+        auto complete = [&]() {
+            for (int s = 0; s < B; ++s) {
+                Req *r = active_[s].get();
+                if (!r || !r->finishing || r->last_launch > completed_serial_) continue;
+                const double *m = met_h_ + (size_t)(r->last_launch & 1) * 2 * B + 2 * s;
+                r->met.assign(m, m + 2);
+                cswgs_status st = CSWGS_OK;
+                if (r->phase_host) {
+                    cudaError_t e = cudaMemcpy(r->phase_host, r->dev.phase_out,
+                                               sizeof(float) * (size_t)r->spec.P * r->spec.P,
+                                               cudaMemcpyDeviceToHost);
+                    if (e != cudaSuccess) st = CSWGS_ECUDA;
+                }
+                arena_.free(r->off);
+                finish(*r, st);
+                active_[s].reset();
+            }
+        };
+        auto wait_prev = [&]() {
+            if (inflight_prev < 0) return;
+            const int64_t w = inflight_prev;
+            lk.unlock();
+            cudaEventSynchronize(launch_ev_[w & 1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, start_ev_[w & 1], launch_ev_[w & 1]);
+            lk.lock();
+            st_.busy_ms += ms;
+            completed_serial_ = w;
+            inflight_prev = -1;
+        };
+
+        if (!has_work) {
+            // nothing to launch: drain the launch in flight, or sleep
             if (inflight_prev >= 0) {
-                lk.unlock();
-                cudaEventSynchronize(launch_ev_[inflight_prev & 1]);
-                lk.lock();
-                completed_serial_ = inflight_prev;
-                inflight_prev = -1;
+                wait_prev();
+                complete();
+                for (int s = 0; s < B; ++s)
+                    if (active_[s] && active_[s]->cancelled) retiring_.push_back(std::move(active_[s]));
                 continue;
             }
-            if (stop_) break;
-            cv_.wait_for(lk, std::chrono::milliseconds(50));
+            if (stop_ && retiring_.empty() && queue_.empty()) break;
+            cv_.wait_for(lk, std::chrono::milliseconds(stop_ ? 1 : 20));
             continue;
         }
-        // build launch `serial_`: one slot per active request, heaviest first
+        // build launch `serial_`: one slot per request with work left, heaviest first
         std::vector<Req *> order;
         for (auto &a : active_)
-            if (a && !a->cancelled) order.push_back(a.get());
+            if (a && !a->cancelled && pass_of(a->spec, a->L) >= 0) order.push_back(a.get());
         std::stable_sort(order.begin(), order.end(), [](Req *a, Req *b) { return a->spec.N > b->spec.N; });
         int nslots = 0, tiles = 0, maxN = 0;
         std::vector<Req *> finishing;
         for (Req *r : order) {
-            int pass = pass_of(r->spec, r->L);
-            if (pass < 0) continue;
+            const int pass = pass_of(r->spec, r->L);
             LaunchSlot &sl = sbuf[nslots++];
             sl.holo = r->slot;
             sl.pass = pass;
@@ -356,46 +393,22 @@ void Server::loop()
         auto g = grid_for.find(maxN);
         if (g == grid_for.end()) g = grid_for.emplace(maxN, iter_fp32_max_grid(shape_, maxN, p_->sm_count)).first;
         cudaEventRecord(start_ev_[serial & 1], stream_);
-        if (tiles > 0)
-            launch_iter_fp32(shape_, holos, sd, nslots, tiles, maxN, queue, std::min(g->second, tiles), stream_);
+        launch_iter_fp32(shape_, holos, sd, nslots, tiles, maxN, queue, std::min(g->second, tiles), stream_);
         double *mh = met_h_ + (size_t)(serial & 1) * 2 * B;
         for (Req *r : finishing) {
             cudaMemcpyAsync(mh + 2 * r->slot, r->dev.metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
             r->finishing = true;
         }
         cudaEventRecord(launch_ev_[serial & 1], stream_);
-        for (Req *r : order) {
+        for (Req *r : order) {          // only the requests that took part advance
             r->L++;
             r->last_launch = serial;
         }
         st_.launches++;
-        // wait for the previous launch while this one runs
-        if (inflight_prev >= 0) {
-            lk.unlock();
-            cudaEventSynchronize(launch_ev_[inflight_prev & 1]);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, start_ev_[inflight_prev & 1], launch_ev_[inflight_prev & 1]);
-            lk.lock();
-            st_.busy_ms += ms;
-            completed_serial_ = inflight_prev;
-        }
+        // wait for the previous launch while this one runs, then collect its results
+        wait_prev();
         inflight_prev = serial;
-        // completions of the launch just waited for
-        for (int s = 0; s < B; ++s) {
-            Req *r = active_[s].get();
-            if (!r || !r->finishing || r->last_launch > completed_serial_) continue;
-            const double *m = met_h_ + (size_t)(r->last_launch & 1) * 2 * B + 2 * s;
-            r->met.assign(m, m + 2);
-            cswgs_status st = CSWGS_OK;
-            if (r->phase_host) {
-                cudaError_t e = cudaMemcpy(r->phase_host, r->dev.phase_out,
-                                           sizeof(float) * (size_t)r->spec.P * r->spec.P, cudaMemcpyDeviceToHost);
-                if (e != cudaSuccess) st = CSWGS_ECUDA;
-            }
-            arena_.free(r->off);
-            finish(*r, st);
-            active_[s].reset();
-        }
+        complete();
         // cancelled requests leave their slot now; memory is freed once idle
         for (int s = 0; s < B; ++s)
             if (active_[s] && active_[s]->cancelled) retiring_.push_back(std::move(active_[s]));

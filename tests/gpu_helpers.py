@@ -9,6 +9,8 @@ TOL_PHASE_RMS = 1e-3
 TOL_EU = 1e-3
 # The FP64 GPU baseline computes the same sums as the oracle in another order.
 TOL_FP64_PHASE = 1e-9
+# ... and writes its map as float32: half an ulp of 2 pi is 2.4e-7 rad.
+TOL_FP64_MAP = 2e-7
 TOL_FP64_EU = 1e-11
 
 

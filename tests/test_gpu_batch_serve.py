@@ -135,7 +135,6 @@ def test_serving_host_output_and_poll():
         assert r is not None and r["status"] == 0
         s, ph = solo(p, pb)
         assert rms_wrapped(out, ph) < TOL_SAME_PHASE
-        assert p.poll(t) is None or True
         from paper_2003_05293_gb300 import CswgsError
         with pytest.raises(CswgsError):
             p.poll(t)                  # collected tickets are gone
@@ -144,7 +143,8 @@ def test_serving_host_output_and_poll():
 def test_serving_cancel():
     from paper_2003_05293_gb300 import Plan
     with Plan(precision="fp32", max_batch=1) as p:
-        big = workloads.problem(512, 200, 5.0, 0.25, 200, seed=1)
+        # ~10^13 phasor pairs: seconds of work, so it is still running when cancelled
+        big = workloads.problem(2048, 1000, 5.0, 1.0, 600, seed=1)
         small = small_mix(3, 8)
         tb = p.submit(big, None)
         ts = [p.submit(pb, None) for pb in small]
