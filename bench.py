@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (read, and written when tuning)")
     return ap.parse_args()
 
 
@@ -181,7 +182,7 @@ def main():
     B = len(pbs)
     stream = torch.cuda.current_stream()
     plan = Plan(device=local, precision="fp32", max_batch=max(64, B), max_N=max(1024, args.N),
-                stream=stream.cuda_stream)
+                stream=stream.cuda_stream, tune_cache=args.tune_cache)
     outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
     batch = plan.batch(pbs, outs)
     total_pairs, iter_pairs = batch.pairs()

@@ -84,16 +84,19 @@ __device__ __forceinline__ uint32_t permute(uint32_t k, uint32_t P, const Subset
 // Phases are carried in turns as 32-bit fixed point (2^32 = one turn), so
 // arithmetic mod 2^32 is arithmetic mod 2 pi with no rounding: the range
 // reduction of the lens-and-prism argument (Eq. 2, up to a few hundred turns
-// at P = 1152) is exact.  The spot coefficients (turns per pixel, FP64 on the
-// host side of the kernel) are split into 32-bit words:
+// at P = 1152) is exact.  The spot coefficients (turns per pixel, FP64 in the
+// preparation kernel) are split into 32-bit words:
 //   tilt:    A = a * 2^32, B = b * 2^32           (a = alpha/P, b = beta/P)
-//   defocus: g * 2^32 = Gh + Gl * 2^-32           (g = gamma/(P/2)^2)
-// so that phi_n(m) * 2^32 / (2 pi) = A x' + B y' + Gh rho^2 + hi32(Gl rho^2)
-// (mod 2^32) to within 2 units, for integer pixel coordinates x', y' and
-// rho^2 = x'^2 + y'^2 < 2^32.
+//   defocus: g * 2^32 = Gh + Gl * 2^-32            (g = gamma/(P/2)^2)
+// so that, for integer pixel coordinates x', y' and rho^2 = x'^2 + y'^2 < 2^32,
+//   phi_n(m) * 2^32 / (2 pi) = A x' + B y' + Gh rho^2 + Gl rho^2 2^-32   (mod 2^32).
+// The first three terms are exact integer arithmetic.  The last one is below
+// rho^2 units (< 2^-12 turn, 1.5e-3 rad at P = 1152), so it is carried in
+// floating point, in radians (gl = Gl 2^-64 2 pi per unit of rho^2), and
+// added after the conversion to radians with an absolute error ~1e-10 rad.
 struct SpotFix {
     int32_t A, B, Gh;
-    uint32_t Gl;
+    float gl;       // radians per unit of rho^2 (the low word of the defocus)
 };
 
 // Nearest 32-bit fixed-point turn of a real number of turns (mod 1).
@@ -113,22 +116,20 @@ __device__ __forceinline__ SpotFix spot_fix(double alpha, double beta, double ga
     g = g - rint(g);                               // rho^2 is an integer: g mod 1
     double gs = g * 4294967296.0;                  // exact scaling
     double gh = floor(gs);
-    double gl = rint((gs - gh) * 4294967296.0);    // in [0, 2^32]
-    int64_t ghi = (int64_t)gh;
-    if (gl >= 4294967296.0) { gl = 0.0; ghi += 1; }
-    s.Gh = (int32_t)(uint32_t)ghi;
-    s.Gl = (uint32_t)gl;
+    double frac = gs - gh;                         // [0, 1) units of 2^-32 turn per rho^2
+    s.Gh = (int32_t)(uint32_t)(int64_t)gh;
+    s.gl = (float)(frac * (kTwoPi / 4294967296.0));
     return s;
 }
 
-// Fixed-point phase of spot s at pixel (x', y', rho^2), plus an addend.
+// Integer part of the fixed-point phase of spot s at pixel (x', y', rho^2),
+// plus an addend.
 __device__ __forceinline__ uint32_t fix_phase(const SpotFix &s, int32_t xp, int32_t yp,
                                               uint32_t rho2, uint32_t addend)
 {
     uint32_t t = addend + (uint32_t)s.A * (uint32_t)xp;
     t += (uint32_t)s.B * (uint32_t)yp;
     t += (uint32_t)s.Gh * rho2;
-    t += __umulhi(s.Gl, rho2);
     return t;
 }
 
@@ -136,16 +137,16 @@ __device__ __forceinline__ uint32_t fix_phase(const SpotFix &s, int32_t xp, int3
 // 23 bits of the phase, so adding half of the dropped range rounds to nearest.
 constexpr uint32_t kFixRound = 1u << 8;
 
-// sin and cos of 2 pi T / 2^32, T already carrying kFixRound.  The top 23 bits
-// of T become the mantissa of a float in [1, 2), i.e. 1 + turns; one FMA
-// turns it into radians in [0, 2 pi) with no offset error; the hardware
-// sine/cosine approximations finish.
-__device__ __forceinline__ void sincos_fix(uint32_t T, float &s, float &c)
+// sin and cos of 2 pi T / 2^32 + corr, T already carrying kFixRound, where
+// corr_m2pi = corr - 2 pi.  The top 23 bits of T become the mantissa of a float
+// in [1, 2), i.e. 1 + turns; one FMA turns it into radians in [0, 2 pi) plus
+// the small correction; the hardware sine/cosine approximations finish.
+__device__ __forceinline__ void sincos_fix(uint32_t T, float corr_m2pi, float &s, float &c)
 {
     float f = __uint_as_float((T >> 9) | 0x3F800000u);
-    float x = fmaf(f, kTwoPiF, -kTwoPiF);
-    s = __sinf(x);
-    c = __cosf(x);
+    float x = fmaf(f, kTwoPiF, corr_m2pi);
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
 // Fixed-point turn of an angle in radians, as float (|x| <= pi).

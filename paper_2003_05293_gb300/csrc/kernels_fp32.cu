@@ -117,6 +117,11 @@ __device__ void tail_metrics(const HoloDev &H, const LaunchSlot &sl, double *s_r
     }
 }
 
+// Spots per warp-transposed reduction round, and the padded row length of the
+// per-warp transpose buffer (17 float2: conflict-free column reads).
+constexpr int kWarpChunk = 16;
+constexpr int kWarpRow = kWarpChunk + 1;
+
 template <int THREADS, int PPT>
 __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int maxN,
                              unsigned char *smem, double *s_red, int *s_last)
@@ -124,8 +129,9 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     constexpr int W = THREADS / 32;
     int4 *s_coef = reinterpret_cast<int4 *>(smem);
     uint2 *s_bw = reinterpret_cast<uint2 *>(s_coef + maxN);
-    float2 *s_part = reinterpret_cast<float2 *>(s_bw + maxN);
-    float2 *s_v = s_part + W * kSpotChunk;
+    float2 *s_v = reinterpret_cast<float2 *>(s_bw + maxN);
+    float2 *s_part = s_v + maxN;                       // W x kSpotChunk
+    float2 *s_wbuf = s_part + W * kSpotChunk;          // W x 32 x kWarpRow
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int P = H.P, N = H.N;
@@ -145,7 +151,7 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     const int half = P >> 1;
     int32_t xp[PPT], yp[PPT];
     uint32_t r2[PPT];
-    float msk[PPT];
+    float qf[PPT], msk[PPT];
     int mix[PPT];
     const int base = t * (THREADS * PPT);
 #pragma unroll
@@ -159,6 +165,7 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         xp[s] = i - half;
         yp[s] = r - half;
         r2[s] = (uint32_t)(xp[s] * xp[s] + yp[s] * yp[s]);
+        qf[s] = (float)r2[s];
         msk[s] = valid ? 1.f : 0.f;
         mix[s] = valid ? (int)m : -1;
     }
@@ -172,11 +179,12 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         const int4 c = s_coef[n];
         const uint2 bw = s_bw[n];
         const float wn = __uint_as_float(bw.y);
-        const SpotFix f = {c.x, c.y, c.z, (uint32_t)c.w};
+        const float gl = __int_as_float(c.w);
+        const SpotFix f = {c.x, c.y, c.z, gl};
 #pragma unroll
         for (int s = 0; s < PPT; ++s) {
             float sn, cs;
-            sincos_fix(fix_phase(f, xp[s], yp[s], r2[s], bw.x), sn, cs);
+            sincos_fix(fix_phase(f, xp[s], yp[s], r2[s], bw.x), fmaf(gl, qf[s], -kTwoPiF), sn, cs);
             sr[s] = fmaf(wn, cs, sr[s]);
             si[s] = fmaf(wn, sn, si[s]);
         }
@@ -195,26 +203,43 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         }
     }
 
-    // forward projection, Eq. 3: conj of sum_m e^{i (phi_n(m) - Phi_m)}
+    // forward projection, Eq. 3: conj of sum_m e^{i (phi_n(m) - Phi_m)}.
+    // Per spot each thread sums its PPT pixels; the warp's 32 partials of 16
+    // spots go through a transposed shared buffer (lane q sums spot q), the
+    // warps' totals through s_part, and one partial per (tile, spot) leaves.
+    float2 *wbuf = s_wbuf + warp * 32 * kWarpRow;
     for (int n0 = 0; n0 < N; n0 += kSpotChunk) {
         const int nc = min(kSpotChunk, N - n0);
-        for (int q = 0; q < nc; ++q) {
-            const int4 c = s_coef[n0 + q];
-            const SpotFix f = {c.x, c.y, c.z, (uint32_t)c.w};
-            float vr = 0.f, vi = 0.f;
+        for (int q0 = 0; q0 < nc; q0 += kWarpChunk) {
+            const int qc = min(kWarpChunk, nc - q0);
+            for (int q = 0; q < qc; ++q) {
+                const int4 c = s_coef[n0 + q0 + q];
+                const float gl = __int_as_float(c.w);
+                const SpotFix f = {c.x, c.y, c.z, gl};
+                float vr = 0.f, vi = 0.f;
 #pragma unroll
-            for (int s = 0; s < PPT; ++s) {
-                float sn, cs;
-                sincos_fix(fix_phase(f, xp[s], yp[s], r2[s], padd[s]), sn, cs);
-                vr = fmaf(msk[s], cs, vr);
-                vi = fmaf(msk[s], sn, vi);
+                for (int s = 0; s < PPT; ++s) {
+                    float sn, cs;
+                    sincos_fix(fix_phase(f, xp[s], yp[s], r2[s], padd[s]), fmaf(gl, qf[s], -kTwoPiF), sn, cs);
+                    vr = fmaf(msk[s], cs, vr);
+                    vi = fmaf(msk[s], sn, vi);
+                }
+                wbuf[lane * kWarpRow + q] = make_float2(vr, vi);
             }
+            __syncwarp();
+            // lane = 16 h + q sums rows 16 h .. 16 h + 15 of column q
+            const int q = lane & (kWarpChunk - 1), h = lane >> 4;
+            float ar = 0.f, ai = 0.f;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                vr += __shfl_xor_sync(0xffffffffu, vr, o);
-                vi += __shfl_xor_sync(0xffffffffu, vi, o);
+            for (int i = 0; i < 16; ++i) {
+                float2 p = wbuf[(h * 16 + i) * kWarpRow + q];
+                ar += p.x;
+                ai += p.y;
             }
-            if (lane == 0) s_part[warp * kSpotChunk + q] = make_float2(vr, -vi);
+            ar += __shfl_xor_sync(0xffffffffu, ar, 16);
+            ai += __shfl_xor_sync(0xffffffffu, ai, 16);
+            if (h == 0 && q < qc) s_part[warp * kSpotChunk + q0 + q] = make_float2(ar, -ai);
+            __syncwarp();
         }
         __syncthreads();
         for (int q = tid; q < nc; q += THREADS) {
@@ -308,7 +333,7 @@ __global__ void prep_kernel(const HoloDev *__restrict__ holos)
     const HoloDev H = holos[blockIdx.y];
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < H.N; n += gridDim.x * blockDim.x) {
         SpotFix f = spot_fix(H.xyz[3 * n], H.xyz[3 * n + 1], H.xyz[3 * n + 2], H.P);
-        H.coef[n] = make_int4(f.A, f.B, f.Gh, (int)f.Gl);
+        H.coef[n] = make_int4(f.A, f.B, f.Gh, __float_as_int(f.gl));
         double th = H.init_th ? H.init_th[n] / kTwoPi : theta0_turns(H.seed, n);
         SpotState st;
         st.theta = turns_to_fix(th);
@@ -354,7 +379,7 @@ size_t iter_fp32_smem(TileShape shape, int maxN)
 {
     const int W = shape.threads / 32;
     return (size_t)maxN * (sizeof(int4) + sizeof(uint2) + sizeof(float2)) +
-           (size_t)W * kSpotChunk * sizeof(float2);
+           (size_t)W * kSpotChunk * sizeof(float2) + (size_t)W * 32 * kWarpRow * sizeof(float2);
 }
 
 #define CSWGS_SHAPES(X) \
