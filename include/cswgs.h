@@ -246,6 +246,34 @@ cswgs_status cswgs_autotune(cswgs_plan p, int P, int N, double subset_fraction, 
  * results per second, *sm_mhz the SM clock seen during the run. */
 cswgs_status cswgs_sincos_peak(cswgs_plan p, double *sincos_per_s, double *sm_mhz);
 
+/* ------------------------------------------------- allocation-free solve --- */
+
+/* The paper has no counterpart of this entry point: it serves callers that
+ * cannot allocate device memory (a real-time loop feeding an SLM that cannot
+ * take an allocation's latency or its risk of failing, a host with a fixed
+ * device-memory budget).  It runs the cswgs_solve method (FP32, the last two
+ * iterations over all pixels, the final pass) on the caller's device buffers
+ * and calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (spot tables, per-tile partial fields, counters) is one 16 MiB array of
+ * device memory in the library's image, present on every GPU that loads the
+ * library until the process exits.
+ *   spots_xyz: device, N x 3 doubles (not checked for finiteness: device data);
+ *   amplitudes: device, N doubles, or NULL (all 1);
+ *   phase_out: device, P*P floats, written in [0, 2 pi);
+ *   eu_out: device, 2 doubles (e, u), or NULL;
+ *   stream: cudaStream_t the work is queued on (NULL: the default stream).
+ * Limits: P even, 2 <= P <= 1152; 1 <= N <= 512; larger sizes fail with
+ * CSWGS_EINVAL and a message.  Runs on the current device and returns once
+ * the work is queued: synchronise the stream before reading the outputs.
+ * The first call on a device looks up the array's device address and the
+ * kernel's launch limits; make that first call before any stream capture.
+ * Every call shares the array and leaves its contents behind (each call
+ * clears the parts that must start at zero); calls whose work overlaps on the
+ * GPU race on it and must be serialised by the caller. */
+cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const double *amplitudes, int N, int P,
+                                 double subset_fraction, int iterations, uint64_t seed,
+                                 float *phase_out, double *eu_out, void *stream);
+
 /* ---------------------------------------------------------------- misc --- */
 
 int cswgs_abi_version(void);

@@ -89,6 +89,8 @@ SIGNATURES = {
     "cswgs_serve_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_serve_stats)]),
     "cswgs_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, c_double_p]),
     "cswgs_sincos_peak": (ctypes.c_int, [_P, c_double_p, c_double_p]),
+    "cswgs_solve_noalloc": (ctypes.c_int, [c_double_p, c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_uint64, c_float_p, c_double_p, ctypes.c_void_p]),
     "cswgs_abi_version": (ctypes.c_int, []),
     "cswgs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cswgs_last_error": (ctypes.c_char_p, []),
