@@ -36,6 +36,12 @@ import workloads  # noqa: E402
 
 METRIC = "holograms/s and p50/p99 latency at M=1152^2, N=100, e,u>=0.9 vs FP64 GPU baseline"
 SFU_PER_CLK_PER_SM = 16       # sine/cosine results per clock per SM (CUDA arithmetic throughput table)
+FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
+# DRAM bytes (read + write) per launch of the iteration kernel at this workload,
+# from an ncu capture of this bench (profiles/iter_kernel_b64_launches.md), or
+# None once the kernel has changed since the counters were taken.
+TRAFFIC_SUB = None
+TRAFFIC_FULL = None
 
 
 def parse():
@@ -200,7 +206,7 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    step_ms, iter_ms, iter_n = [], 0.0, 0
+    step_ms, kts = [], []
     ev0.record(stream)
     t_wall = time.perf_counter()
     for _ in range(args.steps):
@@ -209,8 +215,7 @@ def main():
         res = batch.results()                # waits for the step
         kt = batch.kernel_times()            # prep, then one entry per persistent launch
         step_ms.append(sum(kt))
-        iter_ms += sum(kt[1:])
-        iter_n += len(kt) - 1
+        kts.append(kt)
     ev1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -219,7 +224,13 @@ def main():
     total_ms = max_over_ranks(ev0.elapsed_time(ev1))
     value = B * world * args.steps / (total_ms * 1e-3)
 
-    # roofline of the iteration kernel: algorithmic sine+cosine per pair
+    # rooflines of the iteration kernel, per launch kind (measured live, CUDA
+    # events around every launch of every timed step):
+    #  - compressed iterations: direct phasors, 2 SFU results (sin, cos) per
+    #    pixel-spot pair and pass -> against the SFU peak;
+    #  - full iterations and the final pass: separable phasors, one complex
+    #    multiply-add (8 flops) per pixel-spot pair and pass -> against the FP32
+    #    FMA peak.
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
     max_mhz = 2070.0
@@ -228,8 +239,17 @@ def main():
         max_mhz = float(mp.get("sm_max_mhz", max_mhz))
     except (OSError, ValueError):
         pass
-    peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9        # G sincos-op/s
-    achieved = 2.0 * total_pairs / (iter_ms / args.steps * 1e-3) / 1e9
+    n_sub = args.iters - min(2, args.iters)
+    Mp = math.floor(args.c * args.P * args.P)
+    pairs_sub_launch = B * 2.0 * args.N * Mp
+    pairs_full_launch = B * 2.0 * args.N * args.P * args.P
+    sub_ms = sum(sum(k[1:1 + n_sub]) for k in kts) / args.steps
+    full_ms = sum(sum(k[1 + n_sub:]) for k in kts) / args.steps
+    n_full_launches = len(kts[0]) - 1 - n_sub
+    sfu_peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9           # G sin-or-cos/s
+    fma_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12       # TFLOP/s
+    sfu_achieved = 2.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e9 if n_sub else 0.0
+    fma_achieved = 8.0 * pairs_full_launch * n_full_launches / (full_ms * 1e-3) / 1e12
     probe, probe_mhz = plan.sincos_peak()
 
     eu = [(r["e"], r["u"]) for r in res]
@@ -242,14 +262,25 @@ def main():
                            "what": "batch step = every hologram of the batch, submit to result"},
             "quality": {"e_mean": float(np.mean([a for a, _ in eu])), "u_mean": float(np.mean([b for _, b in eu])),
                         "u_min": float(np.min([b for _, b in eu])), "e_min": float(np.min([a for a, _ in eu]))},
-            "roofline": {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": achieved, "peak": peak,
-                         "unit": "G sincos/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "iter_kernel (all %d persistent launches of a step)" % iter_n_per_step(iter_n, args),
-                         "peak_basis": "%d SMs x %d/clk x %.0f MHz" % (sm_count, SFU_PER_CLK_PER_SM, max_mhz),
-                         "probe_measured": probe / 1e9, "probe_sm_mhz": probe_mhz,
-                         "algorithmic_pairs_per_step": total_pairs,
-                         "tile": {"threads": tile[0], "pixels_per_thread": tile[1], "blocks": tile[2]}},
-            "gpu_launches": args.steps * (1 + iter_n_per_step(iter_n, args)),
+            "roofline": {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": sfu_achieved, "peak": sfu_peak,
+                         "unit": "G sincos/s", "frac": sfu_achieved / sfu_peak, "traffic": TRAFFIC_SUB,
+                         "kernel": "iter_kernel, compressed-iteration launches (%d per step, %.1f%% of the step)"
+                                   % (n_sub, 100 * sub_ms / (sub_ms + full_ms)),
+                         "peak_basis": "%d SMs x %d/clk x %.0f MHz (of derived; probe measured %.0f G/s)"
+                                       % (sm_count, SFU_PER_CLK_PER_SM, max_mhz, probe / 1e9),
+                         "ms_per_launch": sub_ms / max(1, n_sub),
+                         "tile": {k: tile[k] for k in ("threads", "pixels_per_thread", "blocks")}},
+            "roofline_full_passes": {"bound": "alu", "pipe": "FP32 FMA", "achieved": fma_achieved, "peak": fma_peak,
+                                     "unit": "TFLOP/s", "frac": fma_achieved / fma_peak, "traffic": TRAFFIC_FULL,
+                                     "kernel": "iter_kernel, separable full-iteration and final launches (%d per step)"
+                                               % n_full_launches,
+                                     "flops_basis": "8 flops (complex multiply-add) per pixel-spot pair and pass",
+                                     "peak_basis": "%d SMs x %d lanes x 2 flops x %.0f MHz (of derived)"
+                                                   % (sm_count, FP32_LANES_PER_SM, max_mhz),
+                                     "ms_per_launch": full_ms / max(1, n_full_launches),
+                                     "tile": {"threads": tile["full_threads"], "blocks": tile["full_blocks"],
+                                              "pixels": "threads/4 rows x 32 columns, 4 x 2 per thread"}},
+            "gpu_launches": args.steps * len(kts[0]),
             "clocks": clk}
 
     # FP64 GPU baseline (plain double-precision kernels), one hologram at a time
@@ -300,10 +331,6 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
-
-
-def iter_n_per_step(iter_n, args):
-    return iter_n // max(1, args.steps)
 
 
 if __name__ == "__main__":

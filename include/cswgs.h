@@ -187,9 +187,12 @@ cswgs_status cswgs_batch_kernel_times(cswgs_batch b, float *ms, int cap, int *co
  * N * (2 * (I - F) * Mp + 2 * F * M + 2 * M), F = min(full_iterations, I). */
 cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs_iter_launches);
 
-/* Launch shape of the batch's iteration kernel, as chosen by the autotuner:
- * threads per block, pixels per thread, and persistent blocks per launch. */
-cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *blocks);
+/* Launch shapes of the batch's two iteration kernels, as chosen by the
+ * autotuner: for compressed iterations threads per block and pixels per
+ * thread, for full iterations and the final pass threads per block, and the
+ * persistent blocks of each per launch.  Any pointer may be NULL. */
+cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *full_threads,
+                                    int *blocks, int *full_blocks);
 
 cswgs_status cswgs_batch_destroy(cswgs_batch b);
 

@@ -254,10 +254,12 @@ class Batch:
         return a.value, b.value
 
     def tile_shape(self):
-        t, k, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        check(self.lib.cswgs_batch_tile_shape(self.handle, ctypes.byref(t), ctypes.byref(k), ctypes.byref(g)),
-              "cswgs_batch_tile_shape")
-        return t.value, k.value, g.value
+        """dict: threads, pixels_per_thread, blocks (compressed iterations);
+        full_threads, full_blocks (full iterations and final pass)."""
+        v = [ctypes.c_int() for _ in range(5)]
+        check(self.lib.cswgs_batch_tile_shape(self.handle, *[ctypes.byref(x) for x in v]), "cswgs_batch_tile_shape")
+        keys = ("threads", "pixels_per_thread", "full_threads", "blocks", "full_blocks")
+        return dict(zip(keys, (x.value for x in v)))
 
     def close(self):
         if self.handle:

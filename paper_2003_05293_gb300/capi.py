@@ -77,8 +77,7 @@ SIGNATURES = {
     "cswgs_batch_kernel_times": (ctypes.c_int, [_P, c_float_p, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_int)]),
     "cswgs_batch_pairs": (ctypes.c_int, [_P, c_double_p, c_double_p]),
-    "cswgs_batch_tile_shape": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                              ctypes.POINTER(ctypes.c_int)]),
+    "cswgs_batch_tile_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int)] * 5),
     "cswgs_batch_destroy": (ctypes.c_int, [_P]),
     "cswgs_solve_batch": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_request), ctypes.c_int,
                                          ctypes.POINTER(cswgs_result)]),

@@ -424,12 +424,15 @@ cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs
     return CSWGS_OK;
 }
 
-cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *blocks)
+cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *full_threads,
+                                    int *blocks, int *full_blocks)
 {
     if (!b) return set_error(CSWGS_EINVAL, "NULL batch");
     if (threads) *threads = b->b->shape.threads;
     if (pixels_per_thread) *pixels_per_thread = b->b->shape.ppt;
-    if (blocks) *blocks = b->b->grid;
+    if (full_threads) *full_threads = b->b->shape.full_threads;
+    if (blocks) *blocks = b->b->grid[kLaunchSubset];
+    if (full_blocks) *full_blocks = b->b->grid[kLaunchFull];
     return CSWGS_OK;
 }
 

@@ -55,20 +55,24 @@ struct LaunchSlot {
     int count;        // pixels of the pass (Mp or M)
 };
 
-// Tile shape of the FP32 iteration kernel.
+// Tile shapes of the two FP32 iteration kernels.
 struct TileShape {
-    int threads;      // threads per block
-    int ppt;          // pixels per thread
+    int threads;        // compressed iterations: threads per block
+    int ppt;            // compressed iterations: pixels per thread
+    int full_threads;   // full iterations and final pass: threads per block
 };
+
+// The two iteration kernels: compressed-iteration tiles, separable full-pass tiles.
+enum LaunchKind : int { kLaunchSubset = 0, kLaunchFull = 1 };
 
 // Kernel launchers (kernels_fp32.cu).
 cudaError_t launch_prep_fp32(const HoloDev *holos, int count, int maxN, cudaStream_t s);
-cudaError_t launch_iter_fp32(TileShape shape, const HoloDev *holos, const LaunchSlot *slots,
+cudaError_t launch_iter_fp32(TileShape shape, int kind, const HoloDev *holos, const LaunchSlot *slots,
                              int nslots, int total_tiles, int maxN, unsigned *queue,
                              int grid, cudaStream_t s);
-int iter_fp32_max_grid(TileShape shape, int maxN, int sm_count);
+int iter_fp32_max_grid(TileShape shape, int kind, int maxN, int sm_count);
 bool tile_shape_supported(TileShape shape);
-size_t iter_fp32_smem(TileShape shape, int maxN);
+size_t iter_fp32_smem(TileShape shape, int kind, int maxN);
 cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_t *out,
                                  cudaStream_t s);
 cudaError_t launch_sincos_probe(float *sink, long long *cycles, int iters, int blocks,

@@ -19,14 +19,15 @@
 
 namespace cswgs {
 
-template <int THREADS, int PPT>
-__global__ void __launch_bounds__(THREADS)
-iter_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
-            int total_tiles, int maxN, unsigned *queue)
+// The persistent loop both iteration kernels share: blocks take work items
+// (tiles) from the launch's queue until it is empty; the last block out resets
+// the queue for the next launch on the stream.
+template <class TileFn>
+__device__ __forceinline__ void persistent_tiles(const HoloDev *__restrict__ holos,
+                                                 const LaunchSlot *__restrict__ slots, int nslots,
+                                                 int total_tiles, unsigned *queue, TileFn tile)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_red[THREADS / 32];
-    __shared__ int s_item, s_slot, s_last;
+    __shared__ int s_item, s_slot;
     const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) {
@@ -47,9 +48,8 @@ iter_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ sl
         if (item >= total_tiles) break;
         const LaunchSlot sl = slots[s_slot];
         const HoloDev H = holos[sl.holo];
-        process_tile<THREADS, PPT>(H, sl, item - sl.tile_begin, maxN, smem, s_red, &s_last);
+        tile(H, sl, item - sl.tile_begin);   // ends with __syncthreads()
     }
-    // the last block out resets the queue for the next launch on this stream
     if (tid == 0) {
         unsigned done = atomicAdd(queue + 1, 1u);
         if (done == gridDim.x - 1) {
@@ -58,6 +58,42 @@ iter_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ sl
             __threadfence();
         }
     }
+}
+
+// Minimum resident blocks per SM each register budget must allow (without a
+// minimum, ptxas settles on 64 registers and spills): 32 warps per SM for
+// compressed tiles of up to 4 pixels per thread, 24 warps otherwise.
+template <int THREADS, int PPT>
+constexpr int subset_min_blocks() { return (PPT <= 4 ? 1024 : 768) / THREADS; }
+template <int THREADS>
+constexpr int full_min_blocks() { return 768 / THREADS > 0 ? 768 / THREADS : 1; }
+
+// Compressed iterations: tiles of THREADS * PPT pixels of the subsets S_j.
+template <int THREADS, int PPT>
+__global__ void __launch_bounds__(THREADS, (subset_min_blocks<THREADS, PPT>()))
+iter_subset_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
+                   int total_tiles, int maxN, unsigned *queue)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[THREADS / 32];
+    __shared__ int s_last;
+    persistent_tiles(holos, slots, nslots, total_tiles, queue, [&](const HoloDev &H, const LaunchSlot &sl, int t) {
+        process_tile<THREADS, PPT>(H, sl, t, maxN, smem, s_red, &s_last);
+    });
+}
+
+// Full iterations and the final pass: separable tiles of THREADS / 4 rows x 32 columns.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, (full_min_blocks<THREADS>()))
+iter_full_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
+                 int total_tiles, int maxN, unsigned *queue)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[THREADS / 32];
+    __shared__ int s_last;
+    persistent_tiles(holos, slots, nslots, total_tiles, queue, [&](const HoloDev &H, const LaunchSlot &sl, int t) {
+        process_full_tile<THREADS>(H, sl, t, maxN, smem, s_red, &s_last);
+    });
 }
 
 // Spot preparation (step 1 of the path): fixed-point coefficients of Eq. 2,
@@ -101,65 +137,78 @@ __global__ void sincos_probe_kernel(float *sink, long long *cycles, int iters)
 
 // ------------------------------------------------------------- launchers --
 
-size_t iter_fp32_smem(TileShape shape, int maxN)
-{
-    return tile_smem_bytes(shape.threads, maxN);
-}
-
-#define CSWGS_SHAPES(X) \
+#define CSWGS_SUBSET_SHAPES(X) \
     X(128, 2) X(128, 4) X(128, 8) X(256, 2) X(256, 4) X(256, 8) X(512, 1) X(512, 2) X(512, 4)
+#define CSWGS_FULL_SHAPES(X) X(128) X(256) X(512)
+
+size_t iter_fp32_smem(TileShape shape, int kind, int maxN)
+{
+    return kind == kLaunchSubset ? tile_smem_bytes(shape.threads, maxN, false)
+                                 : tile_smem_bytes(shape.full_threads, maxN, true);
+}
 
 bool tile_shape_supported(TileShape shape)
 {
-#define X(T, K) if (shape.threads == T && shape.ppt == K) return true;
-    CSWGS_SHAPES(X)
+    bool sub = false, full = false;
+#define X(T, K) sub |= shape.threads == T && shape.ppt == K;
+    CSWGS_SUBSET_SHAPES(X)
 #undef X
-    return false;
+#define X(T) full |= shape.full_threads == T;
+    CSWGS_FULL_SHAPES(X)
+#undef X
+    return sub && full;
 }
 
 // Dynamic shared memory the iteration kernels are allowed: enough for
 // N = 4096 spots with any supported tile shape.
-constexpr int kMaxDynSmem = 160 * 1024;
+constexpr int kMaxDynSmem = 200 * 1024;
 
-template <int T, int K>
-static int max_grid_impl(int maxN, int sm_count)
+template <class K>
+static int max_grid_of(K kernel, int threads, size_t smem, int sm_count)
 {
-    size_t smem = iter_fp32_smem(TileShape{T, K}, maxN);
     if (smem > (size_t)kMaxDynSmem) return 0;
-    if (cudaFuncSetAttribute(iter_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem) != cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iter_kernel<T, K>, T, smem) != cudaSuccess)
-        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) return 0;
     return per_sm * sm_count;
 }
 
-int iter_fp32_max_grid(TileShape shape, int maxN, int sm_count)
+int iter_fp32_max_grid(TileShape shape, int kind, int maxN, int sm_count)
 {
-#define X(T, K) if (shape.threads == T && shape.ppt == K) return max_grid_impl<T, K>(maxN, sm_count);
-    CSWGS_SHAPES(X)
+    const size_t smem = iter_fp32_smem(shape, kind, maxN);
+    if (kind == kLaunchSubset) {
+#define X(T, K) if (shape.threads == T && shape.ppt == K) return max_grid_of(iter_subset_kernel<T, K>, T, smem, sm_count);
+        CSWGS_SUBSET_SHAPES(X)
 #undef X
+    } else {
+#define X(T) if (shape.full_threads == T) return max_grid_of(iter_full_kernel<T>, T, smem, sm_count);
+        CSWGS_FULL_SHAPES(X)
+#undef X
+    }
     return 0;
 }
 
-template <int T, int K>
-static cudaError_t launch_impl(const HoloDev *holos, const LaunchSlot *slots, int nslots,
-                               int total_tiles, int maxN, unsigned *queue, int grid, cudaStream_t s)
-{
-    // the smem attribute is set by iter_fp32_max_grid, which every batch calls first
-    size_t smem = iter_fp32_smem(TileShape{T, K}, maxN);
-    (void)cudaGetLastError();   // report this launch, not an earlier call's error
-    iter_kernel<T, K><<<grid, T, smem, s>>>(holos, slots, nslots, total_tiles, maxN, queue);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_iter_fp32(TileShape shape, const HoloDev *holos, const LaunchSlot *slots,
+cudaError_t launch_iter_fp32(TileShape shape, int kind, const HoloDev *holos, const LaunchSlot *slots,
                              int nslots, int total_tiles, int maxN, unsigned *queue, int grid,
                              cudaStream_t s)
 {
-#define X(T, K) if (shape.threads == T && shape.ppt == K) return launch_impl<T, K>(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
-    CSWGS_SHAPES(X)
+    // the smem attribute is set by iter_fp32_max_grid, which every batch calls first
+    const size_t smem = iter_fp32_smem(shape, kind, maxN);
+    (void)cudaGetLastError();   // report this launch, not an earlier call's error
+    if (kind == kLaunchSubset) {
+#define X(T, K) if (shape.threads == T && shape.ppt == K) { \
+            iter_subset_kernel<T, K><<<grid, T, smem, s>>>(holos, slots, nslots, total_tiles, maxN, queue); \
+            return cudaGetLastError(); }
+        CSWGS_SUBSET_SHAPES(X)
 #undef X
+    } else {
+#define X(T) if (shape.full_threads == T) { \
+            iter_full_kernel<T><<<grid, T, smem, s>>>(holos, slots, nslots, total_tiles, maxN, queue); \
+            return cudaGetLastError(); }
+        CSWGS_FULL_SHAPES(X)
+#undef X
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -38,7 +38,7 @@ constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-__global__ void __launch_bounds__(kNoAllocThreads)
+__global__ void __launch_bounds__(kNoAllocThreads, 3)
 noalloc_iter_kernel(HoloDev H, LaunchSlot sl, int maxN, unsigned *queue)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -49,7 +49,10 @@ noalloc_iter_kernel(HoloDev H, LaunchSlot sl, int maxN, unsigned *queue)
         __syncthreads();
         const int item = s_item;
         if (item >= sl.tiles) break;
-        process_tile<kNoAllocThreads, kNoAllocPPT>(H, sl, item, maxN, smem, s_red, &s_last);
+        if (sl.pass == kPassSubset)
+            process_tile<kNoAllocThreads, kNoAllocPPT>(H, sl, item, maxN, smem, s_red, &s_last);
+        else
+            process_full_tile<kNoAllocThreads>(H, sl, item, maxN, smem, s_red, &s_last);
     }
     if (threadIdx.x == 0) {
         unsigned done = atomicAdd(queue + 1, 1u);
@@ -82,7 +85,7 @@ static void noalloc_setup(NoAllocDevice &d, int device)
 {
     d.err = cudaGetSymbolAddress(reinterpret_cast<void **>(&d.base), g_noalloc_scratch);
     if (d.err != cudaSuccess) return;
-    const size_t smem = tile_smem_bytes(kNoAllocThreads, kNoAllocMaxN);
+    const size_t smem = tile_smem_bytes(kNoAllocThreads, kNoAllocMaxN, true);
     d.err = cudaFuncSetAttribute(noalloc_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (d.err != cudaSuccess) return;
     int per_sm = 0, sms = 0;
@@ -118,7 +121,9 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
 
     // layout of the scratch array for this size
     const int tp = kNoAllocThreads * kNoAllocPPT;
-    const size_t tiles = (size_t)(M + tp - 1) / tp;
+    const int full_tiles = full_pass_tiles(P, kNoAllocThreads);
+    const int sub_tiles = (Mp + tp - 1) / tp;
+    const size_t tiles = (size_t)(sub_tiles > full_tiles ? sub_tiles : full_tiles);
     size_t off = 0;
     const size_t o_queue = off; off += 256;
     const size_t o_counter = off; off += 256;
@@ -163,7 +168,7 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
     (void)cudaGetLastError();
     noalloc_prep_kernel<<<(N + 127) / 128, 128, 0, s>>>(H);
     CSWGS_CUDA_TRY(cudaGetLastError());
-    const size_t smem = tile_smem_bytes(kNoAllocThreads, N);
+    const size_t smem = tile_smem_bytes(kNoAllocThreads, N, true);
     // the schedule of cswgs_solve: the last two iterations over all pixels, then the final pass
     const int n_full = iterations < 2 ? iterations : 2;
     for (int L = 0; L <= iterations; ++L) {
@@ -172,7 +177,7 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
         sl.pass = L < iterations - n_full ? kPassSubset : (L < iterations ? kPassFull : kPassFinal);
         sl.j = 1 + L;
         sl.count = sl.pass == kPassSubset ? Mp : M;
-        sl.tiles = (sl.count + tp - 1) / tp;
+        sl.tiles = sl.pass == kPassSubset ? sub_tiles : full_tiles;
         sl.tile_begin = 0;
         const int grid = sl.tiles < d.grid ? sl.tiles : d.grid;
         noalloc_iter_kernel<<<grid, kNoAllocThreads, smem, s>>>(H, sl, N, queue);

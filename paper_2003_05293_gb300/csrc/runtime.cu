@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "runtime.h"
+#include "tile.cuh"
 
 namespace cswgs {
 
@@ -77,6 +78,17 @@ static int pass_count(const HoloSpec &h, int pass)
     return pass == kPassSubset ? h.Mp : h.P * h.P;
 }
 
+int pass_tiles(int pass, int P, int Mp, TileShape shape)
+{
+    const int tp = shape.threads * shape.ppt;
+    return pass == kPassSubset ? (Mp + tp - 1) / tp : full_pass_tiles(P, shape.full_threads);
+}
+
+int max_pass_tiles(const HoloSpec &h, TileShape shape)
+{
+    return std::max(pass_tiles(kPassSubset, h.P, h.Mp, shape), pass_tiles(kPassFull, h.P, h.Mp, shape));
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Fp32Batch::~Fp32Batch()
@@ -118,8 +130,8 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     for (int h = 0; h < count; ++h) {
         const HoloSpec &s = b->specs[h];
         const int M = s.P * s.P;
-        const int tiles_it = (std::max(s.Mp, s.iterations > 0 && s.n_full > 0 ? M : 0) + tp - 1) / tp;
-        const int tiles_full = (M + tp - 1) / tp;
+        const int tiles_it = max_pass_tiles(s, shape);
+        const int tiles_full = pass_tiles(kPassFull, s.P, s.Mp, shape);
         w_off[h] = work;
         work += align256(sizeof(int4) * s.N);                                   // coef
         work += align256(sizeof(SpotState) * s.N);                              // state
@@ -165,8 +177,8 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             o += align256(sizeof(double) * s.N);
         }
         const int M = s.P * s.P;
-        const int tiles_it = (std::max(s.Mp, s.iterations > 0 && s.n_full > 0 ? M : 0) + tp - 1) / tp;
-        const int tiles_full = (M + tp - 1) / tp;
+        const int tiles_it = max_pass_tiles(s, shape);
+        const int tiles_full = pass_tiles(kPassFull, s.P, s.Mp, shape);
         size_t w = w_off[h];
         H.coef = reinterpret_cast<int4 *>(base + w);
         w += align256(sizeof(int4) * s.N);
@@ -187,7 +199,8 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         H.phase_out = b->own_phase[h];
     }
 
-    // launch schedule: launch L advances every hologram that still has work
+    // launch schedule: step L advances every hologram that still has work, with
+    // one launch of each kernel kind that has slots in it
     int L_max = 0;
     for (auto &s : b->specs) L_max = std::max(L_max, schedule_launches(s));
     // heavier tiles first: order holograms by N (tile cost) descending
@@ -198,29 +211,31 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     std::vector<LaunchSlot> slots;
     double pairs_total = 0.0, pairs_iter = 0.0;
     for (int L = 0; L < L_max; ++L) {
-        int first = (int)slots.size(), tiles = 0, mN = 0;
-        for (int h : order) {
-            const HoloSpec &s = b->specs[h];
-            int pass = pass_of(s, L);
-            if (pass < 0) continue;
-            LaunchSlot sl;
-            sl.holo = h;
-            sl.pass = pass;
-            sl.j = s.first_j + L;
-            sl.count = pass_count(s, pass);
-            sl.tiles = (sl.count + tp - 1) / tp;
-            sl.tile_begin = tiles;
-            tiles += sl.tiles;
-            mN = std::max(mN, s.N);
-            slots.push_back(sl);
-            double pr = 2.0 * (double)s.N * (double)sl.count;
-            pairs_total += pr;
-            if (pass != kPassFinal) pairs_iter += pr;
+        for (int kind = 0; kind < 2; ++kind) {
+            int first = (int)slots.size(), tiles = 0, mN = 0;
+            for (int h : order) {
+                const HoloSpec &s = b->specs[h];
+                int pass = pass_of(s, L);
+                if (pass < 0 || (pass == kPassSubset) != (kind == kLaunchSubset)) continue;
+                LaunchSlot sl;
+                sl.holo = h;
+                sl.pass = pass;
+                sl.j = s.first_j + L;
+                sl.count = pass_count(s, pass);
+                sl.tiles = pass_tiles(pass, s.P, s.Mp, shape);
+                sl.tile_begin = tiles;
+                tiles += sl.tiles;
+                mN = std::max(mN, s.N);
+                slots.push_back(sl);
+                double pr = 2.0 * (double)s.N * (double)sl.count;
+                pairs_total += pr;
+                if (pass != kPassFinal) pairs_iter += pr;
+            }
+            b->l_slot0.push_back(first);
+            b->l_nslots.push_back((int)slots.size() - first);
+            b->l_tiles.push_back(tiles);
+            b->l_maxN.push_back(mN);
         }
-        b->l_slot0.push_back(first);
-        b->l_nslots.push_back((int)slots.size() - first);
-        b->l_tiles.push_back(tiles);
-        b->l_maxN.push_back(mN);
     }
     b->pairs_total = pairs_total;
     b->pairs_iter = pairs_iter;
@@ -233,11 +248,14 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
                                   cudaMemcpyHostToDevice));
     CSWGS_CUDA_TRY(cudaMemset(b->queue_d.p, 0, 256));
     CSWGS_CUDA_TRY(cudaMemset(b->mem.p, 0, work));
-    b->grid = iter_fp32_max_grid(shape, b->maxN, p->sm_count);
-    if (b->grid <= 0) return set_error(CSWGS_ECUDA, "tile shape %dx%d cannot be resident with N=%d",
-                                       shape.threads, shape.ppt, b->maxN);
+    for (int kind = 0; kind < 2; ++kind) {
+        b->grid[kind] = iter_fp32_max_grid(shape, kind, b->maxN, p->sm_count);
+        if (b->grid[kind] <= 0)
+            return set_error(CSWGS_ECUDA, "tile shape %dx%d / %d cannot be resident with N=%d", shape.threads,
+                             shape.ppt, shape.full_threads, b->maxN);
+    }
     if (timing) {
-        b->events.resize(L_max + 2);
+        b->events.resize(L_max + 2);   // before the preparation, before each step, after the last
         for (auto &e : b->events) CSWGS_CUDA_TRY(cudaEventCreate(&e));
     }
     *out = std::move(b);
@@ -320,16 +338,19 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s));
     if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, evflag));
     CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
-    for (size_t L = 0; L < b->l_tiles.size(); ++L) {
+    const size_t steps = b->l_tiles.size() / 2;
+    for (size_t L = 0; L < steps; ++L) {
         if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[L + 1], s, evflag));
-        const int tiles = b->l_tiles[L];
-        if (tiles == 0) continue;
-        const int grid = std::min(b->grid, tiles);
-        CSWGS_CUDA_TRY(launch_iter_fp32(b->shape, holos, slots + b->l_slot0[L], b->l_nslots[L], tiles,
-                                        b->l_maxN[L], queue, grid, s));
+        for (int kind = 0; kind < 2; ++kind) {
+            const size_t i = 2 * L + kind;
+            const int tiles = b->l_tiles[i];
+            if (tiles == 0) continue;
+            const int grid = std::min(b->grid[kind], tiles);
+            CSWGS_CUDA_TRY(launch_iter_fp32(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
+                                            b->l_maxN[i], queue, grid, s));
+        }
     }
-    if (b->timing)
-        CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[b->l_tiles.size() + 1], s, evflag));
+    if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[steps + 1], s, evflag));
     return CSWGS_OK;
 }
 

@@ -79,6 +79,11 @@ cswgs_status validate_request(const cswgs_plan_desc &d, const double *xyz, const
 // Number of launches of the FP32 schedule: one per iteration plus the final pass.
 int schedule_launches(const HoloSpec &h);
 int pass_of(const HoloSpec &h, int L);   // PassKind of launch L, or -1
+// Work items of a pass: subset tiles of threads * ppt pixels, or separable
+// full-pass tiles (threads / 8 rows x 64 columns).
+int pass_tiles(int pass, int P, int Mp, TileShape shape);
+// Most work items any pass of this hologram has (size of its partial buffer).
+int max_pass_tiles(const HoloSpec &h, TileShape shape);
 
 // An FP32 batch ready to run: device buffers for every hologram, the launch
 // schedule (one persistent launch per iteration), and a CUDA graph of it.
@@ -92,9 +97,9 @@ struct Fp32Batch {
     DevBuf holos_d, slots_d, queue_d;
     void *staging = nullptr;              // pinned host copy of the inputs
     std::vector<float *> own_phase;       // internal phase buffers (host outputs), per hologram
-    std::vector<int> l_slot0, l_nslots, l_tiles, l_maxN;
-    TileShape shape{256, 4};
-    int grid = 0;
+    std::vector<int> l_slot0, l_nslots, l_tiles, l_maxN;   // per (step, kernel kind)
+    TileShape shape{256, 4, 256};
+    int grid[2] = {0, 0};                                     // resident blocks per kernel kind
     int maxN = 0;
     bool timing = false;
     cudaGraph_t graph = nullptr;

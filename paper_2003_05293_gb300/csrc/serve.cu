@@ -135,9 +135,8 @@ cswgs_status Server::start()
 
 size_t Server::footprint(const HoloSpec &s) const
 {
-    const int tp = shape_.threads * shape_.ppt;
     const size_t M = (size_t)s.P * s.P;
-    const size_t tiles = (M + tp - 1) / tp;
+    const size_t tiles = (size_t)max_pass_tiles(s, shape_);
     size_t b = 0;
     b += al256(sizeof(double) * 3 * s.N) + (s.has_amp ? al256(sizeof(double) * s.N) : 0);
     b += al256(sizeof(int4) * s.N) + al256(sizeof(SpotState) * s.N);
@@ -151,9 +150,7 @@ size_t Server::footprint(const HoloSpec &s) const
 void Server::place(Req &r)
 {
     const HoloSpec &s = r.spec;
-    const int tp = shape_.threads * shape_.ppt;
-    const size_t M = (size_t)s.P * s.P;
-    const size_t tiles = (M + tp - 1) / tp;
+    const size_t tiles = (size_t)max_pass_tiles(s, shape_);
     char *b = arena_.base() + r.off;
     size_t o = 0;
     HoloDev &H = r.dev;
@@ -250,13 +247,12 @@ void Server::loop()
 {
     cudaSetDevice(p_->device);
     const int B = p_->desc.max_batch;
-    const int tp = shape_.threads * shape_.ppt;
     HoloDev *holos = holos_d_.as<HoloDev>();
     HoloDev *prep_d = holos + B;
     unsigned *queue = queue_d_.as<unsigned>();
     std::unique_lock<std::mutex> lk(mu_);
     int64_t inflight_prev = -1;   // serial of the previous launch, not yet waited for
-    std::map<int, int> grid_for;
+    std::map<std::pair<int, int>, int> grid_for;   // (kernel kind, max N) -> resident blocks
     while (true) {
         if (stop_) {
             // the plan is going away: everything pending is cancelled
@@ -358,25 +354,31 @@ void Server::loop()
             cv_.wait_for(lk, std::chrono::milliseconds(stop_ ? 1 : 20));
             continue;
         }
-        // build launch `serial_`: one slot per request with work left, heaviest first
+        // build launch `serial_`: one slot per request with work left, heaviest
+        // first; compressed-iteration slots first, then full-pass slots, each
+        // group run by its own kernel
         std::vector<Req *> order;
         for (auto &a : active_)
             if (a && !a->cancelled && pass_of(a->spec, a->L) >= 0) order.push_back(a.get());
         std::stable_sort(order.begin(), order.end(), [](Req *a, Req *b) { return a->spec.N > b->spec.N; });
-        int nslots = 0, tiles = 0, maxN = 0;
+        int nslots = 0, group_slots[2] = {0, 0}, group_tiles[2] = {0, 0}, group_maxN[2] = {0, 0};
         std::vector<Req *> finishing;
-        for (Req *r : order) {
-            const int pass = pass_of(r->spec, r->L);
-            LaunchSlot &sl = sbuf[nslots++];
-            sl.holo = r->slot;
-            sl.pass = pass;
-            sl.j = r->spec.first_j + r->L;
-            sl.count = pass == kPassSubset ? r->spec.Mp : r->spec.P * r->spec.P;
-            sl.tiles = (sl.count + tp - 1) / tp;
-            sl.tile_begin = tiles;
-            tiles += sl.tiles;
-            maxN = std::max(maxN, r->spec.N);
-            if (pass == kPassFinal) finishing.push_back(r);
+        for (int kind = 0; kind < 2; ++kind) {
+            for (Req *r : order) {
+                const int pass = pass_of(r->spec, r->L);
+                if ((pass == kPassSubset) != (kind == kLaunchSubset)) continue;
+                LaunchSlot &sl = sbuf[nslots++];
+                sl.holo = r->slot;
+                sl.pass = pass;
+                sl.j = r->spec.first_j + r->L;
+                sl.count = pass == kPassSubset ? r->spec.Mp : r->spec.P * r->spec.P;
+                sl.tiles = pass_tiles(pass, r->spec.P, r->spec.Mp, shape_);
+                sl.tile_begin = group_tiles[kind];
+                group_tiles[kind] += sl.tiles;
+                group_slots[kind]++;
+                group_maxN[kind] = std::max(group_maxN[kind], r->spec.N);
+                if (pass == kPassFinal) finishing.push_back(r);
+            }
         }
         const int64_t serial = serial_++;
         HoloDev *hbuf = holos_h_[serial & 1];
@@ -390,10 +392,16 @@ void Server::loop()
             launch_prep_fp32(prep_d, nprep, pmax, stream_);
         }
         cudaMemcpyAsync(sd, sbuf, sizeof(LaunchSlot) * nslots, cudaMemcpyHostToDevice, stream_);
-        auto g = grid_for.find(maxN);
-        if (g == grid_for.end()) g = grid_for.emplace(maxN, iter_fp32_max_grid(shape_, maxN, p_->sm_count)).first;
         cudaEventRecord(start_ev_[serial & 1], stream_);
-        launch_iter_fp32(shape_, holos, sd, nslots, tiles, maxN, queue, std::min(g->second, tiles), stream_);
+        for (int kind = 0, first = 0; kind < 2; first += group_slots[kind], ++kind) {
+            if (group_tiles[kind] == 0) continue;
+            auto key = std::make_pair(kind, group_maxN[kind]);
+            auto g = grid_for.find(key);
+            if (g == grid_for.end())
+                g = grid_for.emplace(key, iter_fp32_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
+            launch_iter_fp32(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
+                             queue, std::min(g->second, group_tiles[kind]), stream_);
+        }
         double *mh = met_h_ + (size_t)(serial & 1) * 2 * B;
         for (Req *r : finishing) {
             cudaMemcpyAsync(mh + 2 * r->slot, r->dev.metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);

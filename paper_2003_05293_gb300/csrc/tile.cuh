@@ -111,28 +111,139 @@ __device__ void tail_metrics(const HoloDev &H, const LaunchSlot &sl, double *s_r
 constexpr int kWarpChunk = 16;
 constexpr int kWarpRow = kWarpChunk + 1;
 
+// Separable full-pass tiles: THREADS / 4 rows x kFullCols columns, each thread
+// a 4 x 2 block of pixels (16 threads across a row of the tile, so every
+// factor load is a broadcast or a contiguous 256-byte row); spot factors are
+// made kFactorChunk spots at a time.
+constexpr int kFullCols = 32;
+constexpr int kFactorChunk = 32;
+
+__host__ __device__ inline int full_pass_tiles(int P, int threads)
+{
+    const int rows = threads / 4;
+    return ((P + rows - 1) / rows) * ((P + kFullCols - 1) / kFullCols);
+}
+
+// Shared-memory layout of a tile (both tile processors).
+struct TileSmem {
+    int4 *coef;      // maxN: fixed-point spot coefficients
+    uint2 *bw;       // maxN: (theta addend, w a0)
+    float2 *v;       // maxN: tail scratch
+    float2 *part;    // W x kSpotChunk: per-warp spot totals
+    float2 *wbuf;    // W x 32 x kWarpRow: per-warp transpose buffers
+    float2 *fac;     // kFactorChunk x (THREADS / 4 + kFullCols): separable spot factors
+};
+
+template <int THREADS>
+__device__ __forceinline__ TileSmem tile_smem(unsigned char *smem, int maxN)
+{
+    constexpr int W = THREADS / 32;
+    TileSmem m;
+    m.coef = reinterpret_cast<int4 *>(smem);
+    m.bw = reinterpret_cast<uint2 *>(m.coef + maxN);
+    m.v = reinterpret_cast<float2 *>(m.bw + maxN);
+    m.part = m.v + maxN;
+    m.wbuf = m.part + W * kSpotChunk;
+    m.fac = m.wbuf + W * 32 * kWarpRow;
+    return m;
+}
+
+// Spot tables of hologram H into shared memory.
+template <int THREADS>
+__device__ __forceinline__ void load_spot_tables(const HoloDev &H, const TileSmem &m)
+{
+    for (int n = threadIdx.x; n < H.N; n += THREADS) {
+        m.coef[n] = H.coef[n];
+        SpotState st = H.state[n];
+        m.bw[n] = make_uint2(st.theta + kFixRound, __float_as_uint(st.w * st.a0));
+    }
+}
+
+// The warp's 32 lane partials of qc <= 16 spots sit in wbuf (row = lane,
+// column = spot).  Lane 16 h + q sums rows 16 h .. 16 h + 15 of column q, the
+// two halves meet by one shuffle, and lane q < qc stores the warp total.
+__device__ __forceinline__ void warp_transpose_reduce(const float2 *wbuf, int lane, int qc, float2 *dst)
+{
+    const int q = lane & (kWarpChunk - 1), h = lane >> 4;
+    float ar = 0.f, ai = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        float2 p = wbuf[(h * 16 + i) * kWarpRow + q];
+        ar += p.x;
+        ai += p.y;
+    }
+    ar += __shfl_xor_sync(0xffffffffu, ar, 16);
+    ai += __shfl_xor_sync(0xffffffffu, ai, 16);
+    if (h == 0 && q < qc) dst[q] = make_float2(ar, ai);
+}
+
+// Sums the warps' totals of spots n0 .. n0 + nc - 1 and writes the tile's
+// partial fields (FP64 for the metrics pass).
+template <int THREADS>
+__device__ __forceinline__ void store_tile_partials(const HoloDev &H, int pass, int t, int n0, int nc,
+                                                    const float2 *s_part)
+{
+    constexpr int W = THREADS / 32;
+    for (int q = threadIdx.x; q < nc; q += THREADS) {
+        const size_t o = (size_t)t * H.N + n0 + q;
+        if (pass == kPassFinal) {
+            double ar = 0.0, ai = 0.0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                float2 p = s_part[w * kSpotChunk + q];
+                ar += (double)p.x;
+                ai += (double)p.y;
+            }
+            H.part64[o] = make_double2(ar, ai);
+        } else {
+            float ar = 0.f, ai = 0.f;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                float2 p = s_part[w * kSpotChunk + q];
+                ar += p.x;
+                ai += p.y;
+            }
+            H.part[o] = make_float2(ar, ai);
+        }
+    }
+}
+
+// After a tile's partials are written: the last tile of this hologram's pass
+// (arrival counter) runs the update or the metrics, then resets the counter.
+template <int THREADS>
+__device__ __forceinline__ void finish_tile(const HoloDev &H, const LaunchSlot &sl, float2 *s_v, double *s_red,
+                                            int *s_last)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(H.counter, 1u);
+        *s_last = (prev == (unsigned)(sl.tiles - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*s_last) {
+        __threadfence();
+        if (sl.pass == kPassFinal) tail_metrics<THREADS>(H, sl, s_red);
+        else tail_update<THREADS>(H, sl, s_v, s_red);
+        __syncthreads();
+        if (threadIdx.x == 0) *H.counter = 0u;
+    }
+    __syncthreads();
+}
+
+// A tile of a compressed iteration: THREADS * PPT pixels of the subset S_j,
+// each phasor evaluated directly (fixed-point phase, hardware sine/cosine).
 template <int THREADS, int PPT>
 __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int maxN,
                              unsigned char *smem, double *s_red, int *s_last)
 {
-    constexpr int W = THREADS / 32;
-    int4 *s_coef = reinterpret_cast<int4 *>(smem);
-    uint2 *s_bw = reinterpret_cast<uint2 *>(s_coef + maxN);
-    float2 *s_v = reinterpret_cast<float2 *>(s_bw + maxN);
-    float2 *s_part = s_v + maxN;                       // W x kSpotChunk
-    float2 *s_wbuf = s_part + W * kSpotChunk;          // W x 32 x kWarpRow
-
+    const TileSmem m = tile_smem<THREADS>(smem, maxN);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int P = H.P, N = H.N;
     const int pass = sl.pass;
     const int count = sl.count;
 
-    // spot tables: fixed-point coefficients and (theta addend, w a0)
-    for (int n = tid; n < N; n += THREADS) {
-        s_coef[n] = H.coef[n];
-        SpotState st = H.state[n];
-        s_bw[n] = make_uint2(st.theta + kFixRound, __float_as_uint(st.w * st.a0));
-    }
+    load_spot_tables<THREADS>(H, m);
 
     // this thread's pixels
     SubsetKeys K = {0u, 0u, 0u, 0u};
@@ -148,15 +259,15 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         int idx = base + s * THREADS + tid;
         bool valid = idx < count;
         uint32_t k = valid ? (uint32_t)idx : 0u;
-        uint32_t m = pass == kPassSubset ? permute(k, (uint32_t)P, K) : k;
-        int r = (int)(m / (uint32_t)P);
-        int i = (int)m - r * P;
+        uint32_t mm = pass == kPassSubset ? permute(k, (uint32_t)P, K) : k;
+        int r = (int)(mm / (uint32_t)P);
+        int i = (int)mm - r * P;
         xp[s] = i - half;
         yp[s] = r - half;
         r2[s] = (uint32_t)(xp[s] * xp[s] + yp[s] * yp[s]);
         qf[s] = (float)r2[s];
         msk[s] = valid ? 1.f : 0.f;
-        mix[s] = valid ? (int)m : -1;
+        mix[s] = valid ? (int)mm : -1;
     }
     __syncthreads();
 
@@ -165,8 +276,8 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
 #pragma unroll
     for (int s = 0; s < PPT; ++s) { sr[s] = 0.f; si[s] = 0.f; }
     for (int n = 0; n < N; ++n) {
-        const int4 c = s_coef[n];
-        const uint2 bw = s_bw[n];
+        const int4 c = m.coef[n];
+        const uint2 bw = m.bw[n];
         const float wn = __uint_as_float(bw.y);
         const float gl = __int_as_float(c.w);
         const SpotFix f = {c.x, c.y, c.z, gl};
@@ -192,17 +303,17 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         }
     }
 
-    // forward projection, Eq. 3: conj of sum_m e^{i (phi_n(m) - Phi_m)}.
-    // Per spot each thread sums its PPT pixels; the warp's 32 partials of 16
-    // spots go through a transposed shared buffer (lane q sums spot q), the
-    // warps' totals through s_part, and one partial per (tile, spot) leaves.
-    float2 *wbuf = s_wbuf + warp * 32 * kWarpRow;
+    // forward projection, Eq. 3: each thread's phasor is e^{i (phi_n - Phi_m)},
+    // the conjugate of the term; per spot the thread sums its PPT pixels, the
+    // warp's partials go through the transpose buffer, the warps' totals
+    // through m.part, and one partial per (tile, spot) leaves.
+    float2 *wbuf = m.wbuf + warp * 32 * kWarpRow;
     for (int n0 = 0; n0 < N; n0 += kSpotChunk) {
         const int nc = min(kSpotChunk, N - n0);
         for (int q0 = 0; q0 < nc; q0 += kWarpChunk) {
             const int qc = min(kWarpChunk, nc - q0);
             for (int q = 0; q < qc; ++q) {
-                const int4 c = s_coef[n0 + q0 + q];
+                const int4 c = m.coef[n0 + q0 + q];
                 const float gl = __int_as_float(c.w);
                 const SpotFix f = {c.x, c.y, c.z, gl};
                 float vr = 0.f, vi = 0.f;
@@ -213,65 +324,186 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
                     vr = fmaf(msk[s], cs, vr);
                     vi = fmaf(msk[s], sn, vi);
                 }
-                wbuf[lane * kWarpRow + q] = make_float2(vr, vi);
+                wbuf[lane * kWarpRow + q] = make_float2(vr, -vi);
             }
             __syncwarp();
-            // lane = 16 h + q sums rows 16 h .. 16 h + 15 of column q
-            const int q = lane & (kWarpChunk - 1), h = lane >> 4;
-            float ar = 0.f, ai = 0.f;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                float2 p = wbuf[(h * 16 + i) * kWarpRow + q];
-                ar += p.x;
-                ai += p.y;
-            }
-            ar += __shfl_xor_sync(0xffffffffu, ar, 16);
-            ai += __shfl_xor_sync(0xffffffffu, ai, 16);
-            if (h == 0 && q < qc) s_part[warp * kSpotChunk + q0 + q] = make_float2(ar, -ai);
+            warp_transpose_reduce(wbuf, lane, qc, m.part + warp * kSpotChunk + q0);
             __syncwarp();
         }
         __syncthreads();
-        for (int q = tid; q < nc; q += THREADS) {
-            const size_t o = (size_t)t * N + n0 + q;
-            if (pass == kPassFinal) {
-                double ar = 0.0, ai = 0.0;
+        store_tile_partials<THREADS>(H, pass, t, n0, nc, m.part);
+        __syncthreads();
+    }
+    finish_tile<THREADS>(H, sl, m.v, s_red, s_last);
+}
+
+// One spot factor of a separable tile: e^{i 2 pi (c u + G u^2)} for pixel
+// coordinate u (x' with the tilt A, or y' with the tilt B) plus an addend,
+// scaled by w.  The fixed-point split is that of fix_phase.
+__device__ __forceinline__ float2 spot_factor(int32_t tilt, int32_t Gh, float gl, int32_t u, uint32_t addend, float w)
+{
+    const uint32_t u2 = (uint32_t)(u * u);
+    uint32_t T = addend + (uint32_t)tilt * (uint32_t)u;
+    T += (uint32_t)Gh * u2;
+    float s, c;
+    sincos_fix(T, fmaf(gl, (float)u2, -kTwoPiF), s, c);
+    return make_float2(w * c, w * s);
+}
+
+// A tile of a pass over all pixels (full iteration or final pass), using the
+// separability of the lens-and-prism phase (Eq. 2):
+//   e^{i phi_n(x', y')} = C_n(x') R_n(y'),  C_n = e^{i 2 pi (a x' + g x'^2)},
+//                                           R_n = e^{i 2 pi (b y' + g y'^2)}.
+// Over a rectangle of ROWS x 32 pixels the N spots need ROWS + 32 phasors each
+// instead of 32 ROWS.  Back-propagation (Eq. 1) is then
+//   S(x', y') = sum_n [w_n a_n e^{i theta_n} R_n(y')] C_n(x'),
+// one complex multiply-add per (pixel, spot), and the forward projection
+// (Eq. 3) is  V_n = sum_x' conj(C_n(x')) sum_y' e^{i Phi(x', y')} conj(R_n(y')).
+template <int THREADS>
+__device__ void process_full_tile(const HoloDev &H, const LaunchSlot &sl, int t, int maxN,
+                                  unsigned char *smem, double *s_red, int *s_last)
+{
+    constexpr int ROWS = THREADS / 4;
+    constexpr int COLS = kFullCols;
+    constexpr int NF = kFactorChunk;
+    const TileSmem m = tile_smem<THREADS>(smem, maxN);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int P = H.P, N = H.N, half = P >> 1;
+    const int pass = sl.pass;
+    const int col_tiles = (P + COLS - 1) / COLS;
+    const int y0 = (t / col_tiles) * ROWS, x0 = (t % col_tiles) * COLS;
+    const int tx = tid & 15, ty = tid >> 4;   // pixels: rows y0 + 4 ty + i, columns x0 + 2 tx + j
+    float2 *sR = m.fac;                 // NF x ROWS
+    float2 *sC = m.fac + NF * ROWS;     // NF x COLS
+
+    load_spot_tables<THREADS>(H, m);
+    __syncthreads();
+
+    // back-propagation, Eq. 1
+    float2 S[4][2];
 #pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    float2 p = s_part[w * kSpotChunk + q];
-                    ar += (double)p.x;
-                    ai += (double)p.y;
-                }
-                H.part64[o] = make_double2(ar, ai);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) S[i][j] = make_float2(0.f, 0.f);
+    for (int n0 = 0; n0 < N; n0 += NF) {
+        const int nc = min(NF, N - n0);
+        for (int f = tid; f < nc * (ROWS + COLS); f += THREADS) {
+            if (f < nc * ROWS) {
+                const int q = f / ROWS, r = f - q * ROWS;
+                const int4 c = m.coef[n0 + q];
+                const uint2 bw = m.bw[n0 + q];
+                sR[q * ROWS + r] = spot_factor(c.y, c.z, __int_as_float(c.w), y0 + r - half, bw.x,
+                                               __uint_as_float(bw.y));
             } else {
-                float ar = 0.f, ai = 0.f;
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    float2 p = s_part[w * kSpotChunk + q];
-                    ar += p.x;
-                    ai += p.y;
-                }
-                H.part[o] = make_float2(ar, ai);
+                const int g = f - nc * ROWS, q = g / COLS, x = g - q * COLS;
+                const int4 c = m.coef[n0 + q];
+                sC[q * COLS + x] = spot_factor(c.x, c.z, __int_as_float(c.w), x0 + x - half, kFixRound, 1.f);
             }
+        }
+        __syncthreads();
+        for (int q = 0; q < nc; ++q) {
+            const float4 r01 = *reinterpret_cast<const float4 *>(&sR[q * ROWS + 4 * ty]);
+            const float4 r23 = *reinterpret_cast<const float4 *>(&sR[q * ROWS + 4 * ty + 2]);
+            const float4 cc = *reinterpret_cast<const float4 *>(&sC[q * COLS + 2 * tx]);
+            const float2 R[4] = {make_float2(r01.x, r01.y), make_float2(r01.z, r01.w),
+                                 make_float2(r23.x, r23.y), make_float2(r23.z, r23.w)};
+            const float2 C[2] = {make_float2(cc.x, cc.y), make_float2(cc.z, cc.w)};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    S[i][j].x = fmaf(R[i].x, C[j].x, fmaf(-R[i].y, C[j].y, S[i][j].x));
+                    S[i][j].y = fmaf(R[i].x, C[j].y, fmaf(R[i].y, C[j].x, S[i][j].y));
+                }
         }
         __syncthreads();
     }
 
-    // the last tile of this hologram's pass runs the update / metrics
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        unsigned prev = atomicAdd(H.counter, 1u);
-        *s_last = (prev == (unsigned)(sl.tiles - 1)) ? 1 : 0;
+    // e^{i Phi} = S / |S| (arg 0 = 0); zero outside the grid so it adds nothing below
+    float2 U[4][2];
+    const bool vec_out = pass == kPassFinal && H.phase_out && (reinterpret_cast<uintptr_t>(H.phase_out) & 7) == 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = y0 + 4 * ty + i;
+        float o[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int col = x0 + 2 * tx + j;
+            const bool valid = row < P && col < P;
+            const float n2 = S[i][j].x * S[i][j].x + S[i][j].y * S[i][j].y;
+            if (!valid) U[i][j] = make_float2(0.f, 0.f);
+            else if (n2 > 0.f) {
+                const float rs = rsqrtf(n2);
+                U[i][j] = make_float2(S[i][j].x * rs, S[i][j].y * rs);
+            } else U[i][j] = make_float2(1.f, 0.f);
+            if (pass == kPassFinal) {
+                float ph = atan2f(S[i][j].y, S[i][j].x);
+                ph = ph < 0.f ? ph + kTwoPiF : ph;
+                o[j] = ph >= kTwoPiF ? 0.f : ph;
+            }
+        }
+        if (pass == kPassFinal && H.phase_out && row < P) {
+            const int col = x0 + 2 * tx;        // even, and P is even: both or neither in the grid
+            if (col < P) {
+                float *dst = H.phase_out + (size_t)row * P + col;
+                if (vec_out) *reinterpret_cast<float2 *>(dst) = make_float2(o[0], o[1]);
+                else { dst[0] = o[0]; dst[1] = o[1]; }
+            }
+        }
     }
-    __syncthreads();
-    if (*s_last) {
-        __threadfence();
-        if (pass == kPassFinal) tail_metrics<THREADS>(H, sl, s_red);
-        else tail_update<THREADS>(H, sl, s_v, s_red);
+
+    // forward projection, Eq. 3, reduced like the compressed tiles
+    float2 *wbuf = m.wbuf + warp * 32 * kWarpRow;
+    for (int w0 = 0; w0 < N; w0 += kSpotChunk) {
+        const int wc = min(kSpotChunk, N - w0);
+        for (int n0 = w0; n0 < w0 + wc; n0 += NF) {
+            const int nc = min(NF, w0 + wc - n0);
+            for (int f = tid; f < nc * (ROWS + COLS); f += THREADS) {
+                if (f < nc * ROWS) {
+                    const int q = f / ROWS, r = f - q * ROWS;
+                    const int4 c = m.coef[n0 + q];
+                    sR[q * ROWS + r] = spot_factor(c.y, c.z, __int_as_float(c.w), y0 + r - half, kFixRound, 1.f);
+                } else {
+                    const int g = f - nc * ROWS, q = g / COLS, x = g - q * COLS;
+                    const int4 c = m.coef[n0 + q];
+                    sC[q * COLS + x] = spot_factor(c.x, c.z, __int_as_float(c.w), x0 + x - half, kFixRound, 1.f);
+                }
+            }
+            __syncthreads();
+            for (int q0 = 0; q0 < nc; q0 += kWarpChunk) {
+                const int qc = min(kWarpChunk, nc - q0);
+                for (int q = 0; q < qc; ++q) {
+                    const int qq = q0 + q;
+                    const float4 r01 = *reinterpret_cast<const float4 *>(&sR[qq * ROWS + 4 * ty]);
+                    const float4 r23 = *reinterpret_cast<const float4 *>(&sR[qq * ROWS + 4 * ty + 2]);
+                    const float4 cc = *reinterpret_cast<const float4 *>(&sC[qq * COLS + 2 * tx]);
+                    const float2 R[4] = {make_float2(r01.x, r01.y), make_float2(r01.z, r01.w),
+                                         make_float2(r23.x, r23.y), make_float2(r23.z, r23.w)};
+                    float vr = 0.f, vi = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        float a = 0.f, b = 0.f;             // sum_i U conj(R_i)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            a = fmaf(U[i][j].x, R[i].x, fmaf(U[i][j].y, R[i].y, a));
+                            b = fmaf(U[i][j].y, R[i].x, fmaf(-U[i][j].x, R[i].y, b));
+                        }
+                        const float cr = j ? cc.z : cc.x, ci = j ? cc.w : cc.y;   // times conj(C_j)
+                        vr = fmaf(a, cr, fmaf(b, ci, vr));
+                        vi = fmaf(b, cr, fmaf(-a, ci, vi));
+                    }
+                    wbuf[lane * kWarpRow + q] = make_float2(vr, vi);
+                }
+                __syncwarp();
+                warp_transpose_reduce(wbuf, lane, qc, m.part + warp * kSpotChunk + (n0 - w0) + q0);
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        store_tile_partials<THREADS>(H, pass, t, w0, wc, m.part);
         __syncthreads();
-        if (tid == 0) *H.counter = 0u;
     }
-    __syncthreads();
+    finish_tile<THREADS>(H, sl, m.v, s_red, s_last);
 }
 
 // Spot preparation (step 1 of the path) for spot n of hologram H: fixed-point
@@ -290,12 +522,14 @@ __device__ __forceinline__ void prep_spot(const HoloDev &H, int n)
     H.state[n] = st;
 }
 
-// Dynamic shared memory of process_tile for THREADS threads and up to maxN spots.
-__host__ __device__ constexpr size_t tile_smem_bytes(int threads, int maxN)
+// Dynamic shared memory of the tile processors for THREADS threads and up to
+// maxN spots (the layout of TileSmem; the factor buffer only for full passes).
+__host__ __device__ constexpr size_t tile_smem_bytes(int threads, int maxN, bool factors)
 {
     return (size_t)maxN * (sizeof(int4) + sizeof(uint2) + sizeof(float2)) +
            (size_t)(threads / 32) * kSpotChunk * sizeof(float2) +
-           (size_t)(threads / 32) * 32 * kWarpRow * sizeof(float2);
+           (size_t)(threads / 32) * 32 * kWarpRow * sizeof(float2) +
+           (factors ? (size_t)kFactorChunk * (threads / 4 + kFullCols) * sizeof(float2) : 0);
 }
 
 }  // namespace cswgs

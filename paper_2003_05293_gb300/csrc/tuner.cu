@@ -1,9 +1,10 @@
-// Autotuner of the FP32 iteration kernel's tile shape (threads per block,
-// pixels per thread).  Key: (largest P rounded up to 128, work-weighted spot
+// Autotuner of the FP32 iteration kernels' tile shapes (compressed
+// iterations: threads per block and pixels per thread; full passes: threads
+// per block).  Key: (largest P rounded up to 128, work-weighted spot
 // count rounded up to a power of two, batch size rounded up to a power of
 // two).  Each candidate runs a synthetic batch of that key's size (one
-// compressed iteration, one full iteration, the final pass) and the shape with
-// the least schedule-weighted time wins.  Results live in the plan and,
+// compressed iteration, one full iteration, the final pass); the fastest
+// compressed-iteration shape and the fastest full-pass shape win.  Results live in the plan and,
 // when the plan names a cache file, in a small JSON file.
 #include <algorithm>
 #include <cmath>
@@ -56,8 +57,12 @@ std::string tune_key(const std::vector<HoloSpec> &specs)
     return buf;
 }
 
-static const TileShape kCandidates[] = {{128, 4}, {128, 8}, {256, 2}, {256, 4}, {256, 8},
-                                        {512, 2}, {512, 4}};
+// Candidates: compressed-iteration kernel (threads, pixels per thread) and
+// full-pass kernel (threads); the two kernels run as separate launches, so
+// each is tuned on its own launches.
+static const int kSubCandidates[][2] = {{128, 2}, {128, 4}, {128, 8}, {256, 2}, {256, 4},
+                                        {256, 8}, {512, 1}, {512, 2}, {512, 4}};
+static const int kFullCandidates[] = {128, 256, 512};
 
 static std::vector<HoloSpec> synthetic(const TuneKey &k, double c)
 {
@@ -83,24 +88,24 @@ static std::vector<HoloSpec> synthetic(const TuneKey &k, double c)
     return v;
 }
 
-static cswgs_status time_shape(cswgs_plan_s *p, const std::vector<HoloSpec> &specs, TileShape sh,
-                               double weight_sub, double weight_full, double *ms_out)
+// Best-of-two device times of the synthetic schedule's three steps: a
+// compressed iteration, a full iteration and the final pass.
+static cswgs_status time_steps(cswgs_plan_s *p, const std::vector<HoloSpec> &specs, TileShape sh, double t[3])
 {
     std::unique_ptr<Fp32Batch> b;
     CSWGS_TRY(batch_build_with(p, specs, sh, &b));
     CSWGS_TRY(batch_upload_inputs(b.get(), p->stream));
-    double best = 1e30;
+    for (int i = 0; i < 3; ++i) t[i] = 1e30;
     for (int rep = 0; rep < 3; ++rep) {
         CSWGS_TRY(batch_enqueue_direct(b.get(), p->stream));
         CSWGS_CUDA_TRY(cudaStreamSynchronize(p->stream));
-        float t_sub = 0.f, t_full = 0.f, t_fin = 0.f;
-        CSWGS_CUDA_TRY(cudaEventElapsedTime(&t_sub, b->events[1], b->events[2]));
-        CSWGS_CUDA_TRY(cudaEventElapsedTime(&t_full, b->events[2], b->events[3]));
-        CSWGS_CUDA_TRY(cudaEventElapsedTime(&t_fin, b->events[3], b->events[4]));
-        double t = weight_sub * t_sub + weight_full * t_full + t_fin;
-        if (rep > 0) best = std::min(best, t);   // first run warms up
+        if (rep == 0) continue;   // warm-up
+        for (int i = 0; i < 3; ++i) {
+            float ms = 0.f;
+            CSWGS_CUDA_TRY(cudaEventElapsedTime(&ms, b->events[1 + i], b->events[2 + i]));
+            t[i] = std::min(t[i], (double)ms);
+        }
     }
-    *ms_out = best;
     return CSWGS_OK;
 }
 
@@ -108,20 +113,30 @@ static cswgs_status tune_for(cswgs_plan_s *p, const TuneKey &k, double c, double
                              TileShape *best_shape, double *best_ms)
 {
     std::vector<HoloSpec> specs = synthetic(k, c);
-    double best = 1e30;
-    TileShape bs{256, 4};
-    for (const TileShape &sh : kCandidates) {
-        if (iter_fp32_max_grid(sh, k.N, p->sm_count) <= 0) continue;
-        double ms;
-        cswgs_status st = time_shape(p, specs, sh, wsub, wfull, &ms);
-        if (st != CSWGS_OK) return st;
-        if (ms < best) {
-            best = ms;
-            bs = sh;
+    TileShape best{256, 4, 256};
+    double best_sub = 1e30, best_full = 1e30, t[3];
+    for (const auto &cand : kSubCandidates) {
+        TileShape sh{cand[0], cand[1], best.full_threads};
+        if (iter_fp32_max_grid(sh, kLaunchSubset, k.N, p->sm_count) <= 0) continue;
+        CSWGS_TRY(time_steps(p, specs, sh, t));
+        if (t[0] < best_sub) {
+            best_sub = t[0];
+            best.threads = cand[0];
+            best.ppt = cand[1];
         }
     }
-    *best_shape = bs;
-    if (best_ms) *best_ms = best;
+    for (int ft : kFullCandidates) {
+        TileShape sh{best.threads, best.ppt, ft};
+        if (iter_fp32_max_grid(sh, kLaunchFull, k.N, p->sm_count) <= 0) continue;
+        CSWGS_TRY(time_steps(p, specs, sh, t));
+        const double tf = wfull * t[1] + t[2];
+        if (tf < best_full) {
+            best_full = tf;
+            best.full_threads = ft;
+        }
+    }
+    *best_shape = best;
+    if (best_ms) *best_ms = wsub * best_sub + best_full;
     return CSWGS_OK;
 }
 
@@ -142,7 +157,7 @@ TileShape tuned_shape(cswgs_plan_s *p, const std::vector<HoloSpec> &specs)
         wsub /= specs.size();
         wfull /= specs.size();
     }
-    TileShape sh{256, 4};
+    TileShape sh{256, 4, 256};
     double ms = 0.0;
     if (tune_for(p, key_of(specs), c, wsub, wfull, &sh, &ms) == CSWGS_OK) {
         p->tune[key] = sh;
@@ -176,7 +191,7 @@ void tune_load(cswgs_plan_s *p)
     std::stringstream ss;
     ss << f.rdbuf();
     std::string s = ss.str();
-    // entries look like "P1152_N128_B64": [256, 4]
+    // entries look like "P1152_N128_B64": [256, 4, 128]
     size_t pos = 0;
     while ((pos = s.find('"', pos)) != std::string::npos) {
         size_t end = s.find('"', pos + 1);
@@ -184,9 +199,9 @@ void tune_load(cswgs_plan_s *p)
         std::string key = s.substr(pos + 1, end - pos - 1);
         pos = end + 1;
         if (key.empty() || key[0] != 'P') continue;
-        int t = 0, k = 0;
-        if (sscanf(s.c_str() + pos, " : [ %d , %d ]", &t, &k) == 2 && tile_shape_supported(TileShape{t, k}))
-            p->tune[key] = TileShape{t, k};
+        int t = 0, k = 0, f = 0;
+        if (sscanf(s.c_str() + pos, " : [ %d , %d , %d ]", &t, &k, &f) == 3 && tile_shape_supported(TileShape{t, k, f}))
+            p->tune[key] = TileShape{t, k, f};
     }
 }
 
@@ -196,11 +211,11 @@ void tune_save(cswgs_plan_s *p)
     std::string tmp = p->tune_path + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
     if (!f) return;
-    fprintf(f, "{\n  \"format\": \"cswgs-tune-1\",\n  \"entries\": {");
+    fprintf(f, "{\n  \"format\": \"cswgs-tune-2\",\n  \"entries\": {");
     bool first = true;
     for (auto &kv : p->tune) {
-        fprintf(f, "%s\n    \"%s\": [%d, %d]", first ? "" : ",", kv.first.c_str(), kv.second.threads,
-                kv.second.ppt);
+        fprintf(f, "%s\n    \"%s\": [%d, %d, %d]", first ? "" : ",", kv.first.c_str(), kv.second.threads,
+                kv.second.ppt, kv.second.full_threads);
         first = false;
     }
     fprintf(f, "\n  }\n}\n");
