@@ -186,7 +186,11 @@ def main():
 
     pbs = problems(args, rank)
     B = len(pbs)
-    stream = torch.cuda.current_stream()
+    # one non-default stream for everything: the plan's kernels, the L2 flush
+    # and the timing events (the legacy default stream has handle 0, which
+    # would make the plan create a stream of its own)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     plan = Plan(device=local, precision="fp32", max_batch=max(64, B), max_N=max(1024, args.N),
                 stream=stream.cuda_stream, tune_cache=args.tune_cache)
     outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
@@ -195,34 +199,36 @@ def main():
     tile = batch.tile_shape()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
-    for _ in range(args.warmup):
+    for _ in range(args.warmup):          # the same work as a timed step (loads every kernel)
+        flush.fill_(1)
         batch.run()
         batch.results()
 
+    # timed region: K steps queued back to back on one stream (an L2 flush
+    # before each), a CUDA event after each; one synchronisation at the end
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    step_ms, kts = [], []
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev0.record(stream)
-    t_wall = time.perf_counter()
-    for _ in range(args.steps):
+    for k in range(args.steps):
         flush.fill_(1)                       # evict L2 between steps
         batch.run()                          # graph launch on the same stream
-        res = batch.results()                # waits for the step
-        kt = batch.kernel_times()            # prep, then one entry per persistent launch
-        step_ms.append(sum(kt))
-        kts.append(kt)
-    ev1.record(stream)
+        step_ev[k].record(stream)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
     barrier()
     clk = clocks.stop()
-    total_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    total_ms = max_over_ranks(ev0.elapsed_time(step_ev[-1]))
     value = B * world * args.steps / (total_ms * 1e-3)
+    res = batch.results()
+    # per-step device time (flush + graph) from consecutive events
+    step_ms = [ev0.elapsed_time(step_ev[0])] + [step_ev[k - 1].elapsed_time(step_ev[k])
+                                                 for k in range(1, args.steps)]
+    # per-launch device times of the last timed step (events inside the graph)
+    kts = [batch.kernel_times()]
 
     # rooflines of the iteration kernel, per launch kind (measured live, CUDA
     # events around every launch of every timed step):
@@ -243,8 +249,8 @@ def main():
     Mp = math.floor(args.c * args.P * args.P)
     pairs_sub_launch = B * 2.0 * args.N * Mp
     pairs_full_launch = B * 2.0 * args.N * args.P * args.P
-    sub_ms = sum(sum(k[1:1 + n_sub]) for k in kts) / args.steps
-    full_ms = sum(sum(k[1 + n_sub:]) for k in kts) / args.steps
+    sub_ms = sum(sum(k[1:1 + n_sub]) for k in kts) / len(kts)
+    full_ms = sum(sum(k[1 + n_sub:]) for k in kts) / len(kts)
     n_full_launches = len(kts[0]) - 1 - n_sub
     sfu_peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9           # G sin-or-cos/s
     fma_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12       # TFLOP/s
@@ -259,7 +265,9 @@ def main():
             "config": workload_config(args, {"l2": "flushed between steps (256 MB write), inside the timed region",
                                              "parallelism": "replicas" if world > 1 else "single GPU"}),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                           "what": "batch step = every hologram of the batch, submit to result"},
+                           "steps": [round(x, 3) for x in step_ms],
+                           "what": "device time of one batch step (L2 flush + whole hot path for every hologram "
+                                   "of the batch): a hologram submitted with its batch is done after it"},
             "quality": {"e_mean": float(np.mean([a for a, _ in eu])), "u_mean": float(np.mean([b for _, b in eu])),
                         "u_min": float(np.min([b for _, b in eu])), "e_min": float(np.min([a for a, _ in eu]))},
             "roofline": {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": sfu_achieved, "peak": sfu_peak,
@@ -279,8 +287,9 @@ def main():
                                                    % (sm_count, FP32_LANES_PER_SM, max_mhz),
                                      "ms_per_launch": full_ms / max(1, n_full_launches),
                                      "tile": {"threads": tile["full_threads"], "blocks": tile["full_blocks"],
-                                              "pixels": "threads/4 rows x 32 columns, 4 x 2 per thread"}},
+                                              "pixels": "threads/4 rows x 64 columns, 4 x 4 per thread"}},
             "gpu_launches": args.steps * len(kts[0]),
+            "kernel_times_from": "CUDA events recorded inside the graph around each launch, last timed step",
             "clocks": clk}
 
     # FP64 GPU baseline (plain double-precision kernels), one hologram at a time

@@ -54,7 +54,11 @@ def _out_ptr(out):
 
 
 class Plan:
-    """A cswgs_plan: device, stream, limits, precision, tunings and serving loop."""
+    """A cswgs_plan: device, stream, limits, precision, tunings and serving loop.
+
+    stream: a cudaStream_t handle (e.g. ``torch.cuda.Stream().cuda_stream``) the
+    plan runs on, or None/0 for a stream of the plan's own.  torch's default
+    stream has handle 0, so pass a non-default torch stream to share one."""
 
     def __init__(self, device: int = 0, max_P: int = 2048, max_N: int = 1024, max_batch: int = 64,
                  mem_cap_bytes: int = 0, precision: str = "fp32", stream=None, tune_cache=None):

@@ -112,17 +112,23 @@ constexpr int kWarpChunk = 16;
 constexpr int kWarpRow = kWarpChunk + 1;
 
 // Separable full-pass tiles: THREADS / 4 rows x kFullCols columns, each thread
-// a 4 x 2 block of pixels (16 threads across a row of the tile, so every
-// factor load is a broadcast or a contiguous 256-byte row); spot factors are
-// made kFactorChunk spots at a time.
-constexpr int kFullCols = 32;
-constexpr int kFactorChunk = 32;
+// a 4 x 4 block of pixels (16 threads across a row of the tile).  Row factors
+// are stored in row order (a thread's 4 rows: two 16-byte loads, broadcast to
+// the 16 threads of its row); column factors are interleaved so that the
+// 16-byte halves of each thread's 4 columns sit side by side (every load is a
+// contiguous 256-byte row).  Spot factors are made kFactorChunk spots at a time.
+constexpr int kFullCols = 64;
+constexpr int kFactorChunk = 16;
 
 __host__ __device__ inline int full_pass_tiles(int P, int threads)
 {
     const int rows = threads / 4;
     return ((P + rows - 1) / rows) * ((P + kFullCols - 1) / kFullCols);
 }
+
+// Position of column x (0..63) of a spot's column factors: 16-byte half h of
+// thread x / 4 at float2 index 32 h + 2 (x / 4) + (x % 2).
+__host__ __device__ constexpr int col_slot(int x) { return 32 * ((x >> 1) & 1) + 2 * (x >> 2) + (x & 1); }
 
 // Shared-memory layout of a tile (both tile processors).
 struct TileSmem {
@@ -354,8 +360,8 @@ __device__ __forceinline__ float2 spot_factor(int32_t tilt, int32_t Gh, float gl
 // separability of the lens-and-prism phase (Eq. 2):
 //   e^{i phi_n(x', y')} = C_n(x') R_n(y'),  C_n = e^{i 2 pi (a x' + g x'^2)},
 //                                           R_n = e^{i 2 pi (b y' + g y'^2)}.
-// Over a rectangle of ROWS x 32 pixels the N spots need ROWS + 32 phasors each
-// instead of 32 ROWS.  Back-propagation (Eq. 1) is then
+// Over a rectangle of ROWS x 64 pixels the N spots need ROWS + 64 phasors each
+// instead of 64 ROWS.  Back-propagation (Eq. 1) is then
 //   S(x', y') = sum_n [w_n a_n e^{i theta_n} R_n(y')] C_n(x'),
 // one complex multiply-add per (pixel, spot), and the forward projection
 // (Eq. 3) is  V_n = sum_x' conj(C_n(x')) sum_y' e^{i Phi(x', y')} conj(R_n(y')).
@@ -372,46 +378,60 @@ __device__ void process_full_tile(const HoloDev &H, const LaunchSlot &sl, int t,
     const int pass = sl.pass;
     const int col_tiles = (P + COLS - 1) / COLS;
     const int y0 = (t / col_tiles) * ROWS, x0 = (t % col_tiles) * COLS;
-    const int tx = tid & 15, ty = tid >> 4;   // pixels: rows y0 + 4 ty + i, columns x0 + 2 tx + j
+    const int tx = tid & 15, ty = tid >> 4;   // pixels: rows y0 + 4 ty + i, columns x0 + 4 tx + j
     float2 *sR = m.fac;                 // NF x ROWS
-    float2 *sC = m.fac + NF * ROWS;     // NF x COLS
+    float2 *sC = m.fac + NF * ROWS;     // NF x COLS, interleaved (col_slot)
 
     load_spot_tables<THREADS>(H, m);
     __syncthreads();
 
-    // back-propagation, Eq. 1
-    float2 S[4][2];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) S[i][j] = make_float2(0.f, 0.f);
-    for (int n0 = 0; n0 < N; n0 += NF) {
-        const int nc = min(NF, N - n0);
+    // spot factors of spots n0 .. n0 + nc - 1 into sR, sC; the row factors
+    // carry w_n a_n e^{i theta_n} when `weighted`
+    auto make_factors = [&](int n0, int nc, bool weighted) {
         for (int f = tid; f < nc * (ROWS + COLS); f += THREADS) {
             if (f < nc * ROWS) {
                 const int q = f / ROWS, r = f - q * ROWS;
                 const int4 c = m.coef[n0 + q];
                 const uint2 bw = m.bw[n0 + q];
-                sR[q * ROWS + r] = spot_factor(c.y, c.z, __int_as_float(c.w), y0 + r - half, bw.x,
-                                               __uint_as_float(bw.y));
+                sR[q * ROWS + r] = spot_factor(c.y, c.z, __int_as_float(c.w), y0 + r - half,
+                                               weighted ? bw.x : kFixRound,
+                                               weighted ? __uint_as_float(bw.y) : 1.f);
             } else {
                 const int g = f - nc * ROWS, q = g / COLS, x = g - q * COLS;
                 const int4 c = m.coef[n0 + q];
-                sC[q * COLS + x] = spot_factor(c.x, c.z, __int_as_float(c.w), x0 + x - half, kFixRound, 1.f);
+                sC[q * COLS + col_slot(x)] =
+                    spot_factor(c.x, c.z, __int_as_float(c.w), x0 + x - half, kFixRound, 1.f);
             }
         }
+    };
+    auto load_factors = [&](int q, float2 R[4], float2 C[4]) {
+        const float4 r01 = *reinterpret_cast<const float4 *>(&sR[q * ROWS + 4 * ty]);
+        const float4 r23 = *reinterpret_cast<const float4 *>(&sR[q * ROWS + 4 * ty + 2]);
+        const float4 c01 = *reinterpret_cast<const float4 *>(&sC[q * COLS + 2 * tx]);
+        const float4 c23 = *reinterpret_cast<const float4 *>(&sC[q * COLS + 32 + 2 * tx]);
+        R[0] = make_float2(r01.x, r01.y); R[1] = make_float2(r01.z, r01.w);
+        R[2] = make_float2(r23.x, r23.y); R[3] = make_float2(r23.z, r23.w);
+        C[0] = make_float2(c01.x, c01.y); C[1] = make_float2(c01.z, c01.w);
+        C[2] = make_float2(c23.x, c23.y); C[3] = make_float2(c23.z, c23.w);
+    };
+
+    // back-propagation, Eq. 1
+    float2 S[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) S[i][j] = make_float2(0.f, 0.f);
+    for (int n0 = 0; n0 < N; n0 += NF) {
+        const int nc = min(NF, N - n0);
+        make_factors(n0, nc, true);
         __syncthreads();
         for (int q = 0; q < nc; ++q) {
-            const float4 r01 = *reinterpret_cast<const float4 *>(&sR[q * ROWS + 4 * ty]);
-            const float4 r23 = *reinterpret_cast<const float4 *>(&sR[q * ROWS + 4 * ty + 2]);
-            const float4 cc = *reinterpret_cast<const float4 *>(&sC[q * COLS + 2 * tx]);
-            const float2 R[4] = {make_float2(r01.x, r01.y), make_float2(r01.z, r01.w),
-                                 make_float2(r23.x, r23.y), make_float2(r23.z, r23.w)};
-            const float2 C[2] = {make_float2(cc.x, cc.y), make_float2(cc.z, cc.w)};
+            float2 R[4], C[4];
+            load_factors(q, R, C);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < 4; ++j) {
                     S[i][j].x = fmaf(R[i].x, C[j].x, fmaf(-R[i].y, C[j].y, S[i][j].x));
                     S[i][j].y = fmaf(R[i].x, C[j].y, fmaf(R[i].y, C[j].x, S[i][j].y));
                 }
@@ -419,35 +439,39 @@ __device__ void process_full_tile(const HoloDev &H, const LaunchSlot &sl, int t,
         __syncthreads();
     }
 
-    // e^{i Phi} = S / |S| (arg 0 = 0); zero outside the grid so it adds nothing below
-    float2 U[4][2];
-    const bool vec_out = pass == kPassFinal && H.phase_out && (reinterpret_cast<uintptr_t>(H.phase_out) & 7) == 0;
+    // e^{i Phi} = S / |S| (arg 0 = 0), kept in S; zero outside the grid so it adds
+    // nothing below.  The final pass writes Phi.
+    const bool vec_out = pass == kPassFinal && H.phase_out && (P & 3) == 0 &&
+                         (reinterpret_cast<uintptr_t>(H.phase_out) & 15) == 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int row = y0 + 4 * ty + i;
-        float o[2];
+        float o[4];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int col = x0 + 2 * tx + j;
+        for (int j = 0; j < 4; ++j) {
+            const int col = x0 + 4 * tx + j;
             const bool valid = row < P && col < P;
             const float n2 = S[i][j].x * S[i][j].x + S[i][j].y * S[i][j].y;
-            if (!valid) U[i][j] = make_float2(0.f, 0.f);
-            else if (n2 > 0.f) {
-                const float rs = rsqrtf(n2);
-                U[i][j] = make_float2(S[i][j].x * rs, S[i][j].y * rs);
-            } else U[i][j] = make_float2(1.f, 0.f);
             if (pass == kPassFinal) {
                 float ph = atan2f(S[i][j].y, S[i][j].x);
                 ph = ph < 0.f ? ph + kTwoPiF : ph;
                 o[j] = ph >= kTwoPiF ? 0.f : ph;
             }
+            if (!valid) S[i][j] = make_float2(0.f, 0.f);
+            else if (n2 > 0.f) {
+                const float rs = rsqrtf(n2);
+                S[i][j] = make_float2(S[i][j].x * rs, S[i][j].y * rs);
+            } else S[i][j] = make_float2(1.f, 0.f);
         }
         if (pass == kPassFinal && H.phase_out && row < P) {
-            const int col = x0 + 2 * tx;        // even, and P is even: both or neither in the grid
-            if (col < P) {
-                float *dst = H.phase_out + (size_t)row * P + col;
-                if (vec_out) *reinterpret_cast<float2 *>(dst) = make_float2(o[0], o[1]);
-                else { dst[0] = o[0]; dst[1] = o[1]; }
+            const int col = x0 + 4 * tx;
+            float *dst = H.phase_out + (size_t)row * P + col;
+            if (vec_out && col + 3 < P) {
+                *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (col + j < P) dst[j] = o[j];
             }
         }
     }
@@ -457,47 +481,28 @@ __device__ void process_full_tile(const HoloDev &H, const LaunchSlot &sl, int t,
     for (int w0 = 0; w0 < N; w0 += kSpotChunk) {
         const int wc = min(kSpotChunk, N - w0);
         for (int n0 = w0; n0 < w0 + wc; n0 += NF) {
-            const int nc = min(NF, w0 + wc - n0);
-            for (int f = tid; f < nc * (ROWS + COLS); f += THREADS) {
-                if (f < nc * ROWS) {
-                    const int q = f / ROWS, r = f - q * ROWS;
-                    const int4 c = m.coef[n0 + q];
-                    sR[q * ROWS + r] = spot_factor(c.y, c.z, __int_as_float(c.w), y0 + r - half, kFixRound, 1.f);
-                } else {
-                    const int g = f - nc * ROWS, q = g / COLS, x = g - q * COLS;
-                    const int4 c = m.coef[n0 + q];
-                    sC[q * COLS + x] = spot_factor(c.x, c.z, __int_as_float(c.w), x0 + x - half, kFixRound, 1.f);
-                }
-            }
+            const int nc = min(NF, w0 + wc - n0);   // NF == kWarpChunk: one transpose round
+            make_factors(n0, nc, false);
             __syncthreads();
-            for (int q0 = 0; q0 < nc; q0 += kWarpChunk) {
-                const int qc = min(kWarpChunk, nc - q0);
-                for (int q = 0; q < qc; ++q) {
-                    const int qq = q0 + q;
-                    const float4 r01 = *reinterpret_cast<const float4 *>(&sR[qq * ROWS + 4 * ty]);
-                    const float4 r23 = *reinterpret_cast<const float4 *>(&sR[qq * ROWS + 4 * ty + 2]);
-                    const float4 cc = *reinterpret_cast<const float4 *>(&sC[qq * COLS + 2 * tx]);
-                    const float2 R[4] = {make_float2(r01.x, r01.y), make_float2(r01.z, r01.w),
-                                         make_float2(r23.x, r23.y), make_float2(r23.z, r23.w)};
-                    float vr = 0.f, vi = 0.f;
+            for (int q = 0; q < nc; ++q) {
+                float2 R[4], C[4];
+                load_factors(q, R, C);
+                float vr = 0.f, vi = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        float a = 0.f, b = 0.f;             // sum_i U conj(R_i)
+                for (int j = 0; j < 4; ++j) {
+                    float a = 0.f, b = 0.f;             // sum_i e^{i Phi} conj(R_i)
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            a = fmaf(U[i][j].x, R[i].x, fmaf(U[i][j].y, R[i].y, a));
-                            b = fmaf(U[i][j].y, R[i].x, fmaf(-U[i][j].x, R[i].y, b));
-                        }
-                        const float cr = j ? cc.z : cc.x, ci = j ? cc.w : cc.y;   // times conj(C_j)
-                        vr = fmaf(a, cr, fmaf(b, ci, vr));
-                        vi = fmaf(b, cr, fmaf(-a, ci, vi));
+                    for (int i = 0; i < 4; ++i) {
+                        a = fmaf(S[i][j].x, R[i].x, fmaf(S[i][j].y, R[i].y, a));
+                        b = fmaf(S[i][j].y, R[i].x, fmaf(-S[i][j].x, R[i].y, b));
                     }
-                    wbuf[lane * kWarpRow + q] = make_float2(vr, vi);
+                    vr = fmaf(a, C[j].x, fmaf(b, C[j].y, vr));   // times conj(C_j)
+                    vi = fmaf(b, C[j].x, fmaf(-a, C[j].y, vi));
                 }
-                __syncwarp();
-                warp_transpose_reduce(wbuf, lane, qc, m.part + warp * kSpotChunk + (n0 - w0) + q0);
-                __syncwarp();
+                wbuf[lane * kWarpRow + q] = make_float2(vr, vi);
             }
+            __syncwarp();
+            warp_transpose_reduce(wbuf, lane, nc, m.part + warp * kSpotChunk + (n0 - w0));
             __syncthreads();
         }
         store_tile_partials<THREADS>(H, pass, t, w0, wc, m.part);
