@@ -37,11 +37,25 @@ import workloads  # noqa: E402
 METRIC = "holograms/s and p50/p99 latency at M=1152^2, N=100, e,u>=0.9 vs FP64 GPU baseline"
 SFU_PER_CLK_PER_SM = 16       # sine/cosine results per clock per SM (CUDA arithmetic throughput table)
 FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
-# DRAM bytes (read + write) per launch of the iteration kernel at this workload,
-# from an ncu capture of this bench (profiles/iter_kernel_b64_launches.md), or
-# None once the kernel has changed since the counters were taken.
-TRAFFIC_SUB = None
-TRAFFIC_FULL = None
+# DRAM bytes (read + write) per launch of the iteration kernels at the default
+# workload, from one ncu capture of this bench
+# (profiles/iter_kernels_b64_P1152_N100_launches.md): compressed launches, and
+# full-pixel launches (2 full iterations + the final pass, averaged).  Reported
+# only while the kernel sources hash to the value they had when measured.
+TRAFFIC_MEASURED = {"kernel_sha": "b50bed129f650127", "sub": 311040, "full": 104178858}
+KERNEL_SOURCES = ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu")
+
+
+def measured_traffic(args):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2003_05293_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    default = (args.batch, args.P, args.N, args.c, args.iters) == (64, 1152, 100, 0.125, 30)
+    if not default or h.hexdigest()[:16] != TRAFFIC_MEASURED["kernel_sha"]:
+        return None, None
+    return TRAFFIC_MEASURED["sub"], TRAFFIC_MEASURED["full"]
 
 
 def parse():
@@ -257,6 +271,7 @@ def main():
     sfu_achieved = 2.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e9 if n_sub else 0.0
     fma_achieved = 8.0 * pairs_full_launch * n_full_launches / (full_ms * 1e-3) / 1e12
     probe, probe_mhz = plan.sincos_peak()
+    TRAFFIC_SUB, TRAFFIC_FULL = measured_traffic(args)
 
     eu = [(r["e"], r["u"]) for r in res]
     line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
