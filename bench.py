@@ -74,12 +74,36 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (read, and written when tuning)")
+    ap.add_argument("--serve-rate", type=float, default=1000.0, help="Poisson arrival rate of the serving probe")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving probe's arrival stream")
+    ap.add_argument("--serve-mix", action="store_true",
+                    help="serve the mixed stream (P in {768,1024,1152}, N in {10,100,1000}, gamma +-20, 20 "
+                         "iterations) instead of the headline holograms")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
 def problems(args, rank):
+    """This rank's share of the job: its own batch of holograms (seeds never shared
+    between ranks), so the work scales with the number of GPUs (weak scaling)."""
     return [workloads.problem(args.P, args.N, 10.0, args.c, args.iters, seed=rank * 100000 + h)
             for h in range(args.batch)]
+
+
+def max_over_ranks(x, world, device):
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(per_rank_holograms, world, steps, slowest_ms):
+    """Whole-job holograms/s: every rank's holograms over the slowest rank's time."""
+    return per_rank_holograms * world * steps / (slowest_ms * 1e-3)
 
 
 def workload_config(args, extra=None):
@@ -139,6 +163,76 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ------------------------------------------------------------- serving --
+def serve_probe(args, local, stream_handle):
+    """Continuous batching under a Poisson arrival stream: requests are submitted
+    at their arrival times (cswgs_submit) and collected as they finish
+    (cswgs_wait); returns throughput and submit-to-result latency."""
+    import queue
+    import threading
+
+    import torch
+
+    from paper_2003_05293_gb300 import Plan
+
+    if args.serve_mix:
+        stream = workloads.arrivals(args.serve_rate, args.serve_seconds, seed=7)
+        what = "mixed: P in {768,1024,1152}, N in {10,100,1000}, gamma~U[-20,20], c=1/8, 20 iterations"
+    else:
+        rng = np.random.Generator(np.random.PCG64(7))
+        t, stream = 0.0, []
+        while True:
+            t += float(rng.exponential(1.0 / args.serve_rate))
+            if t >= args.serve_seconds:
+                break
+            stream.append((t, workloads.problem(args.P, args.N, 10.0, args.c, args.iters, seed=10**6 + len(stream))))
+        what = "P=%d, N=%d, c=%g, %d iterations (the batch workload's holograms)" % (args.P, args.N, args.c, args.iters)
+    maxP = max(pb.P for _, pb in stream)
+    nbuf = 192
+    bufs = [torch.empty(maxP * maxP, dtype=torch.float32, device="cuda") for _ in range(nbuf)]
+    free = queue.Queue()
+    for i in range(nbuf):
+        free.put(i)
+    plan = Plan(device=local, precision="fp32", max_batch=64, max_N=1024, max_P=max(2048, maxP))
+    # warm the serving path (tuning, kernel loading) with a few requests
+    for pb in [stream[i][1] for i in range(min(4, len(stream)))]:
+        plan.wait(plan.submit(pb, bufs[0][:pb.M]), 120.0)
+    results, tickets = [], queue.Queue()
+
+    def collect():
+        while True:
+            item = tickets.get()
+            if item is None:
+                return
+            tk, b = item
+            results.append(plan.wait(tk, 600.0))
+            free.put(b)
+
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    for at, pb in stream:
+        delay = at - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        b = free.get()
+        tickets.put((plan.submit(pb, bufs[b][:pb.M]), b))
+    tickets.put(None)
+    th.join()
+    wall = time.perf_counter() - t0
+    st = plan.serve_stats()
+    plan.close()
+    lat = [r["latency_ms"] for r in results if r["status"] == 0]
+    qms = [r["queue_ms"] for r in results if r["status"] == 0]
+    return {"what": what, "rate_hz": args.serve_rate, "seconds": args.serve_seconds, "requests": len(stream),
+            "completed": len(lat), "holograms_per_s": len(lat) / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(np.max(lat))},
+            "queue_ms": {"p50": float(np.percentile(qms, 50)), "p99": float(np.percentile(qms, 99))},
+            "launches": st["launches"], "device_busy_s": st["busy_ms"] / 1e3,
+            "api": "cswgs_submit / cswgs_wait, continuous batching, device outputs"}
+
+
 # -------------------------------------------------------- reference arm --
 def run_reference(args, rank, world):
     """The FP64 CPU oracle on the host cores, one hologram of the workload per step."""
@@ -191,13 +285,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     pbs = problems(args, rank)
     B = len(pbs)
     # one non-default stream for everything: the plan's kernels, the L2 flush
@@ -235,8 +322,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_ms = max_over_ranks(ev0.elapsed_time(step_ev[-1]))
-    value = B * world * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(ev0.elapsed_time(step_ev[-1]), world, "cuda")
+    value = job_throughput(B, world, args.steps, total_ms)
     res = batch.results()
     # per-step device time (flush + graph) from consecutive events
     step_ms = [ev0.elapsed_time(step_ev[0])] + [step_ev[k - 1].elapsed_time(step_ev[k])
@@ -332,11 +419,15 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             plan.solve_batch(pbs, host_outs)
-        dt = max_over_ranks(time.perf_counter() - t0)
+        dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         line["e2e"] = {"value": B * world * args.e2e_steps / dt, "unit": "holograms/s",
                        "h2d_bytes_per_step": int(sum(pb.N * 3 * 8 for pb in pbs)),
                        "d2h_bytes_per_step": int(sum(pb.M * 4 + 16 for pb in pbs)),
                        "api": "cswgs_solve_batch, pageable host buffers"}
+
+    # continuous-batching server under a Poisson arrival stream
+    if not args.no_serve:
+        line["serve"] = serve_probe(args, local, stream.cuda_stream)
 
     # the FP64 CPU oracle on a bounded sample (rank 0, single GPU runs only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
