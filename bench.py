@@ -80,6 +80,7 @@ def parse():
                     help="serve the mixed stream (P in {768,1024,1152}, N in {10,100,1000}, gamma +-20, 20 "
                          "iterations) instead of the headline holograms")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true")
     return ap.parse_args()
 
 
@@ -393,6 +394,40 @@ def main():
             "gpu_launches": args.steps * len(kts[0]),
             "kernel_times_from": "CUDA events recorded inside the graph around each launch, last timed step",
             "clocks": clk}
+
+    # the half-precision sincos option for the compressed iterations
+    if not args.no_fp16:
+        p16 = Plan(device=local, precision="fp32_fp16sincos", max_batch=max(64, B), max_N=max(1024, args.N),
+                   stream=stream.cuda_stream)
+        outs16 = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+        b16 = p16.batch(pbs, outs16)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            b16.run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            b16.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms16 = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+        r16 = b16.results()
+        kt16 = b16.kernel_times()
+        d_e = max(abs(a["e"] - b["e"]) for a, b in zip(r16, res))
+        d_u = max(abs(a["u"] - b["u"]) for a, b in zip(r16, res))
+        d_ph = max(float(torch.sqrt(torch.mean((torch.remainder(o16 - o + math.pi, 2 * math.pi) - math.pi) ** 2)))
+                   for o16, o in zip(outs16, outs))
+        line["fp16_sincos"] = {"value": job_throughput(B, world, args.steps, ms16), "unit": "holograms/s",
+                               "ms_per_step": ms16 / args.steps,
+                               "compressed_ms_per_launch": sum(kt16[1:1 + n_sub]) / max(1, n_sub),
+                               "vs_fp32": {"max_abs_de": d_e, "max_abs_du": d_u, "max_phase_rms_rad": d_ph},
+                               "what": "compressed iterations with half-precision sincos (packed FP16 on the FMA "
+                                       "pipe); full iterations and final pass FP32"}
+        b16.close()
+        p16.close()
 
     # FP64 GPU baseline (plain double-precision kernels), one hologram at a time
     if not args.no_fp64:

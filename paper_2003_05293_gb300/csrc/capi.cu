@@ -208,8 +208,8 @@ cswgs_status cswgs_plan_create(cswgs_plan *out, const cswgs_plan_desc *d)
         d->max_batch > 4096)
         return set_error(CSWGS_EINVAL, "plan limits out of range (max_P %d, max_N %d, max_batch %d)", d->max_P,
                          d->max_N, d->max_batch);
-    if (d->precision != CSWGS_FP64 && d->precision != CSWGS_FP32)
-        return set_error(CSWGS_EINVAL, "precision %d is not available", (int)d->precision);
+    if (d->precision != CSWGS_FP64 && d->precision != CSWGS_FP32 && d->precision != CSWGS_FP32_FP16SINCOS)
+        return set_error(CSWGS_EINVAL, "unknown precision %d", (int)d->precision);
     int ndev = 0;
     CSWGS_CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (d->device < 0 || d->device >= ndev) return set_error(CSWGS_EINVAL, "device %d of %d", d->device, ndev);

@@ -60,6 +60,7 @@ struct TileShape {
     int threads;        // compressed iterations: threads per block
     int ppt;            // compressed iterations: pixels per thread
     int full_threads;   // full iterations and final pass: threads per block
+    int fp16 = 0;       // compressed iterations use the half-precision sincos
 };
 
 // The two iteration kernels: compressed-iteration tiles, separable full-pass tiles.

@@ -82,7 +82,21 @@ iter_subset_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restri
     });
 }
 
-// Full iterations and the final pass: separable tiles of THREADS / 4 rows x 32 columns.
+// Compressed iterations with the half-precision sincos option.
+template <int THREADS, int PPT>
+__global__ void __launch_bounds__(THREADS, (subset_min_blocks<THREADS, PPT>()))
+iter_subset_h2_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
+                      int total_tiles, int maxN, unsigned *queue)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[THREADS / 32];
+    __shared__ int s_last;
+    persistent_tiles(holos, slots, nslots, total_tiles, queue, [&](const HoloDev &H, const LaunchSlot &sl, int t) {
+        process_tile_h2<THREADS, PPT>(H, sl, t, maxN, smem, s_red, &s_last);
+    });
+}
+
+// Full iterations and the final pass: separable tiles of THREADS / 4 rows x 64 columns.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, (full_min_blocks<THREADS>()))
 iter_full_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
@@ -139,6 +153,8 @@ __global__ void sincos_probe_kernel(float *sink, long long *cycles, int iters)
 
 #define CSWGS_SUBSET_SHAPES(X) \
     X(128, 2) X(128, 4) X(128, 8) X(256, 2) X(256, 4) X(256, 8) X(512, 1) X(512, 2) X(512, 4)
+#define CSWGS_SUBSET_H2_SHAPES(X) \
+    X(128, 2) X(128, 4) X(128, 8) X(256, 2) X(256, 4) X(256, 8) X(512, 2) X(512, 4)
 #define CSWGS_FULL_SHAPES(X) X(128) X(256) X(512)
 
 size_t iter_fp32_smem(TileShape shape, int kind, int maxN)
@@ -150,9 +166,15 @@ size_t iter_fp32_smem(TileShape shape, int kind, int maxN)
 bool tile_shape_supported(TileShape shape)
 {
     bool sub = false, full = false;
+    if (shape.fp16) {
 #define X(T, K) sub |= shape.threads == T && shape.ppt == K;
-    CSWGS_SUBSET_SHAPES(X)
+        CSWGS_SUBSET_H2_SHAPES(X)
 #undef X
+    } else {
+#define X(T, K) sub |= shape.threads == T && shape.ppt == K;
+        CSWGS_SUBSET_SHAPES(X)
+#undef X
+    }
 #define X(T) full |= shape.full_threads == T;
     CSWGS_FULL_SHAPES(X)
 #undef X
@@ -177,7 +199,11 @@ static int max_grid_of(K kernel, int threads, size_t smem, int sm_count)
 int iter_fp32_max_grid(TileShape shape, int kind, int maxN, int sm_count)
 {
     const size_t smem = iter_fp32_smem(shape, kind, maxN);
-    if (kind == kLaunchSubset) {
+    if (kind == kLaunchSubset && shape.fp16) {
+#define X(T, K) if (shape.threads == T && shape.ppt == K) return max_grid_of(iter_subset_h2_kernel<T, K>, T, smem, sm_count);
+        CSWGS_SUBSET_H2_SHAPES(X)
+#undef X
+    } else if (kind == kLaunchSubset) {
 #define X(T, K) if (shape.threads == T && shape.ppt == K) return max_grid_of(iter_subset_kernel<T, K>, T, smem, sm_count);
         CSWGS_SUBSET_SHAPES(X)
 #undef X
@@ -196,7 +222,13 @@ cudaError_t launch_iter_fp32(TileShape shape, int kind, const HoloDev *holos, co
     // the smem attribute is set by iter_fp32_max_grid, which every batch calls first
     const size_t smem = iter_fp32_smem(shape, kind, maxN);
     (void)cudaGetLastError();   // report this launch, not an earlier call's error
-    if (kind == kLaunchSubset) {
+    if (kind == kLaunchSubset && shape.fp16) {
+#define X(T, K) if (shape.threads == T && shape.ppt == K) { \
+            iter_subset_h2_kernel<T, K><<<grid, T, smem, s>>>(holos, slots, nslots, total_tiles, maxN, queue); \
+            return cudaGetLastError(); }
+        CSWGS_SUBSET_H2_SHAPES(X)
+#undef X
+    } else if (kind == kLaunchSubset) {
 #define X(T, K) if (shape.threads == T && shape.ppt == K) { \
             iter_subset_kernel<T, K><<<grid, T, smem, s>>>(holos, slots, nslots, total_tiles, maxN, queue); \
             return cudaGetLastError(); }

@@ -149,7 +149,7 @@ namespace cswgs {
 // autotuner
 TileShape tuned_shape(cswgs_plan_s *p, const std::vector<HoloSpec> &specs);
 cswgs_status tune_batch(cswgs_plan_s *p, Fp32Batch *b, double *best_ms);
-std::string tune_key(const std::vector<HoloSpec> &specs);
+std::string tune_key(const std::vector<HoloSpec> &specs, bool fp16);
 void tune_load(cswgs_plan_s *p);
 void tune_save(cswgs_plan_s *p);
 }  // namespace cswgs

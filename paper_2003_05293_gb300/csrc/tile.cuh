@@ -343,6 +343,118 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     finish_tile<THREADS>(H, sl, m.v, s_red, s_last);
 }
 
+// A tile of a compressed iteration with the half-precision sincos option
+// (sincos_fix_h2): as process_tile, with each pair of pixels' phasors made by
+// one packed FP16 evaluation.  The back-propagation sums run in FP16 over 8
+// spots at a time and are flushed into FP32; the forward sums over the
+// thread's PPT pixels run in FP16 and are converted before the reductions.
+template <int THREADS, int PPT>
+__device__ void process_tile_h2(const HoloDev &H, const LaunchSlot &sl, int t, int maxN,
+                                unsigned char *smem, double *s_red, int *s_last)
+{
+    static_assert(PPT % 2 == 0, "pixels go in pairs");
+    constexpr int NP = PPT / 2;
+    constexpr int kFlush = 8;
+    const TileSmem m = tile_smem<THREADS>(smem, maxN);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int P = H.P, N = H.N;
+    const int count = sl.count;
+
+    load_spot_tables<THREADS>(H, m);
+
+    const SubsetKeys K = subset_keys(H.seed, sl.j);
+    const int half = P >> 1;
+    int32_t xp[PPT], yp[PPT];
+    uint32_t r2[PPT];
+    __half2 msk[NP];
+    const int base = t * (THREADS * PPT);
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) {
+        int idx = base + s * THREADS + tid;
+        bool valid = idx < count;
+        uint32_t mm = permute(valid ? (uint32_t)idx : 0u, (uint32_t)P, K);
+        int r = (int)(mm / (uint32_t)P);
+        int i = (int)mm - r * P;
+        xp[s] = i - half;
+        yp[s] = r - half;
+        r2[s] = (uint32_t)(xp[s] * xp[s] + yp[s] * yp[s]);
+        if (s & 1) msk[s / 2] = __floats2half2_rn(idx - THREADS < count ? 1.f : 0.f, valid ? 1.f : 0.f);
+    }
+    __syncthreads();
+
+    // back-propagation, Eq. 1
+    float sr[PPT], si[PPT];
+    __half2 hr[NP], hi[NP];
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) { sr[s] = 0.f; si[s] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) { hr[k] = __float2half2_rn(0.f); hi[k] = __float2half2_rn(0.f); }
+    for (int n0 = 0; n0 < N; n0 += kFlush) {
+        const int n1 = min(n0 + kFlush, N);
+        for (int n = n0; n < n1; ++n) {
+            const int4 c = m.coef[n];
+            const uint2 bw = m.bw[n];
+            const uint32_t add = bw.x - kFixRound + kHalfAddend;
+            const __half2 w2 = __float2half2_rn(__uint_as_float(bw.y));
+            const SpotFix f = {c.x, c.y, c.z, 0.f};
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                __half2 sn, cs;
+                sincos_fix_h2(fix_phase(f, xp[2 * k], yp[2 * k], r2[2 * k], add),
+                              fix_phase(f, xp[2 * k + 1], yp[2 * k + 1], r2[2 * k + 1], add), sn, cs);
+                hr[k] = __hfma2(w2, cs, hr[k]);
+                hi[k] = __hfma2(w2, sn, hi[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 a = __half22float2(hr[k]), b = __half22float2(hi[k]);
+            sr[2 * k] += a.x;
+            sr[2 * k + 1] += a.y;
+            si[2 * k] += b.x;
+            si[2 * k + 1] += b.y;
+            hr[k] = __float2half2_rn(0.f);
+            hi[k] = __float2half2_rn(0.f);
+        }
+    }
+
+    // Phi_m = arg S_m; the forward pass needs -Phi_m as a fixed-point addend
+    uint32_t padd[PPT];
+#pragma unroll
+    for (int s = 0; s < PPT; ++s) padd[s] = kHalfAddend - rad_to_fix(atan2f(si[s], sr[s]));
+
+    // forward projection, Eq. 3 (conjugate phasors, as in process_tile)
+    float2 *wbuf = m.wbuf + warp * 32 * kWarpRow;
+    for (int n0 = 0; n0 < N; n0 += kSpotChunk) {
+        const int nc = min(kSpotChunk, N - n0);
+        for (int q0 = 0; q0 < nc; q0 += kWarpChunk) {
+            const int qc = min(kWarpChunk, nc - q0);
+            for (int q = 0; q < qc; ++q) {
+                const int4 c = m.coef[n0 + q0 + q];
+                const SpotFix f = {c.x, c.y, c.z, 0.f};
+                __half2 vr2 = __float2half2_rn(0.f), vi2 = __float2half2_rn(0.f);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    __half2 sn, cs;
+                    sincos_fix_h2(fix_phase(f, xp[2 * k], yp[2 * k], r2[2 * k], padd[2 * k]),
+                                  fix_phase(f, xp[2 * k + 1], yp[2 * k + 1], r2[2 * k + 1], padd[2 * k + 1]), sn, cs);
+                    vr2 = __hfma2(msk[k], cs, vr2);
+                    vi2 = __hfma2(msk[k], sn, vi2);
+                }
+                const float2 a = __half22float2(vr2), b = __half22float2(vi2);
+                wbuf[lane * kWarpRow + q] = make_float2(a.x + a.y, -(b.x + b.y));
+            }
+            __syncwarp();
+            warp_transpose_reduce(wbuf, lane, qc, m.part + warp * kSpotChunk + q0);
+            __syncwarp();
+        }
+        __syncthreads();
+        store_tile_partials<THREADS>(H, sl.pass, t, n0, nc, m.part);
+        __syncthreads();
+    }
+    finish_tile<THREADS>(H, sl, m.v, s_red, s_last);
+}
+
 // One spot factor of a separable tile: e^{i 2 pi (c u + G u^2)} for pixel
 // coordinate u (x' with the tilt A, or y' with the tilt B) plus an addend,
 // scaled by w.  The fixed-point split is that of fix_phase.

@@ -49,11 +49,11 @@ static TuneKey key_of(const std::vector<HoloSpec> &specs)
     return k;
 }
 
-std::string tune_key(const std::vector<HoloSpec> &specs)
+std::string tune_key(const std::vector<HoloSpec> &specs, bool fp16)
 {
     TuneKey k = key_of(specs);
     char buf[64];
-    snprintf(buf, sizeof buf, "P%d_N%d_B%d", k.P, k.N, k.B);
+    snprintf(buf, sizeof buf, "P%d_N%d_B%d%s", k.P, k.N, k.B, fp16 ? "_H" : "");
     return buf;
 }
 
@@ -113,10 +113,12 @@ static cswgs_status tune_for(cswgs_plan_s *p, const TuneKey &k, double c, double
                              TileShape *best_shape, double *best_ms)
 {
     std::vector<HoloSpec> specs = synthetic(k, c);
-    TileShape best{256, 4, 256};
+    const int fp16 = p->desc.precision == CSWGS_FP32_FP16SINCOS ? 1 : 0;
+    TileShape best{256, 4, 256, fp16};
     double best_sub = 1e30, best_full = 1e30, t[3];
     for (const auto &cand : kSubCandidates) {
-        TileShape sh{cand[0], cand[1], best.full_threads};
+        TileShape sh{cand[0], cand[1], best.full_threads, fp16};
+        if (!tile_shape_supported(sh)) continue;
         if (iter_fp32_max_grid(sh, kLaunchSubset, k.N, p->sm_count) <= 0) continue;
         CSWGS_TRY(time_steps(p, specs, sh, t));
         if (t[0] < best_sub) {
@@ -126,7 +128,7 @@ static cswgs_status tune_for(cswgs_plan_s *p, const TuneKey &k, double c, double
         }
     }
     for (int ft : kFullCandidates) {
-        TileShape sh{best.threads, best.ppt, ft};
+        TileShape sh{best.threads, best.ppt, ft, fp16};
         if (iter_fp32_max_grid(sh, kLaunchFull, k.N, p->sm_count) <= 0) continue;
         CSWGS_TRY(time_steps(p, specs, sh, t));
         const double tf = wfull * t[1] + t[2];
@@ -142,7 +144,8 @@ static cswgs_status tune_for(cswgs_plan_s *p, const TuneKey &k, double c, double
 
 TileShape tuned_shape(cswgs_plan_s *p, const std::vector<HoloSpec> &specs)
 {
-    std::string key = tune_key(specs);
+    const bool fp16 = p->desc.precision == CSWGS_FP32_FP16SINCOS;
+    std::string key = tune_key(specs, fp16);
     auto it = p->tune.find(key);
     if (it != p->tune.end()) return it->second;
     // tune now, with the schedule's own mix of compressed and full iterations
@@ -157,7 +160,7 @@ TileShape tuned_shape(cswgs_plan_s *p, const std::vector<HoloSpec> &specs)
         wsub /= specs.size();
         wfull /= specs.size();
     }
-    TileShape sh{256, 4, 256};
+    TileShape sh{256, 4, 256, fp16 ? 1 : 0};
     double ms = 0.0;
     if (tune_for(p, key_of(specs), c, wsub, wfull, &sh, &ms) == CSWGS_OK) {
         p->tune[key] = sh;
@@ -178,7 +181,7 @@ cswgs_status tune_single(cswgs_plan_s *p, int P, int N, double c, double *best_m
     TuneKey k = key_of(v);
     TileShape sh;
     CSWGS_TRY(tune_for(p, k, c, 28.0, 2.0, &sh, best_ms));
-    p->tune[tune_key(v)] = sh;
+    p->tune[tune_key(v, p->desc.precision == CSWGS_FP32_FP16SINCOS)] = sh;
     tune_save(p);
     return CSWGS_OK;
 }
@@ -199,9 +202,11 @@ void tune_load(cswgs_plan_s *p)
         std::string key = s.substr(pos + 1, end - pos - 1);
         pos = end + 1;
         if (key.empty() || key[0] != 'P') continue;
+        const int fp16 = key.size() > 2 && key.compare(key.size() - 2, 2, "_H") == 0 ? 1 : 0;
         int t = 0, k = 0, f = 0;
-        if (sscanf(s.c_str() + pos, " : [ %d , %d , %d ]", &t, &k, &f) == 3 && tile_shape_supported(TileShape{t, k, f}))
-            p->tune[key] = TileShape{t, k, f};
+        if (sscanf(s.c_str() + pos, " : [ %d , %d , %d ]", &t, &k, &f) == 3 &&
+            tile_shape_supported(TileShape{t, k, f, fp16}))
+            p->tune[key] = TileShape{t, k, f, fp16};
     }
 }
 

@@ -249,3 +249,62 @@ def test_invalid_arguments(fp32):
         assert ei.value.status == 1
     with pytest.raises(CswgsError):
         fp32.solve(np.zeros((0, 3)), 16, 0.5, 1, 0)
+
+
+# ------------------------------------------- half-precision sincos option --
+# The option evaluates the compressed iterations' phasors in FP16 (1.2e-3 rad
+# RMS per phasor); the full iterations and the final pass stay FP32.  Its
+# per-iteration errors are measured, printed and bounded loosely here; as the
+# option is specified, only the final e and u must meet the 1e-3 tolerance.
+# (Its trajectory drifts from the FP64 one, so the final phase map differs by
+# a few 1e-2 rad RMS while the hologram's quality agrees.)
+TOL_FP16_ITER = 3e-3
+TOL_FP16_MAP = 0.15
+
+@pytest.fixture(scope="module")
+def fp16():
+    from paper_2003_05293_gb300 import Plan
+    p = Plan(precision="fp32_fp16sincos")
+    yield p
+    p.close()
+
+
+def test_fp16_phase_on_subset_error(fp16, medium):
+    # the back-propagation of a compressed iteration (the map is written by the
+    # FP32 final pass, so compare one teacher-forced iteration's state instead)
+    pb, states = medium
+    j = 10
+    w0, th0 = states[j - 1]
+    w1, th1 = states[j]
+    r = fp16.solve(pb.xyz, pb.P, pb.c, 1, pb.seed, init_w=w0, init_theta=th0, first_iteration=j,
+                   full_iterations=0, final_pass=False, state=True)
+    err_theta = rms_wrapped(r["theta"], th1)
+    err_w = math.sqrt(np.mean((r["w"] / w1 - 1) ** 2))
+    print("fp16 sincos, one compressed iteration: theta RMS %.2e rad, w RMS %.2e" % (err_theta, err_w))
+    assert err_theta < TOL_FP16_ITER and err_w < TOL_FP16_ITER
+
+
+def test_fp16_final_matches_oracle(fp16, medium):
+    pb, _ = medium
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = run(fp16, pb)
+    print("fp16 sincos, 30 iterations: phase RMS %.2e rad, |de| %.1e, |du| %.1e"
+          % (rms_wrapped(ph, ref["phase"]), abs(r["e"] - ref["e"]), abs(r["u"] - ref["u"])))
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
+    assert rms_wrapped(ph, ref["phase"]) < TOL_FP16_MAP
+
+
+def test_fp16_batch_equals_solo(fp16):
+    pbs = workloads.batch(6, seed=13, P_choices=(64, 128, 256), N_lo=2, N_hi=40, gamma_max=5.0, c=0.25,
+                          iterations=6)
+    outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+    b = fp16.batch(pbs, outs)
+    b.run()
+    res = b.results()
+    for pb, out, r in zip(pbs, outs, res):
+        o2 = torch.empty(pb.M, dtype=torch.float32, device="cuda")
+        s = fp16.solve(pb.xyz, pb.P, pb.c, pb.iterations, pb.seed, out=o2)
+        # other tile shapes pair other pixels in the FP16 evaluation
+        assert rms_wrapped(out.cpu().numpy(), o2.cpu().numpy()) < TOL_FP16_MAP
+        assert abs(r["e"] - s["e"]) < TOL_EU and abs(r["u"] - s["u"]) < TOL_EU
+    b.close()
