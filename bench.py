@@ -81,6 +81,7 @@ def parse():
                          "iterations) instead of the headline holograms")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
+    ap.add_argument("--no-scenarios", action="store_true")
     return ap.parse_args()
 
 
@@ -459,6 +460,20 @@ def main():
                        "h2d_bytes_per_step": int(sum(pb.N * 3 * 8 for pb in pbs)),
                        "d2h_bytes_per_step": int(sum(pb.M * 4 + 16 for pb in pbs)),
                        "api": "cswgs_solve_batch, pageable host buffers"}
+
+    # the paper's scenarios (Section 5): 10 orientations and initial phases of
+    # each, as one batch through the same path
+    if not args.no_scenarios:
+        qual = {}
+        for name in workloads.SCENARIOS:
+            spb = [workloads.scenario(name, args.P, seed=s, c=args.c, iterations=args.iters) for s in range(10)]
+            r = plan.solve_batch(spb)
+            es = np.array([x["e"] for x in r])
+            us = np.array([x["u"] for x in r])
+            qual[name] = {"N": spb[0].N, "e_mean": float(es.mean()), "e_std": float(es.std()),
+                          "u_mean": float(us.mean()), "u_std": float(us.std()),
+                          "e_min": float(es.min()), "u_min": float(us.min())}
+        line["quality_paper_scenarios"] = qual
 
     # continuous-batching server under a Poisson arrival stream
     if not args.no_serve:

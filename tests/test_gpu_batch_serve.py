@@ -177,3 +177,16 @@ def test_serving_admission_by_memory():
             p.submit(workloads.problem(1024, 64, 2.0, 0.25, 4, seed=0), None)
         assert ei.value.status == 2
         assert p.serve_stats()["rejected"] == 1
+
+
+@pytest.mark.parametrize("name", ["grid100", "grid36", "cubes100"])
+def test_paper_scenarios_match_oracle(plan, name):
+    # the paper's scenarios (Section 5) at P = 512: GPU e, u equal the oracle's,
+    # and the rotated grids reach e, u > 0.9 as the paper reports for N <= 100
+    pb = workloads.scenario(name, 512, seed=3)
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = solo(plan, pb)
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
+    assert rms_wrapped(ph, ref["phase"]) < TOL_PHASE_RMS
+    if name.startswith("grid"):
+        assert ref["e"] > 0.9 and ref["u"] > 0.9

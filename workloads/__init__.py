@@ -27,7 +27,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Problem", "spots", "problem", "TINY", "MEDIUM", "LARGE", "batch", "arrivals"]
+__all__ = ["Problem", "spots", "problem", "TINY", "MEDIUM", "LARGE", "batch", "arrivals", "scenario",
+           "SCENARIOS"]
 
 
 @dataclass
@@ -104,3 +105,45 @@ def arrivals(rate_hz: float, duration_s: float, seed: int = 0, P_choices=(768, 1
         hs = int(rng.integers(0, 2**63 - 1))
         out.append((t, problem(P, N, gamma_max, c, iterations, hs)))
     return out
+
+
+# The paper's test scenarios (Section 5), as seeded synthetic stand-ins: a
+# regular 10 x 10 and a 6 x 6 grid of spots rotated in 3D, and a less regular
+# 3D cloud of spots in two cubes.  Each seed draws a new orientation (the
+# paper repeats every scenario with 10 orientations and initial phases).
+# Lateral coordinates are in cycles across the aperture; the axial one is
+# turned into waves of defocus at the aperture edge with KAPPA waves per cycle
+# (the ratio of the two scales for an objective of NA ~ 0.8).
+KAPPA = 0.2
+SCENARIOS = ("grid100", "grid36", "cubes100")
+
+
+def _rotation(rng):
+    a, b, c = rng.uniform(0.0, 2.0 * np.pi, 3)
+
+    def rz(t):
+        return np.array([[np.cos(t), -np.sin(t), 0.0], [np.sin(t), np.cos(t), 0.0], [0.0, 0.0, 1.0]])
+
+    def rx(t):
+        return np.array([[1.0, 0.0, 0.0], [0.0, np.cos(t), -np.sin(t)], [0.0, np.sin(t), np.cos(t)]])
+
+    return rz(a) @ rx(b) @ rz(c)
+
+
+def scenario(name: str, P: int, seed: int, c: float = 0.125, iterations: int = 30) -> Problem:
+    """One of SCENARIOS at grid side P, orientation drawn from `seed`."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if name in ("grid100", "grid36"):
+        n = 10 if name == "grid100" else 6
+        spacing = P / (4.0 * n)                  # the grid spans ~P/4 cycles
+        g = (np.arange(n) - (n - 1) / 2.0) * spacing
+        pts = np.array([[x, y, 0.0] for x in g for y in g])
+    elif name == "cubes100":
+        side = P / 10.0
+        pts = np.concatenate([rng.uniform(-side / 2, side / 2, (50, 3)) + np.array([dx * 0.8 * side, 0.0, 0.0])
+                              for dx in (-1.0, 1.0)])
+    else:
+        raise ValueError("unknown scenario %r" % name)
+    pts = pts @ _rotation(rng).T
+    xyz = np.stack([pts[:, 0], pts[:, 1], KAPPA * pts[:, 2]], axis=1)
+    return Problem(P=P, xyz=xyz, amp=None, c=c, iterations=iterations, seed=seed, extra={"scenario": name})
