@@ -62,6 +62,23 @@ def _load():
         lib.oracle_theta0.argtypes = [ctypes.c_int, u64, d]
         lib.oracle_permute.argtypes = [ctypes.c_int, u64, ctypes.c_int, ctypes.c_int64]
         lib.oracle_permute.restype = ctypes.c_int64
+        lib.oracle_permute_domain.argtypes = [ctypes.c_int64, u64, ctypes.c_int, ctypes.c_int64]
+        lib.oracle_permute_domain.restype = ctypes.c_int64
+        lib.oracle_in_pupil.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64]
+        lib.oracle_in_pupil.restype = ctypes.c_int
+        lib.oracle_pupil_amplitude.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64]
+        lib.oracle_pupil_amplitude.restype = ctypes.c_double
+        lib.oracle_pupil_pixels.argtypes = [ctypes.c_int, ctypes.c_int, i64]
+        lib.oracle_pupil_pixels.restype = ctypes.c_int64
+        lib.oracle_subset_pupil.argtypes = [ctypes.c_int64, i64, ctypes.c_int64, u64, ctypes.c_int, ctypes.c_int, i64]
+        lib.oracle_forward_pupil.argtypes = [ctypes.c_int, ctypes.c_int, d, ctypes.c_int64, i64, d, d,
+                                             ctypes.c_double, d]
+        lib.oracle_metrics_pupil.argtypes = [ctypes.c_int, ctypes.c_int, d, d, ctypes.c_int, ctypes.c_double,
+                                             d, d, d, d]
+        lib.oracle_solve_pupil.argtypes = [ctypes.c_int, ctypes.c_int, d, d, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int, u64, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_int, d, d, d, d, d, d]
+        lib.oracle_solve_pupil.restype = ctypes.c_int
         lib.oracle_subset.argtypes = [ctypes.c_int, ctypes.c_int64, u64, ctypes.c_int, i64]
         lib.oracle_spot_phase.argtypes = [ctypes.c_int, d, ctypes.c_int, ctypes.c_int64]
         lib.oracle_spot_phase.restype = ctypes.c_double
@@ -129,10 +146,41 @@ def permute(P: int, seed: int, j: int, k: int) -> int:
     return int(_load().oracle_permute(P, seed & (2**64 - 1), j, k))
 
 
-def subset(P: int, Mp: int, seed: int, j: int) -> np.ndarray:
-    """S_j: the Mp pixel indices of iteration j (Section 2, CS-WGS)."""
+def permute_domain(D: int, seed: int, j: int, k: int) -> int:
+    """pi_{seed,j}(k): keyed bijection on [0, D) (Feistel network plus cycle walking)."""
+    return int(_load().oracle_permute_domain(D, seed & (2**64 - 1), j, k))
+
+
+APERTURES = {"square": 0, "round": 1}
+SUBSET_MODES = {"fresh": 0, "windows": 1}
+
+
+def pupil_pixels(P: int, aperture: str = "square") -> np.ndarray:
+    """The pupil's pixels Omega in row-major order (Section 4: a round aperture of P pixels)."""
+    lib = _load()
+    ap = APERTURES[aperture]
+    D = int(lib.oracle_pupil_pixels(P, ap, None))
+    out = np.empty(D, dtype=np.int64)
+    lib.oracle_pupil_pixels(P, ap, _ip(out))
+    return out
+
+
+def pupil_amplitude(P: int, waist: float = 0.0) -> np.ndarray:
+    """A at every pixel (P*P): exp(-rho^2 / waist^2), or 1 for waist <= 0."""
+    lib = _load()
+    return np.array([lib.oracle_pupil_amplitude(P, float(waist), m) for m in range(P * P)])
+
+
+def subset(P: int, Mp: int, seed: int, j: int, aperture: str = "square", mode: str = "fresh") -> np.ndarray:
+    """S_j: the Mp pixel indices of iteration j (Section 2, CS-WGS), drawn from
+    the pupil's pixels; mode "windows" takes window j of one fixed permutation."""
     out = np.empty(Mp, dtype=np.int64)
-    _load().oracle_subset(P, Mp, seed & (2**64 - 1), j, _ip(out))
+    if aperture == "square" and mode == "fresh":
+        _load().oracle_subset(P, Mp, seed & (2**64 - 1), j, _ip(out))
+        return out
+    omega = pupil_pixels(P, aperture)
+    _load().oracle_subset_pupil(omega.shape[0], _ip(omega), Mp, seed & (2**64 - 1), j, SUBSET_MODES[mode],
+                                _ip(out))
     return out
 
 
@@ -174,6 +222,19 @@ def forward(P: int, xyz, phi, pix=None) -> np.ndarray:
     return V[0::2] + 1j * V[1::2]
 
 
+def forward_pupil(P: int, xyz, phi, pix, A, norm: float) -> np.ndarray:
+    """Eq. 3 with pupil amplitudes: (1/norm) sum_k A_k e^{i (Phi_k - phi_n(m_k))}."""
+    xyz = _f64(xyz, (-1, 3))
+    N = xyz.shape[0]
+    phi = _f64(phi)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    A = _f64(A)
+    assert phi.shape[0] == pix.shape[0] == A.shape[0]
+    V = np.empty(2 * N)
+    _load().oracle_forward_pupil(P, N, _dp(xyz), pix.shape[0], _ip(pix), _dp(phi), _dp(A), float(norm), _dp(V))
+    return V[0::2] + 1j * V[1::2]
+
+
 def update(V, w, theta):
     """Eqs. 4-6: returns the updated (w, theta)."""
     V = np.asarray(V, dtype=np.complex128)
@@ -186,8 +247,9 @@ def update(V, w, theta):
     return w, theta
 
 
-def metrics(P: int, xyz, phi_full):
-    """Efficiency e, uniformity u (Eq. 7), spot intensities I_n and fields V_n."""
+def metrics(P: int, xyz, phi_full, aperture: str = "square", waist: float = 0.0):
+    """Efficiency e, uniformity u (Eq. 7), spot intensities I_n and fields V_n
+    over the pupil (normalised by the pupil's sum of A)."""
     xyz = _f64(xyz, (-1, 3))
     N = xyz.shape[0]
     phi_full = _f64(phi_full)
@@ -196,17 +258,26 @@ def metrics(P: int, xyz, phi_full):
     In = np.empty(N)
     e = ctypes.c_double()
     u = ctypes.c_double()
-    _load().oracle_metrics(P, N, _dp(xyz), _dp(phi_full), _dp(V), _dp(In), ctypes.byref(e), ctypes.byref(u))
+    lib = _load()
+    if aperture == "square" and not waist > 0:
+        lib.oracle_metrics(P, N, _dp(xyz), _dp(phi_full), _dp(V), _dp(In), ctypes.byref(e), ctypes.byref(u))
+    else:
+        lib.oracle_metrics_pupil(P, N, _dp(xyz), _dp(phi_full), APERTURES[aperture], float(waist), _dp(V),
+                                 _dp(In), ctypes.byref(e), ctypes.byref(u))
     return e.value, u.value, In, V[0::2] + 1j * V[1::2]
 
 
 def solve(P: int, xyz, amp=None, c: float = 1.0, iterations: int = 0, seed: int = 0,
           theta_in=None, w_in=None, first_j: int = 1, final_pass: bool = True,
-          full_iterations: int = 2):
+          full_iterations: int = 2, aperture: str = "square", waist: float = 0.0,
+          subset_mode: str = "fresh"):
     """The whole CS-WGS method (Section 2).
 
-    The last `full_iterations` of the `iterations` run over all pixels (the
-    paper ends with two such iterations); the others over the subsets S_j.
+    The last `full_iterations` of the `iterations` run over all pupil pixels
+    (the paper ends with two such iterations); the others over the subsets S_j.
+    aperture "round", waist > 0 and subset_mode "windows" are the paper's own
+    setup (Section 4: round aperture, Gaussian beam; Section 3: one random
+    reordering of the pupil's pixels).
 
     Returns a dict with phase (P*P, [0, 2 pi), or None without the final pass),
     e, u, w, theta (final state) and I (spot intensities)."""
@@ -222,16 +293,25 @@ def solve(P: int, xyz, amp=None, c: float = 1.0, iterations: int = 0, seed: int 
     In = np.empty(N) if final_pass else None
     e = ctypes.c_double(float("nan"))
     u = ctypes.c_double(float("nan"))
-    rc = _load().oracle_solve(P, N, _dp(xyz), _dp(amp), float(c), int(iterations),
-                              int(full_iterations), seed & (2**64 - 1), _dp(theta_in), _dp(w_in), int(first_j),
-                              1 if final_pass else 0, _dp(phase), ctypes.byref(e),
-                              ctypes.byref(u), _dp(w), _dp(th), _dp(In))
+    if aperture == "square" and not waist > 0 and subset_mode == "fresh":
+        rc = _load().oracle_solve(P, N, _dp(xyz), _dp(amp), float(c), int(iterations),
+                                  int(full_iterations), seed & (2**64 - 1), _dp(theta_in), _dp(w_in), int(first_j),
+                                  1 if final_pass else 0, _dp(phase), ctypes.byref(e),
+                                  ctypes.byref(u), _dp(w), _dp(th), _dp(In))
+    else:
+        rc = _load().oracle_solve_pupil(P, N, _dp(xyz), _dp(amp), float(c), int(iterations),
+                                        int(full_iterations), seed & (2**64 - 1), _dp(theta_in), _dp(w_in),
+                                        int(first_j), 1 if final_pass else 0, APERTURES[aperture], float(waist),
+                                        SUBSET_MODES[subset_mode], _dp(phase), ctypes.byref(e),
+                                        ctypes.byref(u), _dp(w), _dp(th), _dp(In))
     if rc != 0:
         raise ValueError("oracle_solve rejected its arguments")
     return {"phase": phase, "e": e.value, "u": u.value, "w": w, "theta": th, "I": In}
 
 
-def subset_size(P: int, c: float) -> int:
-    """Mp = floor(c M), the size of every subset (Section 2, CS-WGS)."""
+def subset_size(P: int, c: float, aperture: str = "square") -> int:
+    """Mp = floor(c D), the size of every subset (Section 2, CS-WGS), D the
+    pupil's pixel count (M for the square grid)."""
     import math
-    return int(math.floor(c * P * P))
+    D = P * P if aperture == "square" else int(_load().oracle_pupil_pixels(P, APERTURES[aperture], None))
+    return int(math.floor(c * D))

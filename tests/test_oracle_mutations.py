@@ -29,7 +29,17 @@ MUTATIONS = {
                                  "sr += cos(ph);\n            si += sin(ph);"),
     "theta0 scaled to [0, 1)": ("theta[n] = ORACLE_TWO_PI * ((double)(x >> 11) * 0x1.0p-53);",
                                 "theta[n] = ((double)(x >> 11) * 0x1.0p-53);"),
-    "Feistel not a bijection": ("uint32_t nr = (L + F) % (uint32_t)P;", "uint32_t nr = (L + F) % (uint32_t)P | 1u;"),
+    "Feistel not a bijection": ("uint64_t nr = (L + F) % p;", "uint64_t nr = (L + F) % p | 1u;"),
+    "Feistel moduli not alternated": ("            p = q;\n            q = t;", "            (void)t;"),
+    "no cycle walking": ("} while (y >= D);", "} while (0);"),
+    "round aperture edge excluded": ("return xp * xp + yp * yp <= (int64_t)(P / 2) * (P / 2);",
+                                     "return xp * xp + yp * yp < (int64_t)(P / 2) * (P / 2);"),
+    "beam radius at 1/e intensity": ("return exp(-(xp * xp + yp * yp) / (waist * waist));",
+                                     "return exp(-(xp * xp + yp * yp) / (2.0 * waist * waist));"),
+    "pupil amplitude applied twice": ("double a = A ? A[k] : 1.0;", "double a = A ? A[k] * A[k] : 1.0;"),
+    "metrics normalised by pixel count": ("norm += A[k];", "norm += 1.0;"),
+    "window offset from j": ("off = (((int64_t)(j - 1) % D)", "off = (((int64_t)j % D)"),
+    "phase outside the pupil kept": ("for (int64_t m = 0; m < M; ++m) phi[m] = 0.0;", "(void)0;"),
     "full iterations not applied": ("int full = it >= I - n_full;", "int full = 0;"),
 }
 

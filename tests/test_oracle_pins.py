@@ -365,3 +365,214 @@ def test_rejects_bad_arguments():
         args.update(kw)
         with pytest.raises(ValueError):
             oracle.solve(args["P"], xyz, c=args["c"], iterations=args["iterations"])
+
+
+# --------------------------------------------------------------------------
+# pupil (Section 4: round aperture of P pixels, Gaussian beam; Eq. 3's A) and
+# the subset readings over it (Section 3, "Compressed sensing")
+
+# Lattice points with x^2 + y^2 <= r^2, r = 1 .. 12 (the Gauss circle problem,
+# OEIS A000328).  The round pupil of a P-pixel grid is that disc of radius P/2
+# less its two points at x' = P/2 or y' = P/2, which fall off the grid.
+GAUSS_CIRCLE = [5, 13, 29, 49, 81, 113, 149, 197, 253, 317, 377, 441]
+
+
+def test_round_pupil_counts_gauss_circle():
+    for r, n in enumerate(GAUSS_CIRCLE, start=1):
+        P = 2 * r
+        om = oracle.pupil_pixels(P, "round")
+        assert om.shape[0] == n - 2
+        assert np.all(np.diff(om) > 0) and om.min() >= 0 and om.max() < P * P
+    assert np.array_equal(oracle.pupil_pixels(10, "square"), np.arange(100))
+    # the disc's area, to within its perimeter
+    P = 1152
+    D = oracle.subset_size(P, 1.0, "round")
+    assert abs(D - math.pi * (P / 2) ** 2) < 2 * math.pi * (P / 2)
+
+
+def test_gaussian_amplitude_is_beam_radius():
+    # A = 1 on the axis and 1/e at rho = waist (intensity 1/e^2 there), separable
+    P, w = 32, 10.0
+    A = oracle.pupil_amplitude(P, w).reshape(P, P)
+    assert A[P // 2, P // 2] == 1.0
+    assert A[P // 2, P // 2 + 10] == pytest.approx(math.exp(-1.0), rel=1e-15)
+    assert A[P // 2 + 6, P // 2 + 8] == pytest.approx(math.exp(-1.0), rel=1e-15)   # 6-8-10 triangle
+    assert np.allclose(A, np.outer(A[:, P // 2], A[P // 2, :]), rtol=1e-14)
+    assert np.all(oracle.pupil_amplitude(P, 0.0) == 1.0)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 5, 47, 79, 195, 1000, 4093, 12345])
+def test_permutation_on_any_domain_is_bijection(D):
+    for j in (0, 1, 9):
+        img = np.array([oracle.permute_domain(D, 31, j, k) for k in range(D)])
+        assert np.array_equal(np.sort(img), np.arange(D))
+    if D > 100:
+        a = [oracle.permute_domain(D, 31, 1, k) for k in range(100)]
+        b = [oracle.permute_domain(D, 31, 2, k) for k in range(100)]
+        assert a != b
+
+
+def test_permutation_of_square_domain_is_the_grid_permutation():
+    P = 24
+    for k in range(0, P * P, 7):
+        assert oracle.permute_domain(P * P, 5, 3, k) == oracle.permute(P, 5, 3, k)
+
+
+def test_subsets_stay_in_round_pupil():
+    P, c = 64, 0.125
+    Mp = oracle.subset_size(P, c, "round")
+    om = set(oracle.pupil_pixels(P, "round").tolist())
+    for mode in ("fresh", "windows"):
+        for j in (1, 2, 7):
+            s = oracle.subset(P, Mp, 4, j, "round", mode)
+            assert len(set(s.tolist())) == Mp and set(s.tolist()) <= om
+            r, i = np.divmod(s, P)
+            assert np.all((i - P // 2) ** 2 + (r - P // 2) ** 2 <= (P // 2) ** 2)
+
+
+def test_windows_partition_one_permutation():
+    # window j is entries (j-1) Mp .. j Mp - 1 of one fixed order of the pupil's
+    # pixels: windows 1 .. 1/c are disjoint, the first is the prefix of that
+    # order (the fresh draw with key 0), and they wrap around after the last
+    P, c = 16, 0.25
+    om = oracle.pupil_pixels(P, "round")
+    D = om.shape[0]
+    Mp = oracle.subset_size(P, c, "round")
+    wins = [oracle.subset(P, Mp, 8, j, "round", "windows") for j in range(1, 5)]
+    allw = np.concatenate(wins)
+    assert len(np.unique(allw)) == 4 * Mp
+    order = om[[oracle.permute_domain(D, 8, 0, k) for k in range(D)]]
+    assert np.array_equal(wins[0], order[:Mp])
+    assert np.array_equal(wins[2], order[2 * Mp:3 * Mp])
+    w5 = oracle.subset(P, Mp, 8, 5, "round", "windows")
+    assert np.array_equal(w5, order[(4 * Mp + np.arange(Mp)) % D])
+
+
+def test_forward_with_pupil_is_weighted_dft():
+    # Eq. 3 with A: V_n (times the norm) is the DFT of 1_Omega A e^{i Phi} at the spot's bin
+    P, w = 16, 5.0
+    rng = np.random.default_rng(77)
+    xyz = _on_grid_spots(P, 6, rng)
+    phi = rng.uniform(-np.pi, np.pi, P * P)
+    om = oracle.pupil_pixels(P, "round")
+    A = oracle.pupil_amplitude(P, w)
+    V = oracle.forward_pupil(P, xyz, phi[om], om, A[om], 2.5)
+    field = np.zeros(P * P, dtype=complex)
+    field[om] = A[om] * np.exp(1j * phi[om])
+    F = np.fft.fft2(field.reshape(P, P)) / 2.5
+    for n, (al, be, _) in enumerate(xyz):
+        ref = np.exp(1j * np.pi * (al + be)) * F[int(be) % P, int(al) % P]
+        assert abs(V[n] - ref) < 1e-12
+
+
+@pytest.mark.parametrize("aperture,waist", [("round", 0.0), ("round", 9.0), ("square", 7.0)])
+def test_metrics_with_pupil_parseval(aperture, waist):
+    # all P^2 on-grid modes as spots: sum_n I_n = P^2 sum A^2 / (sum A)^2 over the
+    # pupil (Parseval with the single-spot normalisation), for any phase map
+    P = 8
+    a = np.arange(P * P) % P - P // 2
+    b = np.arange(P * P) // P - P // 2
+    xyz = np.stack([a, b, np.zeros(P * P)], axis=1).astype(float)
+    om = oracle.pupil_pixels(P, aperture)
+    A = oracle.pupil_amplitude(P, waist)[om]
+    rng = np.random.default_rng(5)
+    phi = rng.uniform(0, 2 * np.pi, P * P)
+    e, u, In, V = oracle.metrics(P, xyz, phi, aperture, waist)
+    assert e == pytest.approx(P * P * np.sum(A ** 2) / np.sum(A) ** 2, rel=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["fresh", "windows"])
+def test_single_spot_closed_form_round_gaussian_pupil(mode):
+    # N = 1, theta^0 = 0: Phi = phi_1 mod 2 pi on the pupil, 0 outside it; the
+    # spot takes all the light, e = u = 1, whatever A is
+    P = 32
+    xyz = np.array([[4.3, -2.8, 1.9]])
+    res = oracle.solve(P, xyz, c=0.25, iterations=4, seed=3, theta_in=np.zeros(1), aperture="round",
+                       waist=11.0, subset_mode=mode)
+    om = oracle.pupil_pixels(P, "round")
+    out = np.setdiff1d(np.arange(P * P), om)
+    ref = np.array([oracle.spot_phase(P, xyz, 0, int(m)) for m in om]) % (2 * np.pi)
+    assert np.max(np.abs(wrap(res["phase"][om] - ref))) < 1e-12
+    assert np.all(res["phase"][out] == 0.0)
+    assert res["e"] == pytest.approx(1.0, abs=1e-12)
+    assert res["u"] == pytest.approx(1.0, abs=1e-12)
+
+
+def test_wide_beam_is_uniform_pupil():
+    # a beam far wider than the aperture: A -> 1, the uniform result
+    P = 16
+    xyz = np.array([[1.2, -3.4, 0.5], [2.5, 4.1, -1.0], [-5.0, 0.3, 0.2]])
+    a = oracle.solve(P, xyz, c=0.5, iterations=4, seed=2, aperture="round", waist=1e9)
+    b = oracle.solve(P, xyz, c=0.5, iterations=4, seed=2, aperture="round")
+    assert np.max(np.abs(wrap(a["phase"] - b["phase"]))) < 1e-9
+    assert a["e"] == pytest.approx(b["e"], abs=1e-12) and a["u"] == pytest.approx(b["u"], abs=1e-12)
+
+
+def test_wgs_converges_in_round_gaussian_pupil():
+    P = 32
+    xyz = np.array([[-7, -7, 0], [7, -7, 0], [-7, 7, 0], [7, 7, 0], [0, 0, 0]], float)
+    rs = oracle.solve(P, xyz, c=1.0, iterations=0, seed=1, aperture="round", waist=14.0)
+    wgs = oracle.solve(P, xyz, c=1.0, iterations=30, seed=1, aperture="round", waist=14.0)
+    assert wgs["u"] > 0.99 and wgs["u"] > rs["u"]
+    assert 0.5 < wgs["e"] <= 1 + 1e-9 and np.all(wgs["w"] > 0)
+
+
+def test_bruteforce_high_precision_round_gaussian_windows():
+    # the whole method with the paper's own pupil and subset reading, re-run in
+    # 40-digit arithmetic on an 8x8 grid: round aperture (47 pixels), Gaussian
+    # A, windows of one permutation, 2 compressed + 1 full iteration
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    P, c, I, seed, waist = 8, 0.5, 3, 12, 3.0
+    xyz = np.array([[0.7, -1.1, 0.4], [-1.3, 0.9, -0.6]])
+    N = 2
+    res = oracle.solve(P, xyz, c=c, iterations=I, seed=seed, full_iterations=1, aperture="round",
+                       waist=waist, subset_mode="windows")
+    pi = mp.pi
+    half = P // 2
+
+    def coords(m):
+        return mp.mpf(int(m % P) - half), mp.mpf(int(m // P) - half)
+
+    def phase(n, m):
+        xp, yp = coords(m)
+        a, b, g = (mp.mpf(float(v)) for v in xyz[n])
+        return 2 * pi * ((a * xp + b * yp) / P + g * (xp * xp + yp * yp) / mp.mpf(half) ** 2)
+
+    def amp(m):
+        xp, yp = coords(m)
+        return mp.exp(-(xp * xp + yp * yp) / mp.mpf(waist) ** 2)
+
+    omega = [m for m in range(P * P) if (m % P - half) ** 2 + (m // P - half) ** 2 <= half * half]
+    assert len(omega) == 47
+    D = len(omega)
+    Mp = int(math.floor(c * D))
+    w = [mp.mpf(1)] * N
+    th = [mp.mpf(float(t)) for t in oracle.theta0(N, seed)]
+    for j in range(1, I + 1):
+        if j == I:
+            pix = omega
+        else:
+            pix = [omega[oracle.permute_domain(D, seed, 0, ((j - 1) * Mp + k) % D)] for k in range(Mp)]
+        Phi = {}
+        for m in pix:
+            s = sum(w[n] * mp.expj(phase(n, m) + th[n]) for n in range(N))
+            Phi[m] = mp.atan2(s.imag, s.real)
+        V = [sum(amp(m) * mp.expj(Phi[m] - phase(n, m)) for m in pix) for n in range(N)]
+        mean = sum(abs(v) for v in V) / N
+        w = [w[n] * mean / abs(V[n]) for n in range(N)]
+        th = [mp.atan2(V[n].imag, V[n].real) for n in range(N)]
+    Phi = {}
+    for m in omega:
+        s = sum(w[n] * mp.expj(phase(n, m) + th[n]) for n in range(N))
+        Phi[m] = mp.atan2(s.imag, s.real)
+    norm = sum(amp(m) for m in omega)
+    In = [abs(sum(amp(m) * mp.expj(Phi[m] - phase(n, m)) for m in omega) / norm) ** 2 for n in range(N)]
+    phi_ref = np.zeros(P * P)
+    for m in omega:
+        phi_ref[m] = float(Phi[m])
+    assert np.max(np.abs(wrap(res["phase"] - phi_ref))) < 1e-12
+    assert np.all(res["phase"][np.setdiff1d(np.arange(P * P), omega)] == 0.0)
+    assert res["e"] == pytest.approx(float(sum(In)), abs=1e-13)
+    assert res["u"] == pytest.approx(float(1 - (max(In) - min(In)) / (max(In) + min(In))), abs=1e-13)
+    assert np.allclose(res["w"], [float(x) for x in w], rtol=1e-12)
