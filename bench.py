@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-scenarios", action="store_true")
+    ap.add_argument("--no-paper-setup", action="store_true",
+                    help="skip the leg with the paper's optics (round aperture, Gaussian beam, windows, SLM frames)")
     return ap.parse_args()
 
 
@@ -474,6 +476,59 @@ def main():
                           "u_mean": float(us.mean()), "u_std": float(us.std()),
                           "e_min": float(es.min()), "u_min": float(us.min())}
         line["quality_paper_scenarios"] = qual
+
+    # the paper's own optics and output (Section 4: round aperture P pixels
+    # across, 6 mm beam waist on 9.2 um pixels; Section 3: one random
+    # reordering of the pupil, gray frames of a 1920 x 1152 panel)
+    if not args.no_paper_setup:
+        from paper_2003_05293_gb300 import SlmFrame
+        waist = 6000.0 / 9.2 * args.P / 1152
+        lut = torch.arange(256, dtype=torch.int32, device="cuda").to(torch.uint8)
+        W, Hh = max(1920, args.P), max(1152, args.P)
+        frames = [torch.zeros((Hh, W), dtype=torch.uint8, device="cuda") for _ in pbs]
+        ppbs = []
+        for pb, fr in zip(pbs, frames):
+            q = workloads.Problem(P=pb.P, xyz=pb.xyz, amp=pb.amp, c=pb.c, iterations=pb.iterations, seed=pb.seed,
+                                  extra=dict(aperture="round", waist=waist, subset_mode="windows",
+                                             slm=SlmFrame(fr, lut, offset_x=(W - pb.P) // 2, offset_y=(Hh - pb.P) // 2)))
+            ppbs.append(q)
+        bp = plan.batch(ppbs, None)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            bp.run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            bp.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msp = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+        rp = bp.results()
+        ktp = bp.kernel_times()
+        bp.close()
+        sq = {}
+        if not args.no_scenarios:
+            for name in workloads.SCENARIOS:
+                spb = [workloads.scenario(name, args.P, seed=s, c=args.c, iterations=args.iters) for s in range(10)]
+                for q in spb:
+                    q.extra.update(aperture="round", waist=waist, subset_mode="windows")
+                r = plan.solve_batch(spb)
+                es = np.array([x["e"] for x in r])
+                us = np.array([x["u"] for x in r])
+                sq[name] = {"e_mean": float(es.mean()), "u_mean": float(us.mean()), "u_min": float(us.min())}
+        line["paper_setup"] = {
+            "value": job_throughput(B, world, args.steps, msp), "unit": "holograms/s", "ms_per_step": msp / args.steps,
+            "compressed_ms_per_launch": sum(ktp[1:1 + n_sub]) / max(1, n_sub),
+            "full_ms_per_launch": sum(ktp[1 + n_sub:]) / max(1, len(ktp) - 1 - n_sub),
+            "e_mean": float(np.mean([x["e"] for x in rp])), "u_mean": float(np.mean([x["u"] for x in rp])),
+            "u_min": float(np.min([x["u"] for x in rp])), "scenarios": sq,
+            "what": "the same batch with a round aperture of P pixels, Gaussian beam of %.1f px waist, subsets as "
+                    "windows of one random order, and each hologram also written as an 8-bit gray frame (256-level "
+                    "table) into its own %d x %d panel buffer" % (waist, W, Hh)}
+        del frames
 
     # continuous-batching server under a Poisson arrival stream
     if not args.no_serve:

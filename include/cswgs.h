@@ -21,12 +21,15 @@
  *    with x' = i - P/2, y' = r - P/2, pixel index m = r * P + i.
  *  - amplitudes: N doubles a_n^0 > 0 (NULL = all 1).
  *  - The phase map is P * P floats, row-major (m = r * P + i), in [0, 2 pi).
+ *  - The pupil (cswgs_pupil) is the whole P x P grid with amplitude A = 1
+ *    unless a request asks for the paper's round aperture or Gaussian beam.
  *  - A plan is not thread-safe: use one plan per host thread, or the
  *    submit / poll serving calls, which are internally locked.
  *  - Argument checks (each failing with CSWGS_EINVAL): 2 <= P <= max_P and P
  *    even; 1 <= N <= max_N; 0 < subset_fraction <= 1 and
- *    Mp = floor(subset_fraction * P * P) >= 1; iterations >= 0; finite spot
- *    coordinates; amplitudes finite and > 0.
+ *    Mp = floor(subset_fraction * D) >= 1, D the pupil's pixel count (P * P
+ *    for the square grid); iterations >= 0; finite spot coordinates;
+ *    amplitudes finite and > 0; a valid pupil and SLM frame when given.
  */
 #ifndef CSWGS_H
 #define CSWGS_H
@@ -38,7 +41,7 @@
 extern "C" {
 #endif
 
-#define CSWGS_ABI_VERSION 1
+#define CSWGS_ABI_VERSION 2
 
 typedef struct cswgs_plan_s *cswgs_plan;
 typedef struct cswgs_batch_s *cswgs_batch;
@@ -60,6 +63,56 @@ typedef enum {
     CSWGS_FP32_FP16SINCOS = 2   /* as FP32, with packed half-precision sincos in the compressed
                                    iterations (phasor error ~1e-3 rad; full iterations and final pass FP32) */
 } cswgs_precision;
+
+/* --------------------------------------------------------------- pupil --- */
+
+typedef enum {
+    CSWGS_APERTURE_SQUARE = 0,  /* every pixel of the P x P grid */
+    CSWGS_APERTURE_ROUND = 1    /* Section 4: the round aperture of diameter P, x'^2 + y'^2 <= (P/2)^2 */
+} cswgs_aperture;
+
+typedef enum {
+    CSWGS_SUBSET_FRESH = 0,     /* a new random order of the pupil's pixels per iteration j (keyed by seed, j) */
+    CSWGS_SUBSET_WINDOWS = 1    /* Section 3: one random order made at the start (keyed by seed, 0); iteration
+                                   j takes its entries (j-1) Mp .. j Mp - 1, wrapping around after the last */
+} cswgs_subset_mode;
+
+/* The light at the SLM and how the subsets are drawn from it (Eq. 3: the
+ * forward projection sums A e^{i(Phi - phi_n)} over the pupil's pixels Omega;
+ * Section 4: the paper's aperture is round, lit by a Gaussian beam).  An
+ * all-zero cswgs_pupil is the default: square grid, A = 1, fresh subsets.
+ * With a pupil:
+ *  - subsets: Mp = floor(c D) of the D pupil pixels, through a keyed
+ *    permutation of [0, D) applied to the pupil's pixels in row-major order;
+ *  - iterations and the final pass run over the pupil's pixels only; the
+ *    phase map holds 0 outside the pupil (no light falls there);
+ *  - the forward projection weighs each pixel by A (Eq. 3);
+ *  - e, u: V_n = sum_Omega A e^{i(Phi - phi_n)} / sum_Omega A, so that a
+ *    hologram putting all the light into one spot has e = 1. */
+typedef struct {
+    int aperture;               /* cswgs_aperture */
+    int subset_mode;            /* cswgs_subset_mode */
+    double beam_waist;          /* Gaussian beam radius in pixels (1/e^2 of the intensity):
+                                   A = exp(-(x'^2 + y'^2) / waist^2); 0: uniform A = 1 */
+} cswgs_pupil;
+
+/* Headless SLM output (Section 3: the hologram goes straight to the SLM; the
+ * phase-to-gray lookup table is uploaded once at start-up).  The final pass
+ * writes, for every grid pixel (i, r), the gray value
+ *     frame[(offset_y + r) * pitch + offset_x + i] = lut[l],
+ *     l = rint(Phi * s) mod levels,  s = (float)(levels / (2 pi)),
+ * with the product and the rounding in FP32 (Phi the float phase in
+ * [0, 2 pi); pixels outside the pupil have Phi = 0).  Frame pixels outside
+ * the P x P grid are not touched.  The structure is copied at the call; the
+ * frame and the table must stay valid until the hologram is finished. */
+typedef struct {
+    uint8_t *frame;             /* device, height rows of `pitch` bytes, caller-owned */
+    int width, height;          /* frame size in pixels */
+    int pitch;                  /* bytes per frame row, >= width */
+    int offset_x, offset_y;     /* frame position of grid pixel (0, 0); the grid must lie inside the frame */
+    const uint8_t *lut;         /* device, `levels` gray values: lut[l] for phase 2 pi l / levels */
+    int levels;                 /* 2 .. 65536 */
+} cswgs_slm_frame;
 
 /* ---------------------------------------------------------------- plan --- */
 
@@ -117,14 +170,18 @@ typedef struct {
     double *final_w;            /* host, N: the weights after the last iteration, or NULL */
     double *final_theta;        /* host, N: the spot phases after the last iteration (radians), or NULL */
     double *spot_intensity;     /* host, N: I_n = |V_n|^2 of the final hologram, or NULL */
+    cswgs_pupil pupil;          /* aperture, beam and subset reading (default all zero: square, A = 1, fresh) */
+    const cswgs_slm_frame *slm; /* gray-level SLM frame written by the final pass, or NULL */
 } cswgs_solve_opts;
 
 void cswgs_solve_opts_default(cswgs_solve_opts *o);
 
 /* cswgs_solve with options: resume from or teacher-force a state (init_w,
  * init_theta, first_iteration), choose the schedule (full_iterations), skip
- * the final pass, and read back the state.  With final_pass = 0 the phase
- * map, e and u are not written (phase_out may be NULL). */
+ * the final pass, read back the state, take the paper's round aperture and
+ * Gaussian beam (pupil), and write an SLM frame.  With final_pass = 0 the
+ * phase map, frame, e and u are not written (phase_out may be NULL).  The
+ * FP64 baseline solver takes the default pupil and no SLM frame only. */
 cswgs_status cswgs_solve_ex(cswgs_plan p, const double *spots_xyz, const double *amplitudes,
                             int N, int P, double subset_fraction, int iterations, uint64_t seed,
                             const cswgs_solve_opts *opts, float *phase_out, int out_on_host,
@@ -137,6 +194,14 @@ cswgs_status cswgs_solve_ex(cswgs_plan p, const double *spots_xyz, const double 
  * caller-owned.  Runs the same device code the solver uses.  Synchronous. */
 cswgs_status cswgs_subset(cswgs_plan p, int P, int64_t Mp, uint64_t seed, int j,
                           int32_t *out_device);
+
+/* The subset S_j of iteration j under a pupil (NULL: the default pupil):
+ * *count = Mp = floor(subset_fraction * D) pixel indices m = r * P + i of
+ * the pupil's pixels, in the order the solver visits them, written to
+ * out_device (device int32, caller-owned, room for D entries).  Same device
+ * code as the solver.  Synchronous. */
+cswgs_status cswgs_subset_ex(cswgs_plan p, int P, double subset_fraction, uint64_t seed, int j,
+                             const cswgs_pupil *pupil, int32_t *out_device, int64_t *count);
 
 /* ------------------------------------------------- batches and graphs --- */
 
@@ -152,6 +217,8 @@ typedef struct {
     int full_iterations;        /* < 0: the default 2 */
     float *phase_out;           /* P*P floats: device pointer, or host when out_on_host; NULL: not written */
     int out_on_host;
+    cswgs_pupil pupil;          /* default all zero: square, A = 1, fresh subsets */
+    const cswgs_slm_frame *slm; /* gray-level SLM frame written by the final pass, or NULL */
 } cswgs_request;
 
 typedef struct {

@@ -315,3 +315,16 @@ def subset_size(P: int, c: float, aperture: str = "square") -> int:
     import math
     D = P * P if aperture == "square" else int(_load().oracle_pupil_pixels(P, APERTURES[aperture], None))
     return int(math.floor(c * D))
+
+
+def slm_gray(phase_f32, lut, levels: int):
+    """Gray frame of a float32 phase map (Section 3: phase to gray-scale lookup
+    table of the SLM).  The level decision is made in float32, as the library
+    defines it: l = rint(Phi * s) mod levels, s = float32(levels / (2 pi)),
+    gray = lut[l].  Takes the phase the decision is made from, so that both
+    sides decide from the same float."""
+    ph = np.asarray(phase_f32, dtype=np.float32)
+    s = np.float32(levels / (2.0 * np.pi))
+    lvl = np.rint(ph * s).astype(np.int64)
+    lvl = np.where(lvl >= levels, lvl - levels, lvl)
+    return np.asarray(lut, dtype=np.uint8)[lvl]

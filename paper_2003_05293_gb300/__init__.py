@@ -18,12 +18,46 @@ import numpy as np
 
 from . import capi
 from .capi import (CSWGS_FP32, CSWGS_FP32_FP16SINCOS, CSWGS_FP64, CswgsError, check,
-                   cswgs_plan_desc, cswgs_request, cswgs_result, cswgs_serve_stats,
-                   cswgs_solve_opts)
+                   cswgs_plan_desc, cswgs_pupil, cswgs_request, cswgs_result, cswgs_serve_stats,
+                   cswgs_slm_frame, cswgs_solve_opts)
 
-__all__ = ["Plan", "Batch", "CswgsError", "PRECISIONS", "capi"]
+__all__ = ["Plan", "Batch", "CswgsError", "PRECISIONS", "APERTURES", "SUBSET_MODES", "SlmFrame", "capi"]
 
 PRECISIONS = {"fp64": CSWGS_FP64, "fp32": CSWGS_FP32, "fp32_fp16sincos": CSWGS_FP32_FP16SINCOS}
+APERTURES = {"square": capi.CSWGS_APERTURE_SQUARE, "round": capi.CSWGS_APERTURE_ROUND}
+SUBSET_MODES = {"fresh": capi.CSWGS_SUBSET_FRESH, "windows": capi.CSWGS_SUBSET_WINDOWS}
+
+
+def _pupil(aperture="square", waist=0.0, subset_mode="fresh"):
+    p = cswgs_pupil()
+    p.aperture = APERTURES[aperture]
+    p.subset_mode = SUBSET_MODES[subset_mode]
+    p.beam_waist = float(waist)
+    return p
+
+
+def _u8ptr(t):
+    return ctypes.cast(ctypes.c_void_p(t.data_ptr()), capi.c_uint8_p)
+
+
+class SlmFrame:
+    """A gray-level SLM frame on the device (cswgs_slm_frame): `frame` a uint8
+    CUDA tensor of shape (height, pitch), `lut` a uint8 CUDA tensor of the phase
+    levels' gray values, the grid placed at (offset_x, offset_y)."""
+
+    def __init__(self, frame, lut, width=None, offset_x=0, offset_y=0):
+        if frame.dtype.__str__() != "torch.uint8" or frame.dim() != 2 or not frame.is_contiguous():
+            raise ValueError("frame must be a contiguous 2D uint8 CUDA tensor")
+        if lut.dtype.__str__() != "torch.uint8" or lut.dim() != 1 or not lut.is_contiguous():
+            raise ValueError("lut must be a contiguous 1D uint8 CUDA tensor")
+        self.frame, self.lut = frame, lut
+        self.c = cswgs_slm_frame()
+        self.c.frame = _u8ptr(frame)
+        self.c.height, self.c.pitch = frame.shape
+        self.c.width = frame.shape[1] if width is None else int(width)
+        self.c.offset_x, self.c.offset_y = int(offset_x), int(offset_y)
+        self.c.lut = _u8ptr(lut)
+        self.c.levels = lut.shape[0]
 
 
 def _dptr(a):
@@ -97,8 +131,10 @@ class Plan:
     # ------------------------------------------------------------- solve --
     def solve(self, xyz, P: int, c: float, iterations: int, seed: int, amp=None, out=None,
               full_iterations: int = 2, first_iteration: int = 1, final_pass: bool = True,
-              init_w=None, init_theta=None, state: bool = False):
-        """cswgs_solve_ex; returns dict(e, u[, w, theta, I])."""
+              init_w=None, init_theta=None, state: bool = False, aperture: str = "square",
+              waist: float = 0.0, subset_mode: str = "fresh", slm: "SlmFrame" = None):
+        """cswgs_solve_ex; returns dict(e, u[, w, theta, I]).  aperture, waist
+        and subset_mode give the pupil (cswgs_pupil); slm an SLM frame."""
         xyz = _f64(xyz, (-1, 3))
         N = xyz.shape[0]
         amp = _f64(amp)
@@ -117,6 +153,9 @@ class Plan:
         o.final_w = _dptr(w)
         o.final_theta = _dptr(th)
         o.spot_intensity = _dptr(In)
+        o.pupil = _pupil(aperture, waist, subset_mode)
+        if slm is not None:
+            o.slm = ctypes.pointer(slm.c)
         ptr, host = _out_ptr(out)
         e = ctypes.c_double(float("nan"))
         u = ctypes.c_double(float("nan"))
@@ -145,6 +184,17 @@ class Plan:
         ptr = ctypes.cast(ctypes.c_void_p(out.data_ptr()), ctypes.POINTER(ctypes.c_int32))
         check(self.lib.cswgs_subset(self.handle, P, Mp, int(seed) & (2**64 - 1), j, ptr), "cswgs_subset")
 
+    def subset_ex(self, P: int, c: float, seed: int, j: int, out, aperture: str = "square",
+                  subset_mode: str = "fresh") -> int:
+        """cswgs_subset_ex into a CUDA int32 tensor with room for the pupil's
+        pixel count; returns the subset size Mp."""
+        ptr = ctypes.cast(ctypes.c_void_p(out.data_ptr()), ctypes.POINTER(ctypes.c_int32))
+        pu = _pupil(aperture, 0.0, subset_mode)
+        n = ctypes.c_int64()
+        check(self.lib.cswgs_subset_ex(self.handle, P, float(c), int(seed) & (2**64 - 1), j, ctypes.byref(pu),
+                                       ptr, ctypes.byref(n)), "cswgs_subset_ex")
+        return n.value
+
     # ----------------------------------------------------------- batches --
     def _requests(self, problems, outs):
         n = len(problems)
@@ -162,7 +212,14 @@ class Plan:
             r.subset_fraction = pb.c
             r.iterations = pb.iterations
             r.seed = int(pb.seed) & (2**64 - 1)
-            r.full_iterations = int(pb.extra.get("full_iterations", 2)) if hasattr(pb, "extra") else 2
+            extra = getattr(pb, "extra", {}) or {}
+            r.full_iterations = int(extra.get("full_iterations", 2))
+            r.pupil = _pupil(extra.get("aperture", "square"), extra.get("waist", 0.0),
+                             extra.get("subset_mode", "fresh"))
+            slm = extra.get("slm")
+            if slm is not None:
+                r.slm = ctypes.pointer(slm.c)
+                keep.append(slm)
             ptr, host = _out_ptr(outs[i] if outs is not None else None)
             r.phase_out = ptr
             r.out_on_host = host

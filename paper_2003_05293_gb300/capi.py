@@ -26,11 +26,27 @@ class cswgs_plan_desc(ctypes.Structure):
                 ("tune_cache", ctypes.c_char_p)]
 
 
+CSWGS_APERTURE_SQUARE, CSWGS_APERTURE_ROUND = range(2)
+CSWGS_SUBSET_FRESH, CSWGS_SUBSET_WINDOWS = range(2)
+c_uint8_p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class cswgs_pupil(ctypes.Structure):
+    _fields_ = [("aperture", ctypes.c_int), ("subset_mode", ctypes.c_int), ("beam_waist", ctypes.c_double)]
+
+
+class cswgs_slm_frame(ctypes.Structure):
+    _fields_ = [("frame", c_uint8_p), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("pitch", ctypes.c_int), ("offset_x", ctypes.c_int), ("offset_y", ctypes.c_int),
+                ("lut", c_uint8_p), ("levels", ctypes.c_int)]
+
+
 class cswgs_solve_opts(ctypes.Structure):
     _fields_ = [("full_iterations", ctypes.c_int), ("first_iteration", ctypes.c_int),
                 ("final_pass", ctypes.c_int), ("init_w", c_double_p), ("init_theta", c_double_p),
                 ("final_w", c_double_p), ("final_theta", c_double_p),
-                ("spot_intensity", c_double_p)]
+                ("spot_intensity", c_double_p), ("pupil", cswgs_pupil),
+                ("slm", ctypes.POINTER(cswgs_slm_frame))]
 
 
 class cswgs_request(ctypes.Structure):
@@ -38,7 +54,8 @@ class cswgs_request(ctypes.Structure):
                 ("P", ctypes.c_int), ("subset_fraction", ctypes.c_double),
                 ("iterations", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("full_iterations", ctypes.c_int), ("phase_out", c_float_p),
-                ("out_on_host", ctypes.c_int)]
+                ("out_on_host", ctypes.c_int), ("pupil", cswgs_pupil),
+                ("slm", ctypes.POINTER(cswgs_slm_frame))]
 
 
 class cswgs_result(ctypes.Structure):
@@ -70,6 +87,9 @@ SIGNATURES = {
                                       c_double_p, c_double_p]),
     "cswgs_subset": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_int32)]),
+    "cswgs_subset_ex": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int,
+                                       ctypes.POINTER(cswgs_pupil), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int64)]),
     "cswgs_batch_create": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_request), ctypes.c_int,
                                           ctypes.POINTER(_P)]),
     "cswgs_batch_run": (ctypes.c_int, [_P]),

@@ -19,8 +19,9 @@ static std::string shape_key(const std::vector<HoloSpec> &v, bool host_out)
     std::string k = host_out ? "H" : "D";
     char buf[160];
     for (auto &s : v) {
-        snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%d,%d,%d,%d%d%d", s.P, s.N, s.Mp, s.iterations, s.n_full,
-                 s.first_j, s.final_pass, (int)s.has_amp, (int)s.has_init_w, (int)s.has_init_th);
+        snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%d,%d,%d,%d%d%d,%d%d", s.P, s.N, s.Mp, s.iterations, s.n_full,
+                 s.first_j, s.final_pass, (int)s.has_amp, (int)s.has_init_w, (int)s.has_init_th, s.aperture,
+                 s.windows);
         k += buf;
     }
     return k;
@@ -110,10 +111,10 @@ static cswgs_status solve_fp32(cswgs_plan_s *p, HoloSpec h, float *phase_out, in
     } else {
         b = it->second.get();
         b->specs[0] = std::move(h);
-        b->specs[0].seed = v[0].seed;
-        b->holos[0].seed = v[0].seed;
+        b->holos[0].seed = b->specs[0].seed;
+        fill_pupil(b->holos[0], b->specs[0]);
         batch_restage(b, 0);
-        // the seed lives in the device hologram record
+        // the seed, the beam and the SLM frame live in the device hologram record
         CSWGS_CUDA_TRY(cudaMemcpyAsync(b->holos_d.p, b->holos.data(), sizeof(HoloDev), cudaMemcpyHostToDevice,
                                        p->stream));
     }
@@ -269,6 +270,10 @@ cswgs_status cswgs_solve_ex(cswgs_plan p, const double *spots_xyz, const double 
     HoloSpec h;
     CSWGS_TRY(validate_request(p->desc, spots_xyz, amplitudes, N, P, subset_fraction, iterations,
                                o.full_iterations, &h));
+    CSWGS_TRY(apply_pupil(p, o.pupil, subset_fraction, &h));
+    CSWGS_TRY(apply_slm(o.slm, &h));
+    if (p->desc.precision == CSWGS_FP64 && (h.aperture || h.windows || h.waist > 0.0 || h.has_slm))
+        return set_error(CSWGS_EINVAL, "the FP64 baseline solver takes the default pupil and no SLM frame");
     h.seed = seed;
     h.first_j = o.first_iteration;
     h.final_pass = o.final_pass ? 1 : 0;
@@ -315,6 +320,33 @@ cswgs_status cswgs_subset(cswgs_plan p, int P, int64_t Mp, uint64_t seed, int j,
     return CSWGS_OK;
 }
 
+cswgs_status cswgs_subset_ex(cswgs_plan p, int P, double subset_fraction, uint64_t seed, int j,
+                             const cswgs_pupil *pupil, int32_t *out_device, int64_t *count)
+{
+    if (!p || !out_device) return set_error(CSWGS_EINVAL, "NULL plan or output");
+    if (P < 2 || (P & 1) || P > p->desc.max_P) return set_error(CSWGS_EINVAL, "P=%d out of range", P);
+    if (!(subset_fraction > 0.0 && subset_fraction <= 1.0))
+        return set_error(CSWGS_EINVAL, "subset fraction %g not in (0, 1]", subset_fraction);
+    if (j < 0) return set_error(CSWGS_EINVAL, "j=%d < 0", j);
+    HoloSpec h;
+    h.P = P;
+    cswgs_pupil pu{};
+    if (pupil) pu = *pupil;
+    CSWGS_TRY(apply_pupil(p, pu, subset_fraction, &h));
+    if (count) *count = h.Mp;
+    HoloDev H;
+    std::memset(&H, 0, sizeof H);
+    H.P = P;
+    H.Mp = h.Mp;
+    H.seed = seed;
+    fill_pupil(H, h);
+    std::lock_guard<std::mutex> lk(p->mu);
+    CSWGS_TRY(set_device(p));
+    CSWGS_CUDA_TRY(launch_subset_ex_kernel(H, j, out_device, p->stream));
+    CSWGS_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return CSWGS_OK;
+}
+
 static cswgs_status specs_from_requests(cswgs_plan p, const cswgs_request *reqs, int count,
                                         std::vector<HoloSpec> *out)
 {
@@ -327,6 +359,11 @@ static cswgs_status specs_from_requests(cswgs_plan p, const cswgs_request *reqs,
         HoloSpec h;
         cswgs_status st = validate_request(p->desc, r.spots_xyz, r.amplitudes, r.N, r.P, r.subset_fraction,
                                            r.iterations, r.full_iterations, &h);
+        if (st == CSWGS_OK) st = apply_pupil(p, r.pupil, r.subset_fraction, &h);
+        if (st == CSWGS_OK) st = apply_slm(r.slm, &h);
+        if (st == CSWGS_OK && p->desc.precision == CSWGS_FP64 &&
+            (h.aperture || h.windows || h.waist > 0.0 || h.has_slm))
+            st = set_error(CSWGS_EINVAL, "the FP64 baseline solver takes the default pupil and no SLM frame");
         if (st != CSWGS_OK) return set_error(st, "request %d: %s", i, cswgs::last_error());
         h.seed = r.seed;
         out->push_back(std::move(h));
@@ -491,18 +528,25 @@ cswgs_status cswgs_solve_batch(cswgs_plan p, const cswgs_request *reqs, int coun
         p->solve_cache[key] = std::move(nb);
     } else {
         b = it->second.get();
-        bool seeds = false;
+        bool changed = false;
         for (int i = 0; i < count; ++i) {
             b->specs[i].xyz = specs[i].xyz;
             b->specs[i].amp = specs[i].amp;
-            if (b->holos[i].seed != specs[i].seed) {
-                b->holos[i].seed = specs[i].seed;
-                b->specs[i].seed = specs[i].seed;
-                seeds = true;
+            b->specs[i].seed = specs[i].seed;
+            b->specs[i].waist = specs[i].waist;
+            b->specs[i].norm = specs[i].norm;
+            b->specs[i].has_slm = specs[i].has_slm;
+            b->specs[i].slm = specs[i].slm;
+            HoloDev H = b->holos[i];
+            H.seed = specs[i].seed;
+            fill_pupil(H, b->specs[i]);
+            if (std::memcmp(&H, &b->holos[i], sizeof H) != 0) {
+                b->holos[i] = H;
+                changed = true;
             }
             batch_restage(b, i);
         }
-        if (seeds)
+        if (changed)
             CSWGS_CUDA_TRY(cudaMemcpyAsync(b->holos_d.p, b->holos.data(), sizeof(HoloDev) * count,
                                            cudaMemcpyHostToDevice, p->stream));
     }

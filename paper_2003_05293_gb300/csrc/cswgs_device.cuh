@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace cswgs {
@@ -57,28 +58,64 @@ __host__ __device__ __forceinline__ SubsetKeys subset_keys(uint64_t seed, int j)
     return K;
 }
 
-__device__ __forceinline__ void feistel_round(uint32_t &L, uint32_t &R, uint32_t key, uint32_t P)
+// One round (L, R) -> (R, (L + F(R)) mod p), F(R) = floor(fmix32(R ^ key) p / 2^32),
+// p the modulus of the incoming L.
+__device__ __forceinline__ void feistel_round(uint32_t &L, uint32_t &R, uint32_t key, uint32_t p)
 {
-    uint32_t F = __umulhi(fmix32(R ^ key), P);   // in [0, P)
+    uint32_t F = __umulhi(fmix32(R ^ key), p);   // in [0, p)
     uint32_t nr = L + F;
-    nr = nr >= P ? nr - P : nr;                  // (L + F) mod P, both < P
+    nr = nr >= p ? nr - p : nr;                  // (L + F) mod p, both < p
     L = R;
     R = nr;
 }
 
-// pi_{seed,j}(k): keyed bijection of [0, P^2).  k = L P + R; four rounds of
-// (L, R) -> (R, (L + F(R)) mod P); result L P + R.  The subset S_j of an
-// iteration is the image of [0, Mp) (Section 2, CS-WGS; Section 3,
-// "Compressed sensing": a random pixel order, c M pixels per iteration).
+// Keyed bijection of [0, a b): k = L b + R with L in [0, a), R in [0, b);
+// four rounds whose moduli alternate a, b, a, b (each round swaps the two
+// halves' ranges); result L b + R.
+__device__ __forceinline__ uint32_t permute_rect(uint32_t k, uint32_t a, uint32_t b, const SubsetKeys &K)
+{
+    uint32_t L = k / b;
+    uint32_t R = k - L * b;
+    feistel_round(L, R, K.k0, a);
+    feistel_round(L, R, K.k1, b);
+    feistel_round(L, R, K.k2, a);
+    feistel_round(L, R, K.k3, b);
+    return L * b + R;
+}
+
+// pi_{seed,j}(k): keyed bijection of [0, P^2), the square grid's subset order.
+// The subset S_j of an iteration is the image of [0, Mp) (Section 2, CS-WGS;
+// Section 3, "Compressed sensing": a random pixel order, c M pixels per
+// iteration).
 __device__ __forceinline__ uint32_t permute(uint32_t k, uint32_t P, const SubsetKeys &K)
 {
-    uint32_t L = k / P;
-    uint32_t R = k - L * P;
-    feistel_round(L, R, K.k0, P);
-    feistel_round(L, R, K.k1, P);
-    feistel_round(L, R, K.k2, P);
-    feistel_round(L, R, K.k3, P);
-    return L * P + R;
+    return permute_rect(k, P, P, K);
+}
+
+// Keyed bijection of [0, D) for any D, on the rectangle a x b >= D (a the
+// smallest integer with a^2 >= D, b = ceil(D / a)): values that land at or
+// beyond D go through the rectangle's permutation again (cycle walking).  The
+// walk from k < D meets at most a b - D values >= D before it returns below
+// D, so the loop bound never cuts a walk short; the final clamp only keeps a
+// corrupted input in range.
+__device__ __forceinline__ uint32_t permute_domain(uint32_t k, uint32_t D, uint32_t a, uint32_t b,
+                                                   const SubsetKeys &K)
+{
+    uint32_t y = permute_rect(k, a, b, K);
+    const uint32_t extra = a * b - D;
+    for (uint32_t s = 0; y >= D && s < extra; ++s) y = permute_rect(y, a, b, K);
+    return y < D ? y : 0u;
+}
+
+// Host side: the rectangle of permute_domain for a domain of D >= 1 values.
+inline void permute_rect_of(uint32_t D, uint32_t *a, uint32_t *b)
+{
+    uint64_t x = (uint64_t)sqrt((double)D);
+    while (x * x < D) ++x;
+    while (x > 1 && (x - 1) * (x - 1) >= D) --x;
+    if (x == 0) x = 1;
+    *a = (uint32_t)x;
+    *b = (uint32_t)((D + x - 1) / x);
 }
 
 // ------------------------------------------------------ fixed-point phase --

@@ -27,10 +27,12 @@ struct SpotState {
 };
 
 // One hologram's device buffers (FP32 solver).  All pointers are device.
+// The pupil fields describe the square uniform grid when a hologram asks for
+// no other pupil: D = P^2, fa = fb = P, aperture 0, kA 0, norm = P^2.
 struct HoloDev {
     int P, N;
-    int Mp;                 // subset size floor(c M)
-    int pad0;
+    int Mp;                 // subset size floor(c D)
+    int D;                  // pupil pixel count
     uint64_t seed;
     const double *xyz;      // N x 3 inputs
     const double *amp;      // N or nullptr
@@ -43,6 +45,21 @@ struct HoloDev {
     unsigned *counter;      // tiles finished in the current pass
     float *phase_out;       // M or nullptr
     double *metrics;        // 2 + N: e, u, I_0 .. I_{N-1}
+    // pupil (Section 4; Eq. 3's A) and the subset reading (Section 3)
+    const int2 *rows;       // round aperture: P + 1 entries {first pupil index of row r, its first column}
+    uint32_t fa, fb;        // rectangle fa x fb >= D of the subset permutation
+    int aperture;           // cswgs_aperture
+    int windows;            // 1: windows of one permutation; 0: a new permutation per iteration
+    float kA;               // A = exp2(-kA rho^2); 0: uniform
+    int pad1;
+    double norm;            // sum of A over the pupil (metrics normalisation)
+    // SLM frame written by the final pass (nullptr: none)
+    uint8_t *slm;           // frame address of grid pixel (0, 0)
+    const uint8_t *lut;     // levels gray values
+    int slm_pitch;          // bytes per frame row
+    int levels;
+    float lscale;           // (float)(levels / (2 pi))
+    int pad2;
 };
 
 // One hologram's share of one persistent launch.
@@ -76,6 +93,7 @@ bool tile_shape_supported(TileShape shape);
 size_t iter_fp32_smem(TileShape shape, int kind, int maxN);
 cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_t *out,
                                  cudaStream_t s);
+cudaError_t launch_subset_ex_kernel(const HoloDev &H, int j, int32_t *out, cudaStream_t s);
 cudaError_t launch_sincos_probe(float *sink, long long *cycles, int iters, int blocks,
                                 int threads, cudaStream_t s);
 

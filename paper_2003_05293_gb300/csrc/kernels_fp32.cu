@@ -129,6 +129,15 @@ __global__ void subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_t *
         out[k] = (int32_t)permute((uint32_t)k, (uint32_t)P, K);
 }
 
+// S_j under a pupil and subset reading: the solver's own pixel mapping.
+__global__ void subset_ex_kernel(HoloDev H, int j, int32_t *out)
+{
+    const SubsetDraw d = subset_draw(H, j);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < H.Mp;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = (int32_t)subset_pixel(H, d, (uint32_t)k);
+}
+
 // Throughput probe: eight independent sine/cosine chains per thread.
 __global__ void sincos_probe_kernel(float *sink, long long *cycles, int iters)
 {
@@ -259,6 +268,16 @@ cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_
     if (blocks < 1) blocks = 1;
     (void)cudaGetLastError();
     subset_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, Mp, seed, j, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_subset_ex_kernel(const HoloDev &H, int j, int32_t *out, cudaStream_t s)
+{
+    int64_t blocks = ((int64_t)H.Mp + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    (void)cudaGetLastError();
+    subset_ex_kernel<<<(unsigned)blocks, 256, 0, s>>>(H, j, out);
     return cudaGetLastError();
 }
 

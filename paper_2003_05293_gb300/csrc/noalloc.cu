@@ -151,6 +151,9 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
     H.P = P;
     H.N = N;
     H.Mp = Mp;
+    H.D = M;
+    H.fa = H.fb = (uint32_t)P;
+    H.norm = (double)M;
     H.seed = seed;
     H.xyz = spots_xyz;
     H.amp = amplitudes;

@@ -53,12 +53,131 @@ cswgs_status validate_request(const cswgs_plan_desc &d, const double *xyz, const
     out->P = P;
     out->N = N;
     out->Mp = (int)Mp;
+    out->D = (int)M;
+    out->fa = out->fb = (uint32_t)P;
+    out->norm = (double)M;
     out->iterations = iterations;
     out->n_full = n_full < 0 ? 2 : n_full;
     out->xyz.assign(xyz, xyz + (size_t)N * 3);
     out->has_amp = amp != nullptr;
     if (amp) out->amp.assign(amp, amp + N);
     return CSWGS_OK;
+}
+
+// Row r of the round aperture (y' = r - P/2): columns with x'^2 + y'^2 <=
+// (P/2)^2, i.e. |x'| <= h = isqrt((P/2)^2 - y'^2), clipped to x' <= P/2 - 1.
+static void round_row(int P, int r, int *first_col, int *count)
+{
+    const int64_t half = P / 2, y = r - half;
+    const int64_t rem = half * half - y * y;
+    int64_t h = (int64_t)std::sqrt((double)rem);
+    while (h * h > rem) --h;
+    while ((h + 1) * (h + 1) <= rem) ++h;
+    const int64_t hi = std::min<int64_t>(h, half - 1);
+    *first_col = (int)(half - h);
+    *count = (int)(hi + h + 1);
+}
+
+cswgs_status apply_pupil(cswgs_plan_s *p, const cswgs_pupil &pu, double c, HoloSpec *h)
+{
+    if (pu.aperture != CSWGS_APERTURE_SQUARE && pu.aperture != CSWGS_APERTURE_ROUND)
+        return set_error(CSWGS_EINVAL, "unknown aperture %d", pu.aperture);
+    if (pu.subset_mode != CSWGS_SUBSET_FRESH && pu.subset_mode != CSWGS_SUBSET_WINDOWS)
+        return set_error(CSWGS_EINVAL, "unknown subset mode %d", pu.subset_mode);
+    if (!std::isfinite(pu.beam_waist) || pu.beam_waist < 0.0)
+        return set_error(CSWGS_EINVAL, "beam waist %g: need finite and >= 0 (0 = uniform)", pu.beam_waist);
+    const int P = h->P, half = P / 2;
+    h->aperture = pu.aperture;
+    h->windows = pu.subset_mode;
+    h->waist = pu.beam_waist;
+    // the amplitude is separable: A = ex(x') ex(y')
+    std::vector<double> ex(P, 1.0), pre(P + 1, 0.0);
+    if (h->waist > 0.0)
+        for (int i = 0; i < P; ++i) {
+            const double x = (double)(i - half);
+            ex[i] = std::exp(-x * x / (h->waist * h->waist));
+        }
+    for (int i = 0; i < P; ++i) pre[i + 1] = pre[i] + ex[i];
+    int64_t D = 0;
+    double norm = 0.0;
+    std::vector<int2> rows;
+    if (h->aperture == CSWGS_APERTURE_ROUND) {
+        rows.resize(P + 1);
+        for (int r = 0; r < P; ++r) {
+            int c0 = 0, cnt = 0;
+            round_row(P, r, &c0, &cnt);
+            rows[r] = make_int2((int)D, c0);
+            D += cnt;
+            norm += ex[r] * (pre[c0 + cnt] - pre[c0]);
+        }
+        rows[P] = make_int2((int)D, 0);
+    } else {
+        D = (int64_t)P * P;
+        norm = pre[P] * pre[P];
+    }
+    const int64_t Mp = (int64_t)std::floor(c * (double)D);
+    if (Mp < 1) return set_error(CSWGS_EINVAL, "subset fraction %g gives an empty subset of %lld pupil pixels", c,
+                                 (long long)D);
+    h->D = (int)D;
+    h->Mp = (int)Mp;
+    h->norm = norm;
+    permute_rect_of((uint32_t)D, &h->fa, &h->fb);
+    h->rows = nullptr;
+    if (h->aperture == CSWGS_APERTURE_ROUND) {
+        std::lock_guard<std::mutex> lk(p->pupil_mu);
+        auto &slot = p->pupil_rows[P];
+        if (!slot) {
+            auto buf = std::make_unique<DevBuf>();
+            CSWGS_TRY(buf->ensure(sizeof(int2) * rows.size()));
+            CSWGS_CUDA_TRY(cudaSetDevice(p->device));
+            CSWGS_CUDA_TRY(cudaMemcpy(buf->p, rows.data(), sizeof(int2) * rows.size(), cudaMemcpyHostToDevice));
+            slot = std::move(buf);
+        }
+        h->rows = slot->as<int2>();
+    }
+    return CSWGS_OK;
+}
+
+cswgs_status apply_slm(const cswgs_slm_frame *f, HoloSpec *h)
+{
+    h->has_slm = false;
+    if (!f) return CSWGS_OK;
+    if (!f->frame || !f->lut) return set_error(CSWGS_EINVAL, "SLM frame: NULL frame or lookup table");
+    if (f->levels < 2 || f->levels > 65536) return set_error(CSWGS_EINVAL, "SLM frame: %d levels", f->levels);
+    if (f->width < 1 || f->height < 1 || f->pitch < f->width)
+        return set_error(CSWGS_EINVAL, "SLM frame: %d x %d pixels, pitch %d", f->width, f->height, f->pitch);
+    if (f->offset_x < 0 || f->offset_y < 0 || (int64_t)f->offset_x + h->P > f->width ||
+        (int64_t)f->offset_y + h->P > f->height)
+        return set_error(CSWGS_EINVAL, "SLM frame: the %d x %d grid at (%d, %d) leaves the %d x %d frame", h->P,
+                         h->P, f->offset_x, f->offset_y, f->width, f->height);
+    h->has_slm = true;
+    h->slm = *f;
+    return CSWGS_OK;
+}
+
+void fill_pupil(HoloDev &H, const HoloSpec &s)
+{
+    H.D = s.D;
+    H.fa = s.fa;
+    H.fb = s.fb;
+    H.aperture = s.aperture;
+    H.windows = s.windows;
+    H.kA = s.waist > 0.0 ? (float)(1.4426950408889634 / (s.waist * s.waist)) : 0.f;
+    H.norm = s.norm;
+    H.rows = s.rows;
+    if (s.has_slm) {
+        H.slm = s.slm.frame + (size_t)s.slm.offset_y * s.slm.pitch + s.slm.offset_x;
+        H.lut = s.slm.lut;
+        H.slm_pitch = s.slm.pitch;
+        H.levels = s.slm.levels;
+        H.lscale = (float)((double)s.slm.levels / kTwoPi);
+    } else {
+        H.slm = nullptr;
+        H.lut = nullptr;
+        H.slm_pitch = 0;
+        H.levels = 0;
+        H.lscale = 0.f;
+    }
 }
 
 int schedule_launches(const HoloSpec &h) { return h.iterations + (h.final_pass ? 1 : 0); }
@@ -75,7 +194,7 @@ int pass_of(const HoloSpec &h, int L)
 
 static int pass_count(const HoloSpec &h, int pass)
 {
-    return pass == kPassSubset ? h.Mp : h.P * h.P;
+    return pass == kPassSubset ? h.Mp : h.D;
 }
 
 int pass_tiles(int pass, int P, int Mp, TileShape shape)
@@ -157,6 +276,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         H.N = s.N;
         H.Mp = s.Mp;
         H.seed = s.seed;
+        fill_pupil(H, s);
         size_t o = b->in_off[h];
         H.xyz = reinterpret_cast<const double *>(base + o);
         std::memcpy(stg + o, s.xyz.data(), sizeof(double) * 3 * s.N);

@@ -71,10 +71,26 @@ struct HoloSpec {
     uint64_t seed = 0;
     bool has_amp = false, has_init_w = false, has_init_th = false;
     std::vector<double> xyz, amp, init_w, init_th;
+    // pupil (defaults: the square uniform grid) and SLM output (none)
+    int aperture = 0, windows = 0;
+    double waist = 0.0;
+    int D = 0;                       // pupil pixel count
+    uint32_t fa = 0, fb = 0;         // subset permutation rectangle
+    double norm = 0.0;               // sum of A over the pupil
+    const int2 *rows = nullptr;      // device row table of the round aperture (owned by the plan)
+    bool has_slm = false;
+    cswgs_slm_frame slm{};
 };
 
 cswgs_status validate_request(const cswgs_plan_desc &d, const double *xyz, const double *amp, int N,
                               int P, double c, int iterations, int n_full, HoloSpec *out);
+// Applies a pupil (validated) to a validated spec: pupil size, subset size
+// floor(c D), permutation rectangle, sum of A, row table.
+cswgs_status apply_pupil(cswgs_plan_s *p, const cswgs_pupil &pu, double c, HoloSpec *h);
+// Applies an SLM frame (validated; NULL: none).
+cswgs_status apply_slm(const cswgs_slm_frame *f, HoloSpec *h);
+// The pupil and SLM fields of a device hologram record from its spec.
+void fill_pupil(HoloDev &H, const HoloSpec &s);
 
 // Number of launches of the FP32 schedule: one per iteration plus the final pass.
 int schedule_launches(const HoloSpec &h);
@@ -134,6 +150,10 @@ struct cswgs_plan_s {
     cswgs::DevBuf f64_mem;
     // small device scratch for results
     cswgs::DevBuf scratch;
+    // row tables of round apertures, per grid side (uploaded once, like the
+    // paper's fixed per-pixel arrays)
+    std::mutex pupil_mu;
+    std::map<int, std::unique_ptr<cswgs::DevBuf>> pupil_rows;
     std::unique_ptr<cswgs::Server> server;
 };
 

@@ -159,6 +159,7 @@ void Server::place(Req &r)
     H.N = s.N;
     H.Mp = s.Mp;
     H.seed = s.seed;
+    fill_pupil(H, s);
     // inputs go through this slot's pinned staging area (free again once the
     // slot is, i.e. after the request's last launch has completed)
     double *stg = in_h_ + (size_t)r.slot * 4 * p_->desc.max_N;
@@ -195,6 +196,8 @@ cswgs_status Server::submit(const cswgs_request &q, uint64_t *ticket)
     auto r = std::make_unique<Req>();
     CSWGS_TRY(validate_request(p_->desc, q.spots_xyz, q.amplitudes, q.N, q.P, q.subset_fraction, q.iterations,
                                q.full_iterations, &r->spec));
+    CSWGS_TRY(apply_pupil(p_, q.pupil, q.subset_fraction, &r->spec));
+    CSWGS_TRY(apply_slm(q.slm, &r->spec));
     r->spec.seed = q.seed;
     if (q.phase_out) {
         if (q.out_on_host) r->phase_host = q.phase_out;
@@ -371,7 +374,7 @@ void Server::loop()
                 sl.holo = r->slot;
                 sl.pass = pass;
                 sl.j = r->spec.first_j + r->L;
-                sl.count = pass == kPassSubset ? r->spec.Mp : r->spec.P * r->spec.P;
+                sl.count = pass == kPassSubset ? r->spec.Mp : r->spec.D;
                 sl.tiles = pass_tiles(pass, r->spec.P, r->spec.Mp, shape_);
                 sl.tile_begin = group_tiles[kind];
                 group_tiles[kind] += sl.tiles;

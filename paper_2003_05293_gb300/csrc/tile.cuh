@@ -74,13 +74,14 @@ __device__ void tail_update(const HoloDev &H, const LaunchSlot &sl, float2 *s_v,
     }
 }
 
-// Metrics of the final pass: V_n = (1/M) sum over all pixels (FP64 partials),
-// I_n = |V_n|^2, e = sum_n I_n, u by Eq. 7.
+// Metrics of the final pass: V_n = sum over the pupil of A e^{i(Phi - phi_n)}
+// (FP64 partials) divided by the pupil's sum of A, I_n = |V_n|^2,
+// e = sum_n I_n, u by Eq. 7.
 template <int THREADS>
 __device__ void tail_metrics(const HoloDev &H, const LaunchSlot &sl, double *s_red)
 {
     const int N = H.N;
-    const double inv = 1.0 / (double)sl.count;
+    const double inv = 1.0 / H.norm;   // sum of A over the pupil (P^2 for the square uniform grid)
     double e = 0.0, imax = -1.0, imin = 1e300;
     for (int n = threadIdx.x; n < N; n += THREADS) {
         double vr = 0.0, vi = 0.0;
@@ -237,6 +238,59 @@ __device__ __forceinline__ void finish_tile(const HoloDev &H, const LaunchSlot &
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- pupil --
+// The subset draw of iteration j (Section 3, "Compressed sensing"): the
+// permutation's keys, and for the windows reading (one order made at the
+// start, keyed by j = 0) the window's offset ((j - 1) Mp) mod D.
+struct SubsetDraw {
+    SubsetKeys K;
+    uint32_t off;
+};
+
+__device__ __forceinline__ SubsetDraw subset_draw(const HoloDev &H, int j)
+{
+    SubsetDraw d;
+    d.K = subset_keys(H.seed, H.windows ? 0 : j);
+    d.off = 0u;
+    if (H.windows) {
+        const int64_t D = H.D;
+        int64_t t = (((int64_t)(j - 1) % D) * ((int64_t)H.Mp % D)) % D;
+        d.off = (uint32_t)(t < 0 ? t + D : t);
+    }
+    return d;
+}
+
+// Grid pixel m = r P + i of pupil pixel q (the pupil's pixels in row-major
+// order).  Round aperture: the row is found by binary search in the row
+// table (first pupil index of each row, monotone), then the column offset.
+__device__ __forceinline__ uint32_t pupil_pixel(const HoloDev &H, uint32_t q)
+{
+    if (H.aperture == 0) return q;
+    int lo = 0, hi = H.P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint32_t)__ldg(&H.rows[mid].x) <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    const int2 rw = __ldg(&H.rows[lo]);
+    return (uint32_t)lo * (uint32_t)H.P + (uint32_t)rw.y + (q - (uint32_t)rw.x);
+}
+
+// Pixel k (< Mp) of the subset S_j.
+__device__ __forceinline__ uint32_t subset_pixel(const HoloDev &H, const SubsetDraw &d, uint32_t k)
+{
+    uint32_t kk = k + d.off;
+    kk = kk >= (uint32_t)H.D ? kk - (uint32_t)H.D : kk;
+    return pupil_pixel(H, permute_domain(kk, (uint32_t)H.D, H.fa, H.fb, d.K));
+}
+
+// Pupil amplitude A = exp(-rho^2 / waist^2) = exp2(-kA rho^2) (Eq. 3's A;
+// Section 4's Gaussian beam), 1 for a uniform pupil.
+__device__ __forceinline__ float pupil_amp(const HoloDev &H, float rho2)
+{
+    return H.kA != 0.f ? exp2f(-H.kA * rho2) : 1.f;
+}
+
 // A tile of a compressed iteration: THREADS * PPT pixels of the subset S_j,
 // each phasor evaluated directly (fixed-point phase, hardware sine/cosine).
 template <int THREADS, int PPT>
@@ -246,34 +300,30 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     const TileSmem m = tile_smem<THREADS>(smem, maxN);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int P = H.P, N = H.N;
-    const int pass = sl.pass;
+    const int pass = sl.pass;   // kPassSubset
     const int count = sl.count;
 
     load_spot_tables<THREADS>(H, m);
 
-    // this thread's pixels
-    SubsetKeys K = {0u, 0u, 0u, 0u};
-    if (pass == kPassSubset) K = subset_keys(H.seed, sl.j);
+    // this thread's pixels of S_j, with their pupil amplitudes (0 past the end)
+    const SubsetDraw dr = subset_draw(H, sl.j);
     const int half = P >> 1;
     int32_t xp[PPT], yp[PPT];
     uint32_t r2[PPT];
     float qf[PPT], msk[PPT];
-    int mix[PPT];
     const int base = t * (THREADS * PPT);
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
         int idx = base + s * THREADS + tid;
         bool valid = idx < count;
-        uint32_t k = valid ? (uint32_t)idx : 0u;
-        uint32_t mm = pass == kPassSubset ? permute(k, (uint32_t)P, K) : k;
+        uint32_t mm = subset_pixel(H, dr, valid ? (uint32_t)idx : 0u);
         int r = (int)(mm / (uint32_t)P);
         int i = (int)mm - r * P;
         xp[s] = i - half;
         yp[s] = r - half;
         r2[s] = (uint32_t)(xp[s] * xp[s] + yp[s] * yp[s]);
         qf[s] = (float)r2[s];
-        msk[s] = valid ? 1.f : 0.f;
-        mix[s] = valid ? (int)mm : -1;
+        msk[s] = valid ? pupil_amp(H, qf[s]) : 0.f;
     }
     __syncthreads();
 
@@ -299,15 +349,7 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     // Phi_m = arg S_m; the forward pass needs -Phi_m as a fixed-point addend
     uint32_t padd[PPT];
 #pragma unroll
-    for (int s = 0; s < PPT; ++s) {
-        float ph = atan2f(si[s], sr[s]);
-        padd[s] = kFixRound - rad_to_fix(ph);
-        if (pass == kPassFinal && mix[s] >= 0 && H.phase_out) {
-            float o = ph < 0.f ? ph + kTwoPiF : ph;
-            if (o >= kTwoPiF) o = 0.f;
-            H.phase_out[mix[s]] = o;
-        }
-    }
+    for (int s = 0; s < PPT; ++s) padd[s] = kFixRound - rad_to_fix(atan2f(si[s], sr[s]));
 
     // forward projection, Eq. 3: each thread's phasor is e^{i (phi_n - Phi_m)},
     // the conjugate of the term; per spot the thread sums its PPT pixels, the
@@ -362,23 +404,26 @@ __device__ void process_tile_h2(const HoloDev &H, const LaunchSlot &sl, int t, i
 
     load_spot_tables<THREADS>(H, m);
 
-    const SubsetKeys K = subset_keys(H.seed, sl.j);
+    const SubsetDraw dr = subset_draw(H, sl.j);
     const int half = P >> 1;
     int32_t xp[PPT], yp[PPT];
     uint32_t r2[PPT];
     __half2 msk[NP];
+    float amp_prev = 0.f;
     const int base = t * (THREADS * PPT);
 #pragma unroll
     for (int s = 0; s < PPT; ++s) {
         int idx = base + s * THREADS + tid;
         bool valid = idx < count;
-        uint32_t mm = permute(valid ? (uint32_t)idx : 0u, (uint32_t)P, K);
+        uint32_t mm = subset_pixel(H, dr, valid ? (uint32_t)idx : 0u);
         int r = (int)(mm / (uint32_t)P);
         int i = (int)mm - r * P;
         xp[s] = i - half;
         yp[s] = r - half;
         r2[s] = (uint32_t)(xp[s] * xp[s] + yp[s] * yp[s]);
-        if (s & 1) msk[s / 2] = __floats2half2_rn(idx - THREADS < count ? 1.f : 0.f, valid ? 1.f : 0.f);
+        const float a = valid ? pupil_amp(H, (float)r2[s]) : 0.f;
+        if (s & 1) msk[s / 2] = __floats2half2_rn(amp_prev, a);
+        amp_prev = a;
     }
     __syncthreads();
 
@@ -468,6 +513,29 @@ __device__ __forceinline__ float2 spot_factor(int32_t tilt, int32_t Gh, float gl
     return make_float2(w * c, w * s);
 }
 
+// Gray levels of four phases in [0, 2 pi) of grid row `row`, columns col ..
+// col + 3 (those inside the grid), into the SLM frame: level
+// rint(Phi * lscale) mod levels in FP32, gray = lut[level].  Four aligned
+// in-grid bytes go as one 32-bit store.
+__device__ __forceinline__ void write_gray4(const HoloDev &H, int row, int col, const float o[4])
+{
+    uint32_t g[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int l = __float2int_rn(o[j] * H.lscale);
+        l = l >= H.levels ? l - H.levels : l;
+        g[j] = __ldg(H.lut + l);
+    }
+    uint8_t *dst = H.slm + (size_t)row * H.slm_pitch + col;
+    if (col + 3 < H.P && (reinterpret_cast<uintptr_t>(dst) & 3) == 0) {
+        *reinterpret_cast<uint32_t *>(dst) = g[0] | (g[1] << 8) | (g[2] << 16) | (g[3] << 24);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (col + j < H.P) dst[j] = (uint8_t)g[j];
+    }
+}
+
 // A tile of a pass over all pixels (full iteration or final pass), using the
 // separability of the lens-and-prism phase (Eq. 2):
 //   e^{i phi_n(x', y')} = C_n(x') R_n(y'),  C_n = e^{i 2 pi (a x' + g x'^2)},
@@ -493,6 +561,32 @@ __device__ void process_full_tile(const HoloDev &H, const LaunchSlot &sl, int t,
     const int tx = tid & 15, ty = tid >> 4;   // pixels: rows y0 + 4 ty + i, columns x0 + 4 tx + j
     float2 *sR = m.fac;                 // NF x ROWS
     float2 *sC = m.fac + NF * ROWS;     // NF x COLS, interleaved (col_slot)
+
+    // a tile wholly outside the round pupil: zero partials, and in the final
+    // pass phase 0 (gray lut[0]) over its grid pixels
+    if (H.aperture != 0) {
+        const int ylo = y0 - half, yhi = min(y0 + ROWS, P) - 1 - half;
+        const int xlo = x0 - half, xhi = min(x0 + COLS, P) - 1 - half;
+        const int64_t dy = ylo > 0 ? ylo : (yhi < 0 ? yhi : 0);   // nearest y' to 0 in the tile
+        const int64_t dx = xlo > 0 ? xlo : (xhi < 0 ? xhi : 0);
+        if (dx * dx + dy * dy > (int64_t)half * half) {
+            for (int n = tid; n < N; n += THREADS) {
+                if (pass == kPassFinal) H.part64[(size_t)t * N + n] = make_double2(0.0, 0.0);
+                else H.part[(size_t)t * N + n] = make_float2(0.f, 0.f);
+            }
+            if (pass == kPassFinal) {
+                const int rows = min(ROWS, P - y0), cols = min(COLS, P - x0);
+                const uint8_t g0 = H.slm ? __ldg(H.lut) : 0;
+                for (int f = tid; f < rows * cols; f += THREADS) {
+                    const int r = y0 + f / cols, c = x0 + f % cols;
+                    if (H.phase_out) H.phase_out[(size_t)r * P + c] = 0.f;
+                    if (H.slm) H.slm[(size_t)r * H.slm_pitch + c] = g0;
+                }
+            }
+            finish_tile<THREADS>(H, sl, m.v, s_red, s_last);
+            return;
+        }
+    }
 
     load_spot_tables<THREADS>(H, m);
     __syncthreads();
@@ -551,40 +645,48 @@ __device__ void process_full_tile(const HoloDev &H, const LaunchSlot &sl, int t,
         __syncthreads();
     }
 
-    // e^{i Phi} = S / |S| (arg 0 = 0), kept in S; zero outside the grid so it adds
-    // nothing below.  The final pass writes Phi.
+    // A e^{i Phi} = A S / |S| (arg 0 = 0), kept in S; zero outside the grid and
+    // the pupil so it adds nothing below.  The final pass writes Phi (0
+    // outside the pupil) and its gray level.
     const bool vec_out = pass == kPassFinal && H.phase_out && (P & 3) == 0 &&
                          (reinterpret_cast<uintptr_t>(H.phase_out) & 15) == 0;
+    const int64_t R2 = (int64_t)half * half;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int row = y0 + 4 * ty + i;
+        const int yq = row - half;
         float o[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int col = x0 + 4 * tx + j;
-            const bool valid = row < P && col < P;
+            const int xq = col - half;
+            const int64_t rho2 = (int64_t)xq * xq + (int64_t)yq * yq;
+            const bool valid = row < P && col < P && (H.aperture == 0 || rho2 <= R2);
             const float n2 = S[i][j].x * S[i][j].x + S[i][j].y * S[i][j].y;
             if (pass == kPassFinal) {
                 float ph = atan2f(S[i][j].y, S[i][j].x);
                 ph = ph < 0.f ? ph + kTwoPiF : ph;
-                o[j] = ph >= kTwoPiF ? 0.f : ph;
+                o[j] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
             }
             if (!valid) S[i][j] = make_float2(0.f, 0.f);
             else if (n2 > 0.f) {
-                const float rs = rsqrtf(n2);
+                const float rs = rsqrtf(n2) * pupil_amp(H, (float)rho2);
                 S[i][j] = make_float2(S[i][j].x * rs, S[i][j].y * rs);
-            } else S[i][j] = make_float2(1.f, 0.f);
+            } else S[i][j] = make_float2(pupil_amp(H, (float)rho2), 0.f);
         }
-        if (pass == kPassFinal && H.phase_out && row < P) {
+        if (pass == kPassFinal && row < P) {
             const int col = x0 + 4 * tx;
-            float *dst = H.phase_out + (size_t)row * P + col;
-            if (vec_out && col + 3 < P) {
-                *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-            } else {
+            if (H.phase_out) {
+                float *dst = H.phase_out + (size_t)row * P + col;
+                if (vec_out && col + 3 < P) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (col + j < P) dst[j] = o[j];
+                    for (int j = 0; j < 4; ++j)
+                        if (col + j < P) dst[j] = o[j];
+                }
             }
+            if (H.slm) write_gray4(H, row, col, o);
         }
     }
 

@@ -72,6 +72,9 @@ static std::vector<HoloSpec> synthetic(const TuneKey &k, double c)
         s.P = std::min(k.P, 4096);
         s.N = k.N;
         s.Mp = std::max(1, (int)std::floor(c * (double)s.P * s.P));
+        s.D = s.P * s.P;   // the square uniform pupil
+        s.fa = s.fb = (uint32_t)s.P;
+        s.norm = (double)s.D;
         s.iterations = 2;
         s.n_full = 1;
         s.first_j = 1;

@@ -52,7 +52,7 @@ def test_exports_are_c_symbols():
 
 
 def test_host_only_calls(lib):
-    assert lib.cswgs_abi_version() == 1
+    assert lib.cswgs_abi_version() == 2
     assert lib.cswgs_status_string(0) == b"ok"
     assert lib.cswgs_status_string(1) == b"invalid argument"
     from paper_2003_05293_gb300 import capi
@@ -62,6 +62,7 @@ def test_host_only_calls(lib):
     o = capi.cswgs_solve_opts()
     lib.cswgs_solve_opts_default(ctypes.byref(o))
     assert (o.full_iterations, o.first_iteration, o.final_pass) == (2, 1, 1)
+    assert (o.pupil.aperture, o.pupil.subset_mode, o.pupil.beam_waist) == (0, 0, 0.0) and not o.slm
     # NULL arguments are refused before any device work
     assert lib.cswgs_plan_create(None, None) == capi.CSWGS_EINVAL
     assert lib.cswgs_solve(None, None, None, 1, 8, 0.5, 1, 0, None, 0, None, None) == capi.CSWGS_EINVAL
@@ -72,15 +73,19 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_2003_05293_gb300 import capi
     src = tmp_path / "sz.c"
     src.write_text('#include "cswgs.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\","
+                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
                    "sizeof(cswgs_plan_desc), sizeof(cswgs_solve_opts), sizeof(cswgs_request),"
                    "sizeof(cswgs_result), sizeof(cswgs_serve_stats),"
-                   "offsetof(cswgs_request, phase_out), offsetof(cswgs_plan_desc, tune_cache));return 0;}\n")
+                   "offsetof(cswgs_request, phase_out), offsetof(cswgs_plan_desc, tune_cache),"
+                   "sizeof(cswgs_pupil), sizeof(cswgs_slm_frame), offsetof(cswgs_request, slm),"
+                   "offsetof(cswgs_slm_frame, levels));return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(capi.cswgs_plan_desc), ctypes.sizeof(capi.cswgs_solve_opts),
             ctypes.sizeof(capi.cswgs_request), ctypes.sizeof(capi.cswgs_result),
             ctypes.sizeof(capi.cswgs_serve_stats), capi.cswgs_request.phase_out.offset,
-            capi.cswgs_plan_desc.tune_cache.offset]
+            capi.cswgs_plan_desc.tune_cache.offset, ctypes.sizeof(capi.cswgs_pupil),
+            ctypes.sizeof(capi.cswgs_slm_frame), capi.cswgs_request.slm.offset,
+            capi.cswgs_slm_frame.levels.offset]
     assert got == want

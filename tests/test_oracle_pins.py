@@ -576,3 +576,19 @@ def test_bruteforce_high_precision_round_gaussian_windows():
     assert res["e"] == pytest.approx(float(sum(In)), abs=1e-13)
     assert res["u"] == pytest.approx(float(1 - (max(In) - min(In)) / (max(In) + min(In))), abs=1e-13)
     assert np.allclose(res["w"], [float(x) for x in w], rtol=1e-12)
+
+
+def test_slm_gray_levels():
+    # identity table of 256 levels: phase 2 pi k / 256 -> k, half a level rounds
+    # to even, the top of the range wraps to level 0
+    lut = np.arange(256, dtype=np.uint8)
+    k = np.arange(256)
+    ph = (2 * np.pi * k / 256).astype(np.float32)
+    assert np.array_equal(oracle.slm_gray(ph, lut, 256), k.astype(np.uint8))
+    assert oracle.slm_gray(np.float32(np.pi), lut, 256) == 128
+    assert oracle.slm_gray(np.float32(2 * np.pi * 255.7 / 256), lut, 256) == 0
+    assert oracle.slm_gray(np.float32(2 * np.pi * 0.3 / 256), lut, 256) == 0
+    # a non-trivial table: gray = lut[level]
+    lut2 = (255 - np.arange(16) * 17).astype(np.uint8)
+    ph = (2 * np.pi * np.arange(16) / 16).astype(np.float32)
+    assert np.array_equal(oracle.slm_gray(ph, lut2, 16), lut2)
