@@ -40,22 +40,30 @@ FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
 # DRAM bytes (read + write) per launch of the iteration kernels at the default
 # workload, from one ncu capture of this bench
 # (profiles/iter_kernels_b64_P1152_N100_launches.md): compressed launches, and
-# full-pixel launches (2 full iterations + the final pass, averaged).  Reported
-# only while the kernel sources hash to the value they had when measured.
-TRAFFIC_MEASURED = {"kernel_sha": "b50bed129f650127", "sub": 311040, "full": 104178858}
-KERNEL_SOURCES = ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu")
+# full-pixel launches (2 full iterations + the final pass, averaged).  Each is
+# reported only while the sources of its kernel hash to the value they had
+# when it was measured.
+TRAFFIC_MEASURED = {"sub": {"sha": None, "bytes": None}, "full": {"sha": None, "bytes": None}}
+KERNEL_SOURCES = {"sub": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu"),
+                  "full": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu")}
+
+
+def kernel_sha(kind):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2003_05293_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def measured_traffic(args):
-    import hashlib
-    h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2003_05293_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
     default = (args.batch, args.P, args.N, args.c, args.iters) == (64, 1152, 100, 0.125, 30)
-    if not default or h.hexdigest()[:16] != TRAFFIC_MEASURED["kernel_sha"]:
-        return None, None
-    return TRAFFIC_MEASURED["sub"], TRAFFIC_MEASURED["full"]
+    out = []
+    for kind in ("sub", "full"):
+        m = TRAFFIC_MEASURED[kind]
+        out.append(m["bytes"] if default and m["sha"] == kernel_sha(kind) else None)
+    return tuple(out)
 
 
 def parse():
@@ -82,6 +90,10 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-scenarios", action="store_true")
+    ap.add_argument("--compare", action="store_true",
+                    help="the paper's computational comparison instead of the throughput run: RS, WGS and CS-WGS "
+                         "(c = 2^-1 .. 2^-8) on its scenarios, quality against single-hologram latency and at "
+                         "fixed time budgets")
     ap.add_argument("--no-paper-setup", action="store_true",
                     help="skip the leg with the paper's optics (round aperture, Gaussian beam, windows, SLM frames)")
     return ap.parse_args()
@@ -268,6 +280,71 @@ def run_reference(args, rank, world):
 
 
 # -------------------------------------------------------------- our arm --
+def run_compare(args, local):
+    """Section 5's comparison, on synthetic stand-ins of its scenarios with its
+    optics: random superposition (I = 0), WGS (c = 1) and CS-WGS (c = 2^-1 ..
+    2^-8, the last two iterations full), each at several iteration counts.  Per
+    configuration: the device time of one hologram alone (CUDA events on the
+    plan's stream, median of 3) and e, u over 10 orientations and initial
+    phases.  Then, per time budget, the best e * u each method reaches within
+    it."""
+    import torch
+
+    from paper_2003_05293_gb300 import Plan
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    plan = Plan(device=local, precision="fp32", stream=stream.cuda_stream, tune_cache=args.tune_cache)
+    P = args.P
+    waist = 6000.0 / 9.2 * P / 1152
+    pupil = dict(aperture="round", waist=waist, subset_mode="windows")
+    out = torch.empty(P * P, dtype=torch.float32, device="cuda")
+    methods = [("RS", 1.0, [0])] + [("WGS", 1.0, [1, 2, 3, 5, 8, 12, 20, 30])]
+    methods += [("CS-WGS", 2.0 ** -k, [3, 5, 8, 12, 20, 30, 50]) for k in range(1, 9)]
+    budgets_ms = [0.25, 0.5, 1.0, 2.0, 4.0]
+    result = {}
+    for name in workloads.SCENARIOS:
+        rows = []
+        for meth, c, iters in methods:
+            for I in iters:
+                pbs = [workloads.scenario(name, P, seed=s, c=c, iterations=I) for s in range(10)]
+                for q in pbs:
+                    q.extra.update(pupil)
+                    q.extra["full_iterations"] = I if meth == "WGS" else min(2, I)
+                q = pbs[0]
+                kw = dict(full_iterations=q.extra["full_iterations"], **pupil)
+                plan.solve(q.xyz, P, c, I, q.seed, out=out, **kw)           # warm-up (graph, tuning)
+                ts = []
+                for _ in range(3):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    plan.solve(q.xyz, P, c, I, q.seed, out=out, **kw)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                res = plan.solve_batch(pbs)
+                es = np.array([r["e"] for r in res])
+                us = np.array([r["u"] for r in res])
+                rows.append({"method": meth, "c": c, "iterations": I, "ms": float(np.median(ts)),
+                             "e": float(es.mean()), "u": float(us.mean()), "u_min": float(us.min())})
+        best = {}
+        for b in budgets_ms:
+            best[str(b)] = {}
+            for meth in ("RS", "WGS", "CS-WGS"):
+                fit = [r for r in rows if r["method"] == meth and r["ms"] <= b]
+                if fit:
+                    r = max(fit, key=lambda r: r["e"] * r["u"])
+                    best[str(b)][meth] = {k: r[k] for k in ("c", "iterations", "ms", "e", "u")}
+        result[name] = {"N": int(workloads.scenario(name, P, 0).N), "runs": rows, "best_within_budget_ms": best}
+    plan.close()
+    print(json.dumps({"metric": "hologram quality at a fixed single-hologram time budget", "P": P,
+                      "pupil": "round aperture of P px, Gaussian beam waist %.1f px, windows" % waist,
+                      "timing": "device time of one hologram alone (CUDA events), median of 3",
+                      "quality": "mean e, u over 10 orientations and initial phases", "scenarios": result}),
+          flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -275,6 +352,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.compare:
+        if rank == 0:
+            run_compare(args, local)
+        return
 
     import torch
     import torch.distributed as dist

@@ -114,6 +114,31 @@ typedef struct {
     int levels;                 /* 2 .. 65536 */
 } cswgs_slm_frame;
 
+/* ------------------------------------------------- physical-unit input --- */
+
+/* The optics of Eq. 2: wavelength lambda, focal length f of the lens that
+ * images the SLM's Fourier plane, SLM pixel pitch.  All in metres. */
+typedef struct {
+    double wavelength;
+    double focal_length;
+    double pixel_pitch;
+} cswgs_optics;
+
+/* Spots given in the focal volume (metres: x, y lateral, z axial from the
+ * focal plane) -> the normalised units of every solve (alpha, beta cycles
+ * across the P-pixel aperture, gamma waves of defocus at its edge):
+ *     alpha = x P pitch / (lambda f),  beta = y P pitch / (lambda f)
+ * (Eq. 2's tilt: one cycle across the aperture is the first diffraction
+ * order, at lambda f / (P pitch) in the focal plane), and
+ *     gamma = z (P pitch / 2)^2 / (2 lambda f^2)
+ * the paraxial defocus pi z rho^2 / (lambda f^2) at rho = P pitch / 2.  Eq. 2
+ * prints 2 pi / (lambda f^2) for the defocus prefactor, twice the paraxial
+ * one; the paraxial form is taken.  Host arrays, N x 3 in and out (may be
+ * the same array).  Host only: no device work.  CSWGS_EINVAL for
+ * non-positive or non-finite optics or coordinates, N < 1, P < 2. */
+cswgs_status cswgs_spots_from_physical(const cswgs_optics *optics, const double *xyz_m, int N, int P,
+                                       double *spots_out);
+
 /* ---------------------------------------------------------------- plan --- */
 
 typedef struct {

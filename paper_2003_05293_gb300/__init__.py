@@ -21,7 +21,8 @@ from .capi import (CSWGS_FP32, CSWGS_FP32_FP16SINCOS, CSWGS_FP64, CswgsError, ch
                    cswgs_plan_desc, cswgs_pupil, cswgs_request, cswgs_result, cswgs_serve_stats,
                    cswgs_slm_frame, cswgs_solve_opts)
 
-__all__ = ["Plan", "Batch", "CswgsError", "PRECISIONS", "APERTURES", "SUBSET_MODES", "SlmFrame", "capi"]
+__all__ = ["Plan", "Batch", "CswgsError", "PRECISIONS", "APERTURES", "SUBSET_MODES", "SlmFrame", "capi",
+           "spots_from_physical"]
 
 PRECISIONS = {"fp64": CSWGS_FP64, "fp32": CSWGS_FP32, "fp32_fp16sincos": CSWGS_FP32_FP16SINCOS}
 APERTURES = {"square": capi.CSWGS_APERTURE_SQUARE, "round": capi.CSWGS_APERTURE_ROUND}
@@ -85,6 +86,17 @@ def _out_ptr(out):
     if not out.is_cuda or out.dtype.__str__() != "torch.float32" or not out.is_contiguous():
         raise ValueError("device output must be a contiguous float32 CUDA tensor")
     return ctypes.cast(ctypes.c_void_p(out.data_ptr()), capi.c_float_p), 0
+
+
+def spots_from_physical(xyz_m, P: int, wavelength: float, focal_length: float, pixel_pitch: float):
+    """cswgs_spots_from_physical: spots in metres (x, y in the focal plane, z
+    from it) -> the normalised (alpha, beta, gamma) every solve takes."""
+    xyz = _f64(xyz_m, (-1, 3))
+    out = np.empty_like(xyz)
+    o = capi.cswgs_optics(float(wavelength), float(focal_length), float(pixel_pitch))
+    check(capi.load().cswgs_spots_from_physical(ctypes.byref(o), _dptr(xyz), xyz.shape[0], int(P), _dptr(out)),
+          "cswgs_spots_from_physical")
+    return out
 
 
 class Plan:

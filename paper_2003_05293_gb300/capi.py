@@ -41,6 +41,11 @@ class cswgs_slm_frame(ctypes.Structure):
                 ("lut", c_uint8_p), ("levels", ctypes.c_int)]
 
 
+class cswgs_optics(ctypes.Structure):
+    _fields_ = [("wavelength", ctypes.c_double), ("focal_length", ctypes.c_double),
+                ("pixel_pitch", ctypes.c_double)]
+
+
 class cswgs_solve_opts(ctypes.Structure):
     _fields_ = [("full_iterations", ctypes.c_int), ("first_iteration", ctypes.c_int),
                 ("final_pass", ctypes.c_int), ("init_w", c_double_p), ("init_theta", c_double_p),
@@ -110,6 +115,8 @@ SIGNATURES = {
     "cswgs_sincos_peak": (ctypes.c_int, [_P, c_double_p, c_double_p]),
     "cswgs_solve_noalloc": (ctypes.c_int, [c_double_p, c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_uint64, c_float_p, c_double_p, ctypes.c_void_p]),
+    "cswgs_spots_from_physical": (ctypes.c_int, [ctypes.POINTER(cswgs_optics), c_double_p, ctypes.c_int, ctypes.c_int,
+                                                 c_double_p]),
     "cswgs_abi_version": (ctypes.c_int, []),
     "cswgs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cswgs_last_error": (ctypes.c_char_p, []),

@@ -201,6 +201,30 @@ void cswgs_solve_opts_default(cswgs_solve_opts *o)
     o->final_pass = 1;
 }
 
+cswgs_status cswgs_spots_from_physical(const cswgs_optics *optics, const double *xyz_m, int N, int P,
+                                       double *spots_out)
+{
+    if (!optics || !xyz_m || !spots_out) return set_error(CSWGS_EINVAL, "NULL optics, spots or output");
+    if (N < 1 || P < 2) return set_error(CSWGS_EINVAL, "N=%d, P=%d", N, P);
+    const double lam = optics->wavelength, f = optics->focal_length, pitch = optics->pixel_pitch;
+    if (!(std::isfinite(lam) && lam > 0.0 && std::isfinite(f) && f > 0.0 && std::isfinite(pitch) && pitch > 0.0))
+        return set_error(CSWGS_EINVAL, "optics: wavelength %g, focal length %g, pitch %g must be finite and > 0",
+                         lam, f, pitch);
+    const double aperture = (double)P * pitch;            // metres across the P-pixel aperture
+    const double tilt = aperture / (lam * f);              // cycles per metre in the focal plane
+    const double edge = 0.5 * aperture;
+    const double defocus = edge * edge / (2.0 * lam * f * f);   // waves at the edge per metre of z
+    for (int n = 0; n < N; ++n) {
+        const double x = xyz_m[3 * n], y = xyz_m[3 * n + 1], z = xyz_m[3 * n + 2];
+        if (!(std::isfinite(x) && std::isfinite(y) && std::isfinite(z)))
+            return set_error(CSWGS_EINVAL, "spot %d: non-finite coordinate", n);
+        spots_out[3 * n] = x * tilt;
+        spots_out[3 * n + 1] = y * tilt;
+        spots_out[3 * n + 2] = z * defocus;
+    }
+    return CSWGS_OK;
+}
+
 cswgs_status cswgs_plan_create(cswgs_plan *out, const cswgs_plan_desc *d)
 {
     if (!out || !d) return set_error(CSWGS_EINVAL, "NULL plan or descriptor");
