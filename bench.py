@@ -43,7 +43,8 @@ FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
 # full-pixel launches (2 full iterations + the final pass, averaged).  Each is
 # reported only while the sources of its kernel hash to the value they had
 # when it was measured.
-TRAFFIC_MEASURED = {"sub": {"sha": None, "bytes": None}, "full": {"sha": None, "bytes": None}}
+TRAFFIC_MEASURED = {"sub": {"sha": "3bdfbecac4b139e7", "bytes": 335689},
+                    "full": {"sha": "3bdfbecac4b139e7", "bytes": 103352235}}
 KERNEL_SOURCES = {"sub": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu"),
                   "full": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu")}
 
