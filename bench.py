@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
 TRAFFIC_MEASURED = {"sub": {"sha": "3bdfbecac4b139e7", "bytes": 335689},
                     "full": {"sha": "3bdfbecac4b139e7", "bytes": 103352235}}
 KERNEL_SOURCES = {"sub": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu"),
-                  "full": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu")}
+                  "full": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu", "kernels_tc.cu")}
 
 
 def kernel_sha(kind):
@@ -65,6 +65,39 @@ def measured_traffic(args):
         m = TRAFFIC_MEASURED[kind]
         out.append(m["bytes"] if default and m["sha"] == kernel_sha(kind) else None)
     return tuple(out)
+
+
+def full_roofline(tile, achieved_tflops, fma_peak, sm_count, max_mhz, traffic, n_launches, full_ms):
+    """Roofline of the full-iteration and final launches: the tensor-core kernel
+    against the measured dense BF16 peak (its operands are BF16 halves), the
+    CUDA-core kernel against the FP32 FMA peak.  Achieved = algorithmic flops:
+    8 per pixel-spot pair and pass (one complex multiply-add)."""
+    base = {"achieved": achieved_tflops, "unit": "TFLOP/s", "traffic": traffic,
+            "flops_basis": "8 flops (complex multiply-add) per pixel-spot pair and pass",
+            "ms_per_launch": full_ms / max(1, n_launches)}
+    if tile["full_threads"] == 1:
+        peak, basis = 1700.0, "fallback (sustained)"
+        try:
+            mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            peak, basis = float(mp["bf16_tflops_sustained"]), "measured (cuBLAS BF16, sustained: timed inside the step)"
+        except (OSError, ValueError, KeyError):
+            pass
+        base.update({"bound": "tensor", "pipe": "tcgen05 kind::f16 (BF16 in, FP32 accumulate)", "peak": peak,
+                     "frac": achieved_tflops / peak, "peak_basis": "%s dense BF16 peak" % basis,
+                     "kernel": "iter_full_tc_kernel, full-iteration and final launches (%d per step)" % n_launches,
+                     "issued_tensor_flops_per_algorithmic": 3,
+                     "note": "each real product is 3 BF16 products (hi hi + hi lo + lo hi) for FP32-class "
+                             "accuracy, so the tensor pipe runs 3x the algorithmic flops",
+                     "tile": {"threads": 256, "blocks": tile["full_blocks"], "pixels": "128 rows x 64 columns"}})
+    else:
+        base.update({"bound": "alu", "pipe": "FP32 FMA", "peak": fma_peak, "frac": achieved_tflops / fma_peak,
+                     "peak_basis": "%d SMs x %d lanes x 2 flops x %.0f MHz (of derived)"
+                                   % (sm_count, FP32_LANES_PER_SM, max_mhz),
+                     "kernel": "iter_full_kernel, separable full-iteration and final launches (%d per step)"
+                               % n_launches,
+                     "tile": {"threads": tile["full_threads"], "blocks": tile["full_blocks"],
+                              "pixels": "threads/4 rows x 64 columns, 4 x 4 per thread"}})
+    return base
 
 
 def parse():
@@ -466,16 +499,8 @@ def main():
                                        % (sm_count, SFU_PER_CLK_PER_SM, max_mhz, probe / 1e9),
                          "ms_per_launch": sub_ms / max(1, n_sub),
                          "tile": {k: tile[k] for k in ("threads", "pixels_per_thread", "blocks")}},
-            "roofline_full_passes": {"bound": "alu", "pipe": "FP32 FMA", "achieved": fma_achieved, "peak": fma_peak,
-                                     "unit": "TFLOP/s", "frac": fma_achieved / fma_peak, "traffic": TRAFFIC_FULL,
-                                     "kernel": "iter_kernel, separable full-iteration and final launches (%d per step)"
-                                               % n_full_launches,
-                                     "flops_basis": "8 flops (complex multiply-add) per pixel-spot pair and pass",
-                                     "peak_basis": "%d SMs x %d lanes x 2 flops x %.0f MHz (of derived)"
-                                                   % (sm_count, FP32_LANES_PER_SM, max_mhz),
-                                     "ms_per_launch": full_ms / max(1, n_full_launches),
-                                     "tile": {"threads": tile["full_threads"], "blocks": tile["full_blocks"],
-                                              "pixels": "threads/4 rows x 64 columns, 4 x 4 per thread"}},
+            "roofline_full_passes": full_roofline(tile, fma_achieved, fma_peak, sm_count, max_mhz, TRAFFIC_FULL,
+                                                  n_full_launches, full_ms),
             "gpu_launches": args.steps * len(kts[0]),
             "kernel_times_from": "CUDA events recorded inside the graph around each launch, last timed step",
             "clocks": clk}

@@ -51,7 +51,7 @@ typedef enum {
     CSWGS_EINVAL = 1,      /* bad argument */
     CSWGS_ENOMEM = 2,      /* device or host allocation failed, or admission refused */
     CSWGS_ECUDA = 3,       /* a CUDA call failed (message in cswgs_last_error) */
-    CSWGS_ETIMEOUT = 4,    /* a bounded wait ran out */
+    CSWGS_ETIMEOUT = 4,    /* a bounded wait ran out (serving, or a wait inside a kernel) */
     CSWGS_EBUSY = 5,       /* serving: the request is not finished yet */
     CSWGS_ECANCELLED = 6,  /* serving: the request was cancelled */
     CSWGS_ENOTFOUND = 7    /* serving: unknown or already collected ticket */
@@ -282,7 +282,9 @@ cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs
 
 /* Launch shapes of the batch's two iteration kernels, as chosen by the
  * autotuner: for compressed iterations threads per block and pixels per
- * thread, for full iterations and the final pass threads per block, and the
+ * thread; for full iterations and the final pass threads per block of the
+ * CUDA-core kernel, or 1 for the tensor-core kernel (256 threads, tiles of
+ * 128 x 64 pixels, split-BF16 products accumulated in FP32); and the
  * persistent blocks of each per launch.  Any pointer may be NULL. */
 cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *full_threads,
                                     int *blocks, int *full_blocks);

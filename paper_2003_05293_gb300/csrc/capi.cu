@@ -134,7 +134,7 @@ static cswgs_status solve_fp32(cswgs_plan_s *p, HoloSpec h, float *phase_out, in
     }
     if (final_w || final_theta)
         CSWGS_CUDA_TRY(cudaMemcpyAsync(st.data(), H.state, sizeof(SpotState) * N, cudaMemcpyDeviceToHost, s));
-    CSWGS_CUDA_TRY(cudaStreamSynchronize(s));
+    CSWGS_TRY(batch_status(b, s));
     for (int n = 0; n < N; ++n) {
         if (final_w) final_w[n] = (double)st[n].w;
         if (final_theta) final_theta[n] = (double)(int32_t)st[n].theta * (2.0 * M_PI / 4294967296.0);
@@ -449,7 +449,7 @@ cswgs_status cswgs_batch_results(cswgs_batch b, cswgs_result *results)
     for (int i = 0; i < b->count; ++i)
         CSWGS_CUDA_TRY(cudaMemcpyAsync(&eu[2 * i], fb->holos[i].metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                        p->stream));
-    CSWGS_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    CSWGS_TRY(batch_status(fb, p->stream));
     float ms = 0.f;
     if (fb->timing) cudaEventElapsedTime(&ms, fb->events.front(), fb->events.back());
     for (int i = 0; i < b->count; ++i) {
@@ -587,7 +587,7 @@ cswgs_status cswgs_solve_batch(cswgs_plan p, const cswgs_request *reqs, int coun
             CSWGS_CUDA_TRY(cudaMemcpyAsync(reqs[i].phase_out, b->own_phase[i],
                                            sizeof(float) * (size_t)specs[i].P * specs[i].P, cudaMemcpyDeviceToHost, s));
     }
-    CSWGS_CUDA_TRY(cudaStreamSynchronize(s));
+    CSWGS_TRY(batch_status(b, s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->events.front(), b->events.back());
     for (int i = 0; i < count; ++i) {

@@ -76,9 +76,13 @@ struct LaunchSlot {
 struct TileShape {
     int threads;        // compressed iterations: threads per block
     int ppt;            // compressed iterations: pixels per thread
-    int full_threads;   // full iterations and final pass: threads per block
+    int full_threads;   // full iterations and final pass: threads per block, or kFullTc
     int fp16 = 0;       // compressed iterations use the half-precision sincos
 };
+
+// full_threads value that selects the tensor-core kernel for full iterations
+// and the final pass (kernels_tc.cu: 256 threads, 128 x 64-pixel tiles)
+constexpr int kFullTc = 1;
 
 // The two iteration kernels: compressed-iteration tiles, separable full-pass tiles.
 enum LaunchKind : int { kLaunchSubset = 0, kLaunchFull = 1 };
@@ -93,6 +97,20 @@ bool tile_shape_supported(TileShape shape);
 size_t iter_fp32_smem(TileShape shape, int kind, int maxN);
 cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_t *out,
                                  cudaStream_t s);
+// Tensor-core full-pass kernel (kernels_tc.cu).
+int full_tc_tiles(int P);
+size_t full_tc_smem(int maxN);
+int full_tc_max_grid(int maxN, int sm_count);
+cudaError_t launch_full_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
+                           unsigned *queue, int grid, cudaStream_t s);
+
+// Either full-pass kernel, by tile shape (runtime.cu).
+bool shape_supported(TileShape shape);
+int shape_max_grid(TileShape shape, int kind, int maxN, int sm_count);
+int shape_full_tiles(int P, TileShape shape);
+cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const LaunchSlot *slots, int nslots,
+                         int total_tiles, int maxN, unsigned *queue, int grid, cudaStream_t s);
+
 cudaError_t launch_subset_ex_kernel(const HoloDev &H, int j, int32_t *out, cudaStream_t s);
 cudaError_t launch_sincos_probe(float *sink, long long *cycles, int iters, int blocks,
                                 int threads, cudaStream_t s);

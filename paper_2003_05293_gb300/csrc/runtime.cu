@@ -197,10 +197,37 @@ static int pass_count(const HoloSpec &h, int pass)
     return pass == kPassSubset ? h.Mp : h.D;
 }
 
+bool shape_supported(TileShape shape)
+{
+    if (shape.full_threads != kFullTc) return tile_shape_supported(shape);
+    TileShape cuda_core = shape;
+    cuda_core.full_threads = 256;
+    return tile_shape_supported(cuda_core);
+}
+
+int shape_max_grid(TileShape shape, int kind, int maxN, int sm_count)
+{
+    if (kind == kLaunchFull && shape.full_threads == kFullTc) return full_tc_max_grid(maxN, sm_count);
+    return iter_fp32_max_grid(shape, kind, maxN, sm_count);
+}
+
+int shape_full_tiles(int P, TileShape shape)
+{
+    return shape.full_threads == kFullTc ? full_tc_tiles(P) : full_pass_tiles(P, shape.full_threads);
+}
+
+cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const LaunchSlot *slots, int nslots,
+                         int total_tiles, int maxN, unsigned *queue, int grid, cudaStream_t s)
+{
+    if (kind == kLaunchFull && shape.full_threads == kFullTc)
+        return launch_full_tc(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+    return launch_iter_fp32(shape, kind, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+}
+
 int pass_tiles(int pass, int P, int Mp, TileShape shape)
 {
     const int tp = shape.threads * shape.ppt;
-    return pass == kPassSubset ? (Mp + tp - 1) / tp : full_pass_tiles(P, shape.full_threads);
+    return pass == kPassSubset ? (Mp + tp - 1) / tp : shape_full_tiles(P, shape);
 }
 
 int max_pass_tiles(const HoloSpec &h, TileShape shape)
@@ -225,6 +252,13 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     auto b = std::make_unique<Fp32Batch>();
     b->plan = p;
     b->specs = std::move(specs);
+    // the tensor-core full pass holds every spot table in shared memory; past
+    // its limit the batch keeps the CUDA-core kernel
+    if (shape.full_threads == kFullTc) {
+        int mN = 1;
+        for (auto &s : b->specs) mN = std::max(mN, s.N);
+        if (full_tc_max_grid(mN, p->sm_count) <= 0) shape.full_threads = 256;
+    }
     b->shape = shape;
     b->timing = timing;
     const int count = (int)b->specs.size();
@@ -369,7 +403,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     CSWGS_CUDA_TRY(cudaMemset(b->queue_d.p, 0, 256));
     CSWGS_CUDA_TRY(cudaMemset(b->mem.p, 0, work));
     for (int kind = 0; kind < 2; ++kind) {
-        b->grid[kind] = iter_fp32_max_grid(shape, kind, b->maxN, p->sm_count);
+        b->grid[kind] = shape_max_grid(shape, kind, b->maxN, p->sm_count);
         if (b->grid[kind] <= 0)
             return set_error(CSWGS_ECUDA, "tile shape %dx%d / %d cannot be resident with N=%d", shape.threads,
                              shape.ppt, shape.full_threads, b->maxN);
@@ -424,6 +458,15 @@ void batch_restage(Fp32Batch *b, int h)
     }
 }
 
+cswgs_status batch_status(Fp32Batch *b, cudaStream_t s)
+{
+    unsigned st = 0;
+    CSWGS_CUDA_TRY(cudaMemcpyAsync(&st, b->queue_d.as<unsigned>() + 2, sizeof st, cudaMemcpyDeviceToHost, s));
+    CSWGS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) return set_error(CSWGS_ETIMEOUT, "a bounded wait inside the tensor-core kernel ran out (status %u)", st);
+    return CSWGS_OK;
+}
+
 cswgs_status batch_upload_inputs(Fp32Batch *b, cudaStream_t s)
 {
     if (b->in_bytes)
@@ -466,7 +509,7 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
             const int tiles = b->l_tiles[i];
             if (tiles == 0) continue;
             const int grid = std::min(b->grid[kind], tiles);
-            CSWGS_CUDA_TRY(launch_iter_fp32(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
+            CSWGS_CUDA_TRY(shape_launch(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
                                             b->l_maxN[i], queue, grid, s));
         }
     }

@@ -128,6 +128,8 @@ struct Fp32Batch {
 cswgs_status batch_build(cswgs_plan_s *p, std::vector<HoloSpec> specs, bool timing,
                          std::unique_ptr<Fp32Batch> *out);
 cswgs_status batch_upload_inputs(Fp32Batch *b, cudaStream_t s);
+// CSWGS_ETIMEOUT when a bounded wait inside a kernel of the batch ran out (synchronises s)
+cswgs_status batch_status(Fp32Batch *b, cudaStream_t s);
 cswgs_status batch_set_outputs(Fp32Batch *b, const std::vector<float *> &dev_phase, cudaStream_t s);
 cswgs_status batch_enqueue(Fp32Batch *b, cudaStream_t s);   // graph launch (captures on first use)
 cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing = false);

@@ -95,6 +95,7 @@ Server::~Server()
         if (start_ev_[i]) cudaEventDestroy(start_ev_[i]);
     }
     if (met_h_) cudaFreeHost(met_h_);
+    if (status_h_) cudaFreeHost(status_h_);
     if (in_h_) cudaFreeHost(in_h_);
     if (stream_) cudaStreamDestroy(stream_);
 }
@@ -117,6 +118,8 @@ cswgs_status Server::start()
     CSWGS_CUDA_TRY(cudaMemset(queue_d_.p, 0, 256));
     master_.assign(B, HoloDev{});
     CSWGS_CUDA_TRY(cudaMallocHost(&met_h_, sizeof(double) * 4 * B));
+    CSWGS_CUDA_TRY(cudaMallocHost(&status_h_, 2 * sizeof(unsigned)));
+    status_h_[0] = status_h_[1] = 0u;
     CSWGS_CUDA_TRY(cudaMallocHost(&in_h_, sizeof(double) * 4 * (size_t)p_->desc.max_N * B));
     for (int i = 0; i < 2; ++i) {
         CSWGS_CUDA_TRY(cudaMallocHost(&holos_h_[i], sizeof(HoloDev) * B));
@@ -211,6 +214,10 @@ cswgs_status Server::submit(const cswgs_request &q, uint64_t *ticket)
             std::lock_guard<std::mutex> pk(p_->mu);
             cudaSetDevice(p_->device);
             shape_ = tuned_shape(p_, v);
+            // the tensor-core full pass holds every spot table in shared memory:
+            // beyond its limit the serving loop keeps the CUDA-core kernel
+            if (shape_.full_threads == kFullTc && full_tc_max_grid(p_->desc.max_N, p_->sm_count) <= 0)
+                shape_.full_threads = 256;
         }
         shape_set_ = true;
         CSWGS_TRY(start());
@@ -319,7 +326,7 @@ void Server::loop()
                 if (!r || !r->finishing || r->last_launch > completed_serial_) continue;
                 const double *m = met_h_ + (size_t)(r->last_launch & 1) * 2 * B + 2 * s;
                 r->met.assign(m, m + 2);
-                cswgs_status st = CSWGS_OK;
+                cswgs_status st = status_h_[r->last_launch & 1] ? CSWGS_ETIMEOUT : CSWGS_OK;
                 if (r->phase_host) {
                     cudaError_t e = cudaMemcpy(r->phase_host, r->dev.phase_out,
                                                sizeof(float) * (size_t)r->spec.P * r->spec.P,
@@ -401,8 +408,8 @@ void Server::loop()
             auto key = std::make_pair(kind, group_maxN[kind]);
             auto g = grid_for.find(key);
             if (g == grid_for.end())
-                g = grid_for.emplace(key, iter_fp32_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
-            launch_iter_fp32(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
+                g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
+            shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
                              queue, std::min(g->second, group_tiles[kind]), stream_);
         }
         double *mh = met_h_ + (size_t)(serial & 1) * 2 * B;
@@ -410,6 +417,8 @@ void Server::loop()
             cudaMemcpyAsync(mh + 2 * r->slot, r->dev.metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
             r->finishing = true;
         }
+        // the launches' status word (a timed-out wait inside a kernel sets it)
+        cudaMemcpyAsync(status_h_ + (serial & 1), queue + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_);
         cudaEventRecord(launch_ev_[serial & 1], stream_);
         for (Req *r : order) {          // only the requests that took part advance
             r->L++;

@@ -75,6 +75,7 @@ private:
     HoloDev *holos_h_[2] = {nullptr, nullptr};      // pinned, double-buffered copies of master_
     LaunchSlot *slots_h_[2] = {nullptr, nullptr};   // pinned, double-buffered (slots, then prep list)
     double *met_h_ = nullptr;                       // pinned: e, u per slot, double-buffered
+    unsigned *status_h_ = nullptr;                  // pinned: the launches' status word, double-buffered
     double *in_h_ = nullptr;                        // pinned: per-slot input staging (N x 4 doubles)
     cudaEvent_t launch_ev_[2] = {nullptr, nullptr};
     cudaEvent_t start_ev_[2] = {nullptr, nullptr};

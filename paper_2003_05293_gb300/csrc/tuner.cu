@@ -62,7 +62,7 @@ std::string tune_key(const std::vector<HoloSpec> &specs, bool fp16)
 // each is tuned on its own launches.
 static const int kSubCandidates[][2] = {{128, 2}, {128, 4}, {128, 8}, {256, 2}, {256, 4},
                                         {256, 8}, {512, 1}, {512, 2}, {512, 4}};
-static const int kFullCandidates[] = {128, 256, 512};
+static const int kFullCandidates[] = {128, 256, 512, kFullTc};
 
 static std::vector<HoloSpec> synthetic(const TuneKey &k, double c)
 {
@@ -121,8 +121,8 @@ static cswgs_status tune_for(cswgs_plan_s *p, const TuneKey &k, double c, double
     double best_sub = 1e30, best_full = 1e30, t[3];
     for (const auto &cand : kSubCandidates) {
         TileShape sh{cand[0], cand[1], best.full_threads, fp16};
-        if (!tile_shape_supported(sh)) continue;
-        if (iter_fp32_max_grid(sh, kLaunchSubset, k.N, p->sm_count) <= 0) continue;
+        if (!shape_supported(sh)) continue;
+        if (shape_max_grid(sh, kLaunchSubset, k.N, p->sm_count) <= 0) continue;
         CSWGS_TRY(time_steps(p, specs, sh, t));
         if (t[0] < best_sub) {
             best_sub = t[0];
@@ -132,7 +132,7 @@ static cswgs_status tune_for(cswgs_plan_s *p, const TuneKey &k, double c, double
     }
     for (int ft : kFullCandidates) {
         TileShape sh{best.threads, best.ppt, ft, fp16};
-        if (iter_fp32_max_grid(sh, kLaunchFull, k.N, p->sm_count) <= 0) continue;
+        if (shape_max_grid(sh, kLaunchFull, k.N, p->sm_count) <= 0) continue;
         CSWGS_TRY(time_steps(p, specs, sh, t));
         const double tf = wfull * t[1] + t[2];
         if (tf < best_full) {
@@ -208,7 +208,7 @@ void tune_load(cswgs_plan_s *p)
         const int fp16 = key.size() > 2 && key.compare(key.size() - 2, 2, "_H") == 0 ? 1 : 0;
         int t = 0, k = 0, f = 0;
         if (sscanf(s.c_str() + pos, " : [ %d , %d , %d ]", &t, &k, &f) == 3 &&
-            tile_shape_supported(TileShape{t, k, f, fp16}))
+            shape_supported(TileShape{t, k, f, fp16}))
             p->tune[key] = TileShape{t, k, f, fp16};
     }
 }
