@@ -60,6 +60,10 @@ struct HoloDev {
     int levels;
     float lscale;           // (float)(levels / (2 pi))
     int pad2;
+    // factor tables of the tensor-core full passes (nullptr: not used)
+    unsigned char *rwtab;   // R' = w a e^{i theta} R blocks, remade before every full pass
+    unsigned char *ctab;    // C blocks (GEMM 1 operand), made once
+    unsigned char *cstab;   // C blocks for GEMM 2, made once
 };
 
 // One hologram's share of one persistent launch.
@@ -103,6 +107,10 @@ size_t full_tc_smem(int maxN);
 int full_tc_max_grid(int maxN, int sm_count);
 cudaError_t launch_full_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
                            unsigned *queue, int grid, cudaStream_t s);
+void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs);
+cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count, cudaStream_t s);
+cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
+                                cudaStream_t s);
 
 // Either full-pass kernel, by tile shape (runtime.cu).
 bool shape_supported(TileShape shape);

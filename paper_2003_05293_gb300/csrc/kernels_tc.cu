@@ -13,12 +13,22 @@
 // products become real ones (re re - im im, re im + im re), and every FP32
 // operand is split into two BF16 halves, v = hi + lo, with the product kept as
 // hi hi + hi lo + lo hi: 2^-16 relative per product, FP32-class phases.  The
-// accumulators (FP32) live in tensor memory; operands are staged in shared
-// memory in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per
-// core matrix).  One thread issues the MMAs and commits them to an mbarrier;
-// every wait on it is bounded and records a timeout in the launch's status
-// word instead of hanging.
+// accumulators (FP32) live in tensor memory.
+//
+// The operands are factor tables in global memory, laid out block by block
+// exactly as the MMAs read them from shared memory (no-swizzle K-major core
+// matrices, 8 rows x 16 bytes): C (per 64 columns and 16 spots) and C for
+// GEMM 2 (per 64 columns and 128 spots) depend on the spots only and are made
+// once per hologram; R' (per 128 rows and 16 spots) carries w and theta and is
+// remade before every full pass.  A tile streams its blocks into shared memory
+// with bulk copies (cp.async.bulk, completion counted on an mbarrier) through
+// a four-stage ring, so the tile's threads only run the two epilogues.  One
+// thread issues copies and MMAs and commits them to mbarriers; every wait is
+// bounded and a timeout is recorded in the launch's status word instead of
+// hanging.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "tile.cuh"
 
@@ -31,6 +41,7 @@ constexpr int kThreads = 256;
 constexpr int kChunk = 16;          // spots per GEMM 1 instruction (K)
 constexpr int kSpotBlock = 128;     // spots per GEMM 2 instruction (M)
 constexpr int kTmemCols = 256;      // S (cols 0..127) and then Z (cols 0..255)
+constexpr int kStages = 4;          // GEMM 1 ring (the ring also takes GEMM 2's C blocks)
 constexpr uint32_t kWaitPolls = 1u << 20;
 
 // component tiles (bytes): GEMM 1 operands per stage, GEMM 2 operands
@@ -42,23 +53,34 @@ constexpr uint32_t kCs = kSpotBlock * kCols * 2;    // C component [128 spots][6
 
 __host__ __device__ constexpr size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
-// Dynamic shared memory: spot tables, two GEMM 1 stages, u, C for GEMM 2,
-// the half sums of the last epilogue (and 1 KB to align the base).
+static_assert(kStages * kStage >= 4 * kCs, "the GEMM 1 ring holds GEMM 2's C block");
+
+// Dynamic shared memory: tail scratch, the GEMM 1 ring (which also receives
+// GEMM 2's C block), u, the half sums of the last epilogue (and 1 KB to align
+// the base).
 __host__ __device__ constexpr size_t smem_bytes(int maxN)
 {
-    return 1024 + align1k((size_t)maxN * (sizeof(int4) + sizeof(uint2) + sizeof(float2))) + 2 * (size_t)kStage +
-           4 * (size_t)kU + 4 * (size_t)kCs + kSpotBlock * sizeof(float2);
+    return 1024 + align1k((size_t)maxN * sizeof(float2)) + (size_t)kStages * kStage + 4 * (size_t)kU +
+           kSpotBlock * sizeof(float2);
 }
 
 __host__ __device__ inline int tiles(int P) { return ((P + kRows - 1) / kRows) * ((P + kCols - 1) / kCols); }
 
+// Factor tables of one hologram (bytes): R' blocks (row block, spot chunk), C
+// blocks (column block, spot chunk), GEMM 2 C blocks (column block, spot block).
+__host__ __device__ inline int nchunks(int N) { return (N + kChunk - 1) / kChunk; }
+__host__ __device__ inline int nspotblocks(int N) { return (N + kSpotBlock - 1) / kSpotBlock; }
+__host__ __device__ inline size_t rw_table_bytes(int P, int N) { return (size_t)((P + kRows - 1) / kRows) * nchunks(N) * 4 * kA1; }
+__host__ __device__ inline size_t c_table_bytes(int P, int N) { return (size_t)((P + kCols - 1) / kCols) * nchunks(N) * 4 * kB1; }
+__host__ __device__ inline size_t cs_table_bytes(int P, int N)
+{
+    return (size_t)((P + kCols - 1) / kCols) * nspotblocks(N) * 4 * kCs;
+}
+
 struct Smem {
-    int4 *coef;
-    uint2 *bw;
     float2 *v;                  // tail scratch (maxN)
-    unsigned char *g1[2];       // stages: A components (4 x kA1), then B components (4 x kB1)
+    unsigned char *ring;        // kStages x kStage: R' block (4 x kA1) then C block (4 x kB1)
     unsigned char *u;           // 4 x kU: u re hi, re lo, im hi, im lo
-    unsigned char *cs;          // 4 x kCs: C re hi, re lo, im hi, im lo
     float2 *vh;                 // kSpotBlock half sums
 };
 
@@ -66,15 +88,11 @@ __device__ __forceinline__ Smem carve(unsigned char *raw, int maxN)
 {
     unsigned char *b = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
     Smem m;
-    m.coef = reinterpret_cast<int4 *>(b);
-    m.bw = reinterpret_cast<uint2 *>(m.coef + maxN);
-    m.v = reinterpret_cast<float2 *>(m.bw + maxN);
-    b += align1k((size_t)maxN * (sizeof(int4) + sizeof(uint2) + sizeof(float2)));
-    m.g1[0] = b;
-    m.g1[1] = b + kStage;
-    m.u = b + 2 * kStage;
-    m.cs = m.u + 4 * kU;
-    m.vh = reinterpret_cast<float2 *>(m.cs + 4 * kCs);
+    m.v = reinterpret_cast<float2 *>(b);
+    b += align1k((size_t)maxN * sizeof(float2));
+    m.ring = b;
+    m.u = b + kStages * kStage;
+    m.vh = reinterpret_cast<float2 *>(m.u + 4 * kU);
     return m;
 }
 
@@ -129,6 +147,20 @@ __device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
+// One bulk copy global -> shared, counted on an mbarrier (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+// The arrival of the issuing thread, announcing `bytes` of copies to come.
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -176,11 +208,15 @@ __device__ __forceinline__ void put8(unsigned char *base, uint32_t stride, uint3
         *reinterpret_cast<uint4 *>(base + c * stride + off) = make_uint4(w[c][0], w[c][1], w[c][2], w[c][3]);
 }
 
-// Per-block state that lives across tiles: tensor memory and the barriers.
+// Per-block state that lives across tiles: tensor memory, the barriers and how
+// many phases each has been given (a wait always targets the newest phase, so
+// its parity is (issued - 1) & 1).  Every thread keeps the same counts.
+enum Bar { kLd0 = 0, kMma0 = kStages, kLdCs = 2 * kStages, kMma2 = 2 * kStages + 1, kBars = 2 * kStages + 2 };
+
 struct State {
     uint32_t tmem;
-    uint32_t mbar[3];     // GEMM 1 stages 0 and 1, GEMM 2
-    uint32_t phase[3];
+    uint32_t mbar[kBars];
+    uint32_t issued[kBars];
     bool failed;
 };
 
@@ -207,32 +243,48 @@ __device__ __forceinline__ void complex_mma(uint32_t d_re, uint32_t d_im, const 
     mma(d_im, a[3], b[0], id_ir, 1u);
 }
 
-// Waits, on every thread, for the next phase of barrier b.  The outcome is
-// voted across the block, so every thread takes the same path afterwards; a
-// timed-out wait sets bit 0 of the launch's status word and turns the block's
-// remaining tiles into empty ones (nothing waits on a barrier again).
-__device__ __forceinline__ void wait_all(State &st, int b, unsigned *status)
+// Thread 0's wait for the newest phase of barrier b; a timeout marks the block
+// failed in shared memory (read by everyone after the next __syncthreads).
+__device__ __forceinline__ void wait0(State &st, int b, int *s_fail)
+{
+    if (*s_fail) return;
+    if (!wait(st.mbar[b], (st.issued[b] - 1u) & 1u)) *s_fail = 1;
+}
+
+// Every thread's wait for the newest phase of barrier b, voted across the block.
+__device__ __forceinline__ void wait_all(State &st, int b, int *s_fail, unsigned *status)
 {
     bool ok = true;
-    if (!st.failed) ok = wait(st.mbar[b], st.phase[b]);
-    ok = __syncthreads_and(ok) != 0;
-    st.phase[b] ^= 1u;
+    if (!st.failed) ok = wait(st.mbar[b], (st.issued[b] - 1u) & 1u);
+    ok = __syncthreads_and(ok && !*s_fail) != 0;
     if (!ok) {
         if (!st.failed && threadIdx.x == 0) atomicOr(status, 1u);
         st.failed = true;
     }
 }
 
+// GEMM 1's operand blocks of spot chunk c into ring stage s.
+__device__ __forceinline__ void load_chunk(const HoloDev &H, State &st, const Smem &m, int rb, int cb, int c, int s)
+{
+    const int nc = nchunks(H.N);
+    unsigned char *stg = m.ring + s * kStage;
+    const uint32_t bar = st.mbar[kLd0 + s];
+    expect_tx(bar, kStage);
+    bulk_load(saddr(stg), H.rwtab + ((size_t)rb * nc + c) * (4 * kA1), 4 * kA1, bar);
+    bulk_load(saddr(stg + 4 * kA1), H.ctab + ((size_t)cb * nc + c) * (4 * kB1), 4 * kB1, bar);
+}
+
 // One tile of a full iteration or the final pass.
 __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int maxN, unsigned char *raw,
-                             double *s_red, int *s_last, State &st, unsigned *status)
+                             double *s_red, int *s_last, int *s_fail, State &st, unsigned *status)
 {
     const Smem m = carve(raw, maxN);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = H.P, N = H.N, half = P >> 1;
     const int pass = sl.pass;
     const int col_tiles = (P + kCols - 1) / kCols;
-    const int y0 = (t / col_tiles) * kRows, x0 = (t % col_tiles) * kCols;
+    const int rb = t / col_tiles, cb = t % col_tiles;
+    const int y0 = rb * kRows, x0 = cb * kCols;
 
     // a tile wholly outside the round pupil: zero partials; in the final pass
     // phase 0 (gray lut[0]) over its grid pixels.  After a timed-out wait the
@@ -264,75 +316,54 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         return;
     }
 
-    for (int n = tid; n < N; n += kThreads) {
-        m.coef[n] = H.coef[n];
-        const SpotState s = H.state[n];
-        m.bw[n] = make_uint2(s.theta + kFixRound, __float_as_uint(s.w * s.a0));
-    }
-    __syncthreads();
-
     const uint32_t id1 = idesc(kRows, kCols, 0), id1n = idesc(kRows, kCols, 1);
     const uint32_t id2 = idesc(kSpotBlock, kRows, 0), id2n = idesc(kSpotBlock, kRows, 1);
     const uint32_t t_re = st.tmem, t_im1 = st.tmem + kCols, t_im2 = st.tmem + kRows;
 
-    // ---- GEMM 1: S = R' C^T over spot chunks, two stages ----------------------
-    const int nchunk = (N + kChunk - 1) / kChunk;
+    // ---- GEMM 1: S = R' C^T over spot chunks, operands streamed through the ring
+    const int nchunk = nchunks(N);
+    const int pre = min(kStages, nchunk);
+    if (tid == 0 && !st.failed)
+        for (int c = 0; c < pre; ++c) load_chunk(H, st, m, rb, cb, c, c);
+    for (int c = 0; c < pre; ++c) st.issued[kLd0 + c]++;
     for (int c = 0; c < nchunk; ++c) {
-        const int s = c & 1;
-        if (c >= 2) wait_all(st, s, status);
-        unsigned char *stg = m.g1[s];
-        // 256 row items (row, 8 spots) of R', then 128 column items of C
-        for (int i = tid; i < 2 * kRows + 2 * kCols; i += kThreads) {
-            float2 v[8];
-            if (i < 2 * kRows) {
-                const int row = i >> 1, g = i & 1;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int n = c * kChunk + g * 8 + q;
-                    if (n < N) {
-                        const int4 cf = m.coef[n];
-                        const uint2 bw = m.bw[n];
-                        v[q] = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + row - half, bw.x,
-                                           __uint_as_float(bw.y));
-                    } else {
-                        v[q] = make_float2(0.f, 0.f);
-                    }
+        const int s = c % kStages;
+        if (tid == 0 && !st.failed) {
+            wait0(st, kLd0 + s, s_fail);
+            if (!*s_fail) {
+                unsigned char *stg = m.ring + s * kStage;
+                uint64_t a[4], b[4];
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = desc(saddr(stg + q * kA1), 128, 256);
+                    b[q] = desc(saddr(stg + 4 * kA1 + q * kB1), 128, 256);
                 }
-                put8(stg, kA1, core_off(row, g * 8, kChunk), v);
-            } else {
-                const int j = i - 2 * kRows, col = j >> 1, g = j & 1;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int n = c * kChunk + g * 8 + q;
-                    if (n < N) {
-                        const int4 cf = m.coef[n];
-                        v[q] = spot_factor(cf.x, cf.z, __int_as_float(cf.w), x0 + col - half, kFixRound, 1.f);
-                    } else {
-                        v[q] = make_float2(0.f, 0.f);
-                    }
-                }
-                put8(stg + 4 * kA1, kB1, core_off(col, g * 8, kChunk), v);
+                complex_mma(t_re, t_im1, a, b, id1, id1n, c > 0 ? 1u : 0u, 0);
+                commit(st.mbar[kMma0 + s]);
             }
         }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (tid == 0 && !st.failed) {
-            uint64_t a[4], b[4];
-            for (int q = 0; q < 4; ++q) {
-                a[q] = desc(saddr(stg + q * kA1), 128, 256);
-                b[q] = desc(saddr(stg + 4 * kA1 + q * kB1), 128, 256);
+        st.issued[kMma0 + s]++;
+        if (c + kStages < nchunk) {
+            // this chunk's MMAs free stage s for chunk c + kStages
+            if (tid == 0 && !st.failed) {
+                wait0(st, kMma0 + s, s_fail);
+                if (!*s_fail) load_chunk(H, st, m, rb, cb, c + kStages, s);
             }
-            complex_mma(t_re, t_im1, a, b, id1, id1n, c > 0 ? 1u : 0u, 0);
-            commit(st.mbar[s]);
+            st.issued[kLd0 + s]++;
         }
     }
-    // the last two chunks' commits (every earlier one was waited for above)
-    for (int c = max(0, nchunk - 2); c < nchunk; ++c) wait_all(st, c & 1, status);
+    // the last chunk's commit covers every MMA before it
+    wait_all(st, kMma0 + (nchunk - 1) % kStages, s_fail, status);
     fence_after();
 
     // ---- epilogue 1: u = A S / |S| into GEMM 2's B operand; Phi and gray out --
+    // (meanwhile the first spot block's GEMM 2 operand streams into the ring)
+    if (tid == 0 && !st.failed) {
+        const uint32_t bar = st.mbar[kLdCs];
+        expect_tx(bar, 4 * kCs);
+        const unsigned char *src = H.cstab + ((size_t)cb * nspotblocks(N)) * (4 * kCs);
+        for (int q = 0; q < 4; ++q) bulk_load(saddr(m.ring + q * kCs), src + q * kCs, kCs, bar);
+    }
+    st.issued[kLdCs]++;
     {
         const int q = warp & 3, h = warp >> 2;
         const int row = 32 * q + lane, xs = 32 * h;
@@ -388,47 +419,47 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
             }
         }
     }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
 
     // ---- GEMM 2 per block of 128 spots, then V_n = sum_y conj(R_n(y)) Z(n, y) --
-    for (int sb = 0; sb * kSpotBlock < N; ++sb) {
-        // C of this block's spots over the tile's 64 columns: 128 x 8 items
-        for (int i = tid; i < kSpotBlock * (kCols / 8); i += kThreads) {
-            const int nl = i >> 3, g = i & 7, n = sb * kSpotBlock + nl;
-            float2 v[8];
-            if (n < N) {
-                const int4 cf = m.coef[n];
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    v[e] = spot_factor(cf.x, cf.z, __int_as_float(cf.w), x0 + 8 * g + e - half, kFixRound, 1.f);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = make_float2(0.f, 0.f);
+    const int nsb = nspotblocks(N);
+    for (int sb = 0; sb < nsb; ++sb) {
+        if (sb > 0) {
+            // the previous block's MMAs are done (waited below): stream this block's C
+            if (tid == 0 && !st.failed) {
+                const uint32_t bar = st.mbar[kLdCs];
+                expect_tx(bar, 4 * kCs);
+                const unsigned char *src = H.cstab + ((size_t)cb * nsb + sb) * (4 * kCs);
+                for (int q = 0; q < 4; ++q) bulk_load(saddr(m.ring + q * kCs), src + q * kCs, kCs, bar);
             }
-            put8(m.cs, kCs, core_off(nl, 8 * g, kCols), v);
+            st.issued[kLdCs]++;
         }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
         if (tid == 0 && !st.failed) {
-            for (int ks = 0; ks < kCols / 16; ++ks) {
-                uint64_t a[4], b[4];
-                for (int q = 0; q < 4; ++q) {
-                    a[q] = desc(saddr(m.cs + q * kCs) + ks * 256, 128, (kCols / 8) * 128);
-                    b[q] = desc(saddr(m.u + q * kU) + ks * 256, 128, (kCols / 8) * 128);
+            wait0(st, kLdCs, s_fail);
+            if (!*s_fail) {
+                for (int ks = 0; ks < kCols / 16; ++ks) {
+                    uint64_t a[4], b[4];
+                    for (int q = 0; q < 4; ++q) {
+                        a[q] = desc(saddr(m.ring + q * kCs) + ks * 256, 128, (kCols / 8) * 128);
+                        b[q] = desc(saddr(m.u + q * kU) + ks * 256, 128, (kCols / 8) * 128);
+                    }
+                    complex_mma(t_re, t_im2, a, b, id2, id2n, ks > 0 ? 1u : 0u, 1);
                 }
-                complex_mma(t_re, t_im2, a, b, id2, id2n, ks > 0 ? 1u : 0u, 1);
+                commit(st.mbar[kMma2]);
             }
-            commit(st.mbar[2]);
         }
-        wait_all(st, 2, status);
+        st.issued[kMma2]++;
+        wait_all(st, kMma2, s_fail, status);
         fence_after();
         {
             const int q = warp & 3, h = warp >> 2;
             const int nl = 32 * q + lane, n = sb * kSpotBlock + nl;
             const uint32_t lanes = (uint32_t)(32 * q) << 16;
             int4 cf = make_int4(0, 0, 0, 0);
-            if (n < N) cf = m.coef[n];
+            if (n < N) cf = H.coef[n];
             float vr = 0.f, vi = 0.f;
             for (int y16 = 0; y16 < 64; y16 += 16) {
                 const int ys = 64 * h + y16;
@@ -461,6 +492,86 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     finish_tile<kThreads>(H, sl, m.v, s_red, s_last);
 }
 
+// ------------------------------------------------------------- factor tables --
+// Items of eight phasors; consecutive threads take consecutive rows of one
+// core matrix, so a warp's 16-byte stores fill whole 128-byte lines.
+
+// C (GEMM 1's B: 64 columns x 16 spots per block) and C for GEMM 2 (128 spots
+// x 64 columns per block) of hologram blockIdx.y, from its spot coefficients.
+__global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__restrict__ holos, int count)
+{
+    const HoloDev H = holos[blockIdx.y];
+    if (!H.ctab) return;
+    const int P = H.P, N = H.N, half = P >> 1, nc = nchunks(N), nsb = nspotblocks(N);
+    const int ncb = (P + kCols - 1) / kCols;
+    const int items_c = ncb * nc * 128;                 // (block, 64 columns x 2 groups)
+    const int items_cs = ncb * nsb * 1024;              // (block, 128 spots x 8 groups)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items_c + items_cs; i += gridDim.x * blockDim.x) {
+        float2 v[8];
+        if (i < items_c) {
+            const int blk = i >> 7, j = i & 127;
+            const int cb = blk / nc, c = blk % nc;
+            const int col = (j & 7) + 8 * (j >> 4), g = (j >> 3) & 1;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int n = c * kChunk + 8 * g + e;
+                if (n < N) {
+                    const int4 cf = H.coef[n];
+                    v[e] = spot_factor(cf.x, cf.z, __int_as_float(cf.w), cb * kCols + col - half, kFixRound, 1.f);
+                } else {
+                    v[e] = make_float2(0.f, 0.f);
+                }
+            }
+            put8(H.ctab + (size_t)blk * (4 * kB1), kB1, core_off(col, 8 * g, kChunk), v);
+        } else {
+            const int k = i - items_c, blk = k >> 10, j = k & 1023;
+            const int cb = blk / nsb, sb = blk % nsb;
+            const int nl = (j & 7) + 8 * (j >> 6), g = (j >> 3) & 7, n = sb * kSpotBlock + nl;
+            if (n < N) {
+                const int4 cf = H.coef[n];
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    v[e] = spot_factor(cf.x, cf.z, __int_as_float(cf.w), cb * kCols + 8 * g + e - half, kFixRound, 1.f);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = make_float2(0.f, 0.f);
+            }
+            put8(H.cstab + (size_t)blk * (4 * kCs), kCs, core_off(nl, 8 * g, kCols), v);
+        }
+    }
+}
+
+// R' = w a e^{i theta} R (GEMM 1's A: 128 rows x 16 spots per block) of the
+// hologram of each full-pass slot, from its current spot state.
+__global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restrict__ holos,
+                                                        const LaunchSlot *__restrict__ slots)
+{
+    const LaunchSlot sl = slots[blockIdx.y];
+    const HoloDev H = holos[sl.holo];
+    if (!H.rwtab || sl.pass == kPassSubset) return;
+    const int P = H.P, N = H.N, half = P >> 1, nc = nchunks(N);
+    const int items = ((P + kRows - 1) / kRows) * nc * 256;      // (block, 128 rows x 2 groups)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items; i += gridDim.x * blockDim.x) {
+        const int blk = i >> 8, j = i & 255;
+        const int rb = blk / nc, c = blk % nc;
+        const int row = (j & 7) + 8 * (j >> 4), g = (j >> 3) & 1;
+        float2 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int n = c * kChunk + 8 * g + e;
+            if (n < N) {
+                const int4 cf = H.coef[n];
+                const SpotState s = H.state[n];
+                v[e] = spot_factor(cf.y, cf.z, __int_as_float(cf.w), rb * kRows + row - half, s.theta + kFixRound,
+                                   s.w * s.a0);
+            } else {
+                v[e] = make_float2(0.f, 0.f);
+            }
+        }
+        put8(H.rwtab + (size_t)blk * (4 * kA1), kA1, core_off(row, 8 * g, kChunk), v);
+    }
+}
+
 }  // namespace tc
 
 __global__ void __launch_bounds__(tc::kThreads, 1)
@@ -469,14 +580,15 @@ iter_full_tc_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restr
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ double s_red[tc::kThreads / 32];
-    __shared__ int s_last, s_item, s_slot;
-    __shared__ __align__(8) uint64_t s_mbar[3];
+    __shared__ int s_last, s_item, s_slot, s_fail;
+    __shared__ __align__(8) uint64_t s_mbar[tc::kBars];
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        for (int b = 0; b < 3; ++b)
+        for (int b = 0; b < tc::kBars; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc::saddr(&s_mbar[b])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
     }
     if ((tid >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -488,9 +600,9 @@ iter_full_tc_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restr
     tc::fence_after();
     tc::State st;
     st.tmem = s_tmem;
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b < tc::kBars; ++b) {
         st.mbar[b] = tc::saddr(&s_mbar[b]);
-        st.phase[b] = 0u;
+        st.issued[b] = 0u;
     }
     st.failed = false;
     unsigned *status = queue + 2;
@@ -514,7 +626,7 @@ iter_full_tc_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restr
         if (item >= total_tiles) break;
         const LaunchSlot sl = slots[s_slot];
         const HoloDev H = holos[sl.holo];
-        tc::process_tile(H, sl, item - sl.tile_begin, maxN, smem, s_red, &s_last, st, status);
+        tc::process_tile(H, sl, item - sl.tile_begin, maxN, smem, s_red, &s_last, &s_fail, st, status);
     }
     tc::fence_before();
     __syncthreads();
@@ -552,6 +664,32 @@ int full_tc_max_grid(int maxN, int sm_count)
     // tensor memory: each block holds kTmemCols of the SM's 512 columns
     per_sm = min(per_sm, 512 / tc::kTmemCols);
     return per_sm * sm_count;
+}
+
+void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs)
+{
+    *rw = tc::rw_table_bytes(P, N);
+    *c = tc::c_table_bytes(P, N);
+    *cs = tc::cs_table_bytes(P, N);
+}
+
+cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    (void)cudaGetLastError();
+    dim3 grid((unsigned)std::max(1, 2 * sm_count / std::max(1, count)), (unsigned)count);
+    tc::const_tables_kernel<<<grid, 256, 0, s>>>(holos, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
+                                cudaStream_t s)
+{
+    if (nslots <= 0) return cudaSuccess;
+    (void)cudaGetLastError();
+    dim3 grid((unsigned)std::max(1, 2 * sm_count / std::max(1, nslots)), (unsigned)nslots);
+    tc::rw_tables_kernel<<<grid, 256, 0, s>>>(holos, slots);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_full_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,

@@ -293,6 +293,11 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         work += 256;                                                            // counter
         work += align256(sizeof(double) * (2 + s.N));                           // metrics
         if (host_out) work += align256(sizeof(float) * (size_t)M);              // own phase
+        if (shape.full_threads == kFullTc) {                                    // tensor-core factor tables
+            size_t rw, c, cs;
+            full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
+            work += align256(rw) + align256(c) + align256(cs);
+        }
         b->maxN = std::max(b->maxN, s.N);
     }
     CSWGS_TRY(b->mem.ensure(work));
@@ -351,6 +356,16 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             w += align256(sizeof(float) * (size_t)M);
         }
         H.phase_out = b->own_phase[h];
+        if (shape.full_threads == kFullTc) {
+            size_t rw, c, cs;
+            full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
+            H.rwtab = reinterpret_cast<unsigned char *>(base + w);
+            w += align256(rw);
+            H.ctab = reinterpret_cast<unsigned char *>(base + w);
+            w += align256(c);
+            H.cstab = reinterpret_cast<unsigned char *>(base + w);
+            w += align256(cs);
+        }
     }
 
     // launch schedule: step L advances every hologram that still has work, with
@@ -501,6 +516,8 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s));
     if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, evflag));
     CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
+    const bool tc = b->shape.full_threads == kFullTc;
+    if (tc) CSWGS_CUDA_TRY(launch_tc_const_tables(holos, count, b->plan->sm_count, s));
     const size_t steps = b->l_tiles.size() / 2;
     for (size_t L = 0; L < steps; ++L) {
         if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[L + 1], s, evflag));
@@ -509,6 +526,8 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
             const int tiles = b->l_tiles[i];
             if (tiles == 0) continue;
             const int grid = std::min(b->grid[kind], tiles);
+            if (tc && kind == kLaunchFull)
+                CSWGS_CUDA_TRY(launch_tc_rw_tables(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count, s));
             CSWGS_CUDA_TRY(shape_launch(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
                                             b->l_maxN[i], queue, grid, s));
         }

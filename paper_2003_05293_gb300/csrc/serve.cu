@@ -146,6 +146,11 @@ size_t Server::footprint(const HoloSpec &s) const
     b += al256(sizeof(float2) * tiles * s.N) + al256(sizeof(double2) * tiles * s.N);
     b += 256 + al256(sizeof(double) * (2 + s.N));
     b += al256(sizeof(float) * M);   // phase map (the caller's device buffer is used when given)
+    if (shape_.full_threads == kFullTc) {
+        size_t rw, c, cs;
+        full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
+        b += al256(rw) + al256(c) + al256(cs);
+    }
     return b;
 }
 
@@ -191,7 +196,18 @@ void Server::place(Req &r)
     H.metrics = reinterpret_cast<double *>(b + o);
     o += al256(sizeof(double) * (2 + s.N));
     float *own = reinterpret_cast<float *>(b + o);
+    o += al256(sizeof(float) * (size_t)s.P * s.P);
     H.phase_out = r.phase_dev ? r.phase_dev : own;
+    if (shape_.full_threads == kFullTc) {
+        size_t rw, c, cs;
+        full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
+        H.rwtab = reinterpret_cast<unsigned char *>(b + o);
+        o += al256(rw);
+        H.ctab = reinterpret_cast<unsigned char *>(b + o);
+        o += al256(c);
+        H.cstab = reinterpret_cast<unsigned char *>(b + o);
+        o += al256(cs);
+    }
 }
 
 cswgs_status Server::submit(const cswgs_request &q, uint64_t *ticket)
@@ -400,6 +416,7 @@ void Server::loop()
             int pmax = 0;
             for (int i = 0; i < nprep; ++i) pmax = std::max(pmax, prep_h[i].N);
             launch_prep_fp32(prep_d, nprep, pmax, stream_);
+            if (shape_.full_threads == kFullTc) launch_tc_const_tables(prep_d, nprep, p_->sm_count, stream_);
         }
         cudaMemcpyAsync(sd, sbuf, sizeof(LaunchSlot) * nslots, cudaMemcpyHostToDevice, stream_);
         cudaEventRecord(start_ev_[serial & 1], stream_);
@@ -409,6 +426,8 @@ void Server::loop()
             auto g = grid_for.find(key);
             if (g == grid_for.end())
                 g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
+            if (kind == kLaunchFull && shape_.full_threads == kFullTc)
+                launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, stream_);
             shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
                              queue, std::min(g->second, group_tiles[kind]), stream_);
         }
