@@ -37,7 +37,8 @@ namespace tc {
 
 constexpr int kRows = 128;          // tile rows (GEMM 1 M, GEMM 2 N)
 constexpr int kCols = 64;           // tile columns (GEMM 1 N, GEMM 2 K)
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int kGroups = kThreads / 128;   // warps per TMEM lane quadrant: the epilogues split columns among them
 constexpr int kChunk = 16;          // spots per GEMM 1 instruction (K)
 constexpr int kSpotBlock = 128;     // spots per GEMM 2 instruction (M)
 constexpr int kTmemCols = 256;      // S (cols 0..127) and then Z (cols 0..255)
@@ -61,7 +62,7 @@ static_assert(kStages * kStage >= 4 * kCs, "the GEMM 1 ring holds GEMM 2's C blo
 __host__ __device__ constexpr size_t smem_bytes(int maxN)
 {
     return 1024 + align1k((size_t)maxN * sizeof(float2)) + (size_t)kStages * kStage + 4 * (size_t)kU +
-           kSpotBlock * sizeof(float2);
+           (kGroups - 1) * kSpotBlock * sizeof(float2);
 }
 
 __host__ __device__ inline int tiles(int P) { return ((P + kRows - 1) / kRows) * ((P + kCols - 1) / kCols); }
@@ -77,11 +78,12 @@ __host__ __device__ inline size_t cs_table_bytes(int P, int N)
     return (size_t)((P + kCols - 1) / kCols) * nspotblocks(N) * 4 * kCs;
 }
 
+
 struct Smem {
     float2 *v;                  // tail scratch (maxN)
     unsigned char *ring;        // kStages x kStage: R' block (4 x kA1) then C block (4 x kB1)
     unsigned char *u;           // 4 x kU: u re hi, re lo, im hi, im lo
-    float2 *vh;                 // kSpotBlock half sums
+    float2 *vh;                 // (kGroups - 1) x kSpotBlock partial sums
 };
 
 __device__ __forceinline__ Smem carve(unsigned char *raw, int maxN)
@@ -320,35 +322,40 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     const uint32_t id2 = idesc(kSpotBlock, kRows, 0), id2n = idesc(kSpotBlock, kRows, 1);
     const uint32_t t_re = st.tmem, t_im1 = st.tmem + kCols, t_im2 = st.tmem + kRows;
 
-    // ---- GEMM 1: S = R' C^T over spot chunks, operands streamed through the ring
+    // ---- GEMM 1: S = R' C^T over spot chunks, operands streamed through the ring.
+    // Chunk c's MMAs are queued before thread 0 waits for chunk c - 1's, whose
+    // stage then takes chunk c - 1 + kStages: the tensor pipe always has work.
     const int nchunk = nchunks(N);
     const int pre = min(kStages, nchunk);
     if (tid == 0 && !st.failed)
         for (int c = 0; c < pre; ++c) load_chunk(H, st, m, rb, cb, c, c);
     for (int c = 0; c < pre; ++c) st.issued[kLd0 + c]++;
+    // descriptors of stage 0; stage s and component q are a start-address offset
+    // ((s kStage + q kA1) / 16 for A, (s kStage + 4 kA1 + q kB1) / 16 for B)
+    const uint64_t a0 = desc(saddr(m.ring), 128, 256);
     for (int c = 0; c < nchunk; ++c) {
         const int s = c % kStages;
         if (tid == 0 && !st.failed) {
             wait0(st, kLd0 + s, s_fail);
             if (!*s_fail) {
-                unsigned char *stg = m.ring + s * kStage;
                 uint64_t a[4], b[4];
                 for (int q = 0; q < 4; ++q) {
-                    a[q] = desc(saddr(stg + q * kA1), 128, 256);
-                    b[q] = desc(saddr(stg + 4 * kA1 + q * kB1), 128, 256);
+                    a[q] = a0 + ((uint64_t)(s * kStage + q * kA1) >> 4);
+                    b[q] = a0 + ((uint64_t)(s * kStage + 4 * kA1 + q * kB1) >> 4);
                 }
                 complex_mma(t_re, t_im1, a, b, id1, id1n, c > 0 ? 1u : 0u, 0);
                 commit(st.mbar[kMma0 + s]);
             }
         }
         st.issued[kMma0 + s]++;
-        if (c + kStages < nchunk) {
-            // this chunk's MMAs free stage s for chunk c + kStages
+        const int cr = c - 1;   // the chunk whose stage is refilled now
+        if (cr >= 0 && cr + kStages < nchunk) {
+            const int sr = cr % kStages;
             if (tid == 0 && !st.failed) {
-                wait0(st, kMma0 + s, s_fail);
-                if (!*s_fail) load_chunk(H, st, m, rb, cb, c + kStages, s);
+                wait0(st, kMma0 + sr, s_fail);
+                if (!*s_fail) load_chunk(H, st, m, rb, cb, cr + kStages, sr);
             }
-            st.issued[kLd0 + s]++;
+            st.issued[kLd0 + sr]++;
         }
     }
     // the last chunk's commit covers every MMA before it
@@ -366,56 +373,57 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
     st.issued[kLdCs]++;
     {
         const int q = warp & 3, h = warp >> 2;
-        const int row = 32 * q + lane, xs = 32 * h;
+        const int row = 32 * q + lane;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
-        float sr[32], si[32];
-        ld16(t_re + lanes + xs, sr);
-        ld16(t_re + lanes + xs + 16, sr + 16);
-        ld16(t_im1 + lanes + xs, si);
-        ld16(t_im1 + lanes + xs + 16, si + 16);
-        ld_wait();
         const int gy = y0 + row, yq = gy - half;
         const int64_t R2 = (int64_t)half * half;
-        float o[32];
+        for (int xc = 0; xc < kCols / kGroups; xc += 16) {
+            const int xs = (kCols / kGroups) * h + xc;
+            float sr[16], si[16];
+            ld16(t_re + lanes + xs, sr);
+            ld16(t_im1 + lanes + xs, si);
+            ld_wait();
+            float o[16];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float2 u[8];
+            for (int g = 0; g < 2; ++g) {
+                float2 u[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int j = 8 * g + e;
-                const int gx = x0 + xs + j, xq = gx - half;
-                const int64_t rho2 = (int64_t)xq * xq + (int64_t)yq * yq;
-                const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2);
-                const float a = sr[j], b = si[j];
-                const float n2 = a * a + b * b;
-                if (pass == kPassFinal) {
-                    float ph = atan2f(b, a);
-                    ph = ph < 0.f ? ph + kTwoPiF : ph;
-                    o[j] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
-                }
-                if (!valid) u[e] = make_float2(0.f, 0.f);
-                else if (n2 > 0.f) {
-                    const float rs = rsqrtf(n2) * pupil_amp(H, (float)rho2);
-                    u[e] = make_float2(a * rs, b * rs);
-                } else u[e] = make_float2(pupil_amp(H, (float)rho2), 0.f);
-            }
-            put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
-        }
-        if (pass == kPassFinal && gy < P) {
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const int col = x0 + xs + 4 * g;
-                if (col >= P) break;
-                if (H.phase_out) {
-                    float *dst = H.phase_out + (size_t)gy * P + col;
-                    if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-                        *reinterpret_cast<float4 *>(dst) = make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
-                    } else {
-                        for (int e = 0; e < 4; ++e)
-                            if (col + e < P) dst[e] = o[4 * g + e];
+                for (int e = 0; e < 8; ++e) {
+                    const int j = 8 * g + e;
+                    const int gx = x0 + xs + j, xq = gx - half;
+                    const int64_t rho2 = (int64_t)xq * xq + (int64_t)yq * yq;
+                    const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2);
+                    const float a = sr[j], b = si[j];
+                    const float n2 = a * a + b * b;
+                    if (pass == kPassFinal) {
+                        float ph = atan2f(b, a);
+                        ph = ph < 0.f ? ph + kTwoPiF : ph;
+                        o[j] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
                     }
+                    if (!valid) u[e] = make_float2(0.f, 0.f);
+                    else if (n2 > 0.f) {
+                        const float rs = rsqrtf(n2) * pupil_amp(H, (float)rho2);
+                        u[e] = make_float2(a * rs, b * rs);
+                    } else u[e] = make_float2(pupil_amp(H, (float)rho2), 0.f);
                 }
-                if (H.slm) write_gray4(H, gy, col, o + 4 * g);
+                put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+            }
+            if (pass == kPassFinal && gy < P) {
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int col = x0 + xs + 4 * g;
+                    if (col >= P) break;
+                    if (H.phase_out) {
+                        float *dst = H.phase_out + (size_t)gy * P + col;
+                        if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                            *reinterpret_cast<float4 *>(dst) = make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
+                        } else {
+                            for (int e = 0; e < 4; ++e)
+                                if (col + e < P) dst[e] = o[4 * g + e];
+                        }
+                    }
+                    if (H.slm) write_gray4(H, gy, col, o + 4 * g);
+                }
             }
         }
     }
@@ -440,11 +448,13 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         if (tid == 0 && !st.failed) {
             wait0(st, kLdCs, s_fail);
             if (!*s_fail) {
+                const uint64_t ca = desc(saddr(m.ring), 128, (kCols / 8) * 128);
+                const uint64_t ua = desc(saddr(m.u), 128, (kCols / 8) * 128);
                 for (int ks = 0; ks < kCols / 16; ++ks) {
                     uint64_t a[4], b[4];
                     for (int q = 0; q < 4; ++q) {
-                        a[q] = desc(saddr(m.ring + q * kCs) + ks * 256, 128, (kCols / 8) * 128);
-                        b[q] = desc(saddr(m.u + q * kU) + ks * 256, 128, (kCols / 8) * 128);
+                        a[q] = ca + ((uint64_t)(q * kCs + ks * 256) >> 4);
+                        b[q] = ua + ((uint64_t)(q * kU + ks * 256) >> 4);
                     }
                     complex_mma(t_re, t_im2, a, b, id2, id2n, ks > 0 ? 1u : 0u, 1);
                 }
@@ -461,29 +471,44 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
             int4 cf = make_int4(0, 0, 0, 0);
             if (n < N) cf = H.coef[n];
             float vr = 0.f, vi = 0.f;
-            for (int y16 = 0; y16 < 64; y16 += 16) {
-                const int ys = 64 * h + y16;
+            for (int y16 = 0; y16 < kRows / kGroups; y16 += 16) {
+                const int ys = (kRows / kGroups) * h + y16;
                 float zr[16], zi[16];
                 ld16(t_re + lanes + ys, zr);
                 ld16(t_im2 + lanes + ys, zi);
+                float4 r4[8];
+                if (n < N) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float2 a = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e - half, kFixRound, 1.f);
+                        const float2 b = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e + 1 - half, kFixRound, 1.f);
+                        r4[e] = make_float4(a.x, a.y, b.x, b.y);
+                    }
+                }
                 ld_wait();
                 if (n < N) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const float2 r = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + e - half, kFixRound, 1.f);
-                        vr = fmaf(r.x, zr[e], fmaf(r.y, zi[e], vr));
-                        vi = fmaf(r.x, zi[e], fmaf(-r.y, zr[e], vi));
+                    for (int e = 0; e < 8; ++e) {
+                        vr = fmaf(r4[e].x, zr[2 * e], fmaf(r4[e].y, zi[2 * e], vr));
+                        vi = fmaf(r4[e].x, zi[2 * e], fmaf(-r4[e].y, zr[2 * e], vi));
+                        vr = fmaf(r4[e].z, zr[2 * e + 1], fmaf(r4[e].w, zi[2 * e + 1], vr));
+                        vi = fmaf(r4[e].z, zi[2 * e + 1], fmaf(-r4[e].w, zr[2 * e + 1], vi));
                     }
                 }
             }
-            if (h == 1) m.vh[nl] = make_float2(vr, vi);
+            if (h > 0) m.vh[(h - 1) * kSpotBlock + nl] = make_float2(vr, vi);
             fence_before();
             __syncthreads();
             if (h == 0 && n < N) {
-                const float2 o2 = m.vh[nl];
+#pragma unroll
+                for (int g = 0; g < kGroups - 1; ++g) {
+                    const float2 o2 = m.vh[g * kSpotBlock + nl];
+                    vr += o2.x;
+                    vi += o2.y;
+                }
                 const size_t off = (size_t)t * N + n;
-                if (pass == kPassFinal) H.part64[off] = make_double2((double)vr + (double)o2.x, (double)vi + (double)o2.y);
-                else H.part[off] = make_float2(vr + o2.x, vi + o2.y);
+                if (pass == kPassFinal) H.part64[off] = make_double2((double)vr, (double)vi);
+                else H.part[off] = make_float2(vr, vi);
             }
         }
         __syncthreads();
