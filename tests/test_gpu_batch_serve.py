@@ -98,6 +98,28 @@ def test_solve_batch_host_outputs(plan):
         assert abs(r["u"] - s["u"]) < TOL_SAME_EU
 
 
+def test_pinned_and_pageable_host_outputs(plan):
+    # host phase maps in pinned and in pageable memory: both give the device
+    # result, for batches and single solves
+    pbs = small_mix(4, 7)
+    pinned = [torch.empty(pb.M, dtype=torch.float32, pin_memory=True).numpy() for pb in pbs]
+    pageable = [np.empty(pb.M, dtype=np.float32) for pb in pbs]
+    for o in pinned + pageable:
+        o.fill(-1.0)
+    r1 = plan.solve_batch(pbs, pinned)
+    r2 = plan.solve_batch(pbs, pageable)
+    for pb, a, b, x, y in zip(pbs, pinned, pageable, r1, r2):
+        s, ph = solo(plan, pb)
+        assert np.all(a >= 0) and rms_wrapped(a, ph) < TOL_SAME_PHASE
+        assert np.array_equal(a, b)
+        assert x["e"] == y["e"] and abs(x["e"] - s["e"]) < TOL_SAME_EU
+    pb = pbs[0]
+    host = torch.full((pb.M,), -1.0, dtype=torch.float32, pin_memory=True).numpy()
+    r = plan.solve(pb.xyz, pb.P, pb.c, pb.iterations, pb.seed, amp=pb.amp, out=host)
+    s, ph = solo(plan, pb)
+    assert np.all(host >= 0) and rms_wrapped(host, ph) < TOL_SAME_PHASE and abs(r["e"] - s["e"]) < TOL_SAME_EU
+
+
 def test_serving_mixed_stream_equals_solo():
     from paper_2003_05293_gb300 import Plan
     with Plan(precision="fp32", max_batch=4) as p:
