@@ -653,8 +653,16 @@ def main():
         import oracle
         pb = pbs[0]
         t0 = time.perf_counter()
-        oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+        ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
         dt = time.perf_counter() - t0
+        # the same hologram from the timed batch against the oracle (wrapped phase
+        # RMS over the map, e and u)
+        ph = outs[0].cpu().numpy().astype(np.float64)
+        d = (ph - ref["phase"] + np.pi) % (2 * np.pi) - np.pi
+        line["parity_vs_oracle"] = {"hologram": "the batch's first (P=%d, N=%d)" % (pb.P, pb.N),
+                                    "phase_rms_rad": float(np.sqrt(np.mean(d * d))),
+                                    "abs_de": abs(res[0]["e"] - ref["e"]), "abs_du": abs(res[0]["u"] - ref["u"]),
+                                    "tolerance": {"phase_rms_rad": 1e-3, "abs_de": 1e-3, "abs_du": 1e-3}}
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "holograms/s", "cores": oracle.threads(),
                                 "kind": "oracle",
                                 "sample": "1 hologram of the workload (P=%d, N=%d, c=%g, %d iterations), FP64 C "

@@ -175,13 +175,13 @@ void Server::place(Req &r)
     double *xyz = reinterpret_cast<double *>(b + o);
     o += al256(sizeof(double) * 3 * s.N);
     H.xyz = xyz;
-    cudaMemcpyAsync(xyz, stg, sizeof(double) * 3 * s.N, cudaMemcpyHostToDevice, stream_);
+    note(cudaMemcpyAsync(xyz, stg, sizeof(double) * 3 * s.N, cudaMemcpyHostToDevice, stream_));
     if (s.has_amp) {
         std::memcpy(stg + 3 * s.N, s.amp.data(), sizeof(double) * s.N);
         double *a = reinterpret_cast<double *>(b + o);
         o += al256(sizeof(double) * s.N);
         H.amp = a;
-        cudaMemcpyAsync(a, stg + 3 * s.N, sizeof(double) * s.N, cudaMemcpyHostToDevice, stream_);
+        note(cudaMemcpyAsync(a, stg + 3 * s.N, sizeof(double) * s.N, cudaMemcpyHostToDevice, stream_));
     }
     H.coef = reinterpret_cast<int4 *>(b + o);
     o += al256(sizeof(int4) * s.N);
@@ -279,6 +279,8 @@ void Server::loop()
     std::unique_lock<std::mutex> lk(mu_);
     int64_t inflight_prev = -1;   // serial of the previous launch, not yet waited for
     std::map<std::pair<int, int>, int> grid_for;   // (kernel kind, max N) -> resident blocks
+    // a failed CUDA call is kept: every request finished after it reports CSWGS_ECUDA
+    auto chk = [this](cudaError_t e) { note(e); };
     while (true) {
         if (stop_) {
             // the plan is going away: everything pending is cancelled
@@ -342,7 +344,8 @@ void Server::loop()
                 if (!r || !r->finishing || r->last_launch > completed_serial_) continue;
                 const double *m = met_h_ + (size_t)(r->last_launch & 1) * 2 * B + 2 * s;
                 r->met.assign(m, m + 2);
-                cswgs_status st = status_h_[r->last_launch & 1] ? CSWGS_ETIMEOUT : CSWGS_OK;
+                cswgs_status st = cuda_err_ != cudaSuccess ? CSWGS_ECUDA
+                                  : status_h_[r->last_launch & 1] ? CSWGS_ETIMEOUT : CSWGS_OK;
                 if (r->phase_host) {
                     cudaError_t e = cudaMemcpy(r->phase_host, r->dev.phase_out,
                                                sizeof(float) * (size_t)r->spec.P * r->spec.P,
@@ -358,9 +361,9 @@ void Server::loop()
             if (inflight_prev < 0) return;
             const int64_t w = inflight_prev;
             lk.unlock();
-            cudaEventSynchronize(launch_ev_[w & 1]);
+            chk(cudaEventSynchronize(launch_ev_[w & 1]));
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, start_ev_[w & 1], launch_ev_[w & 1]);
+            chk(cudaEventElapsedTime(&ms, start_ev_[w & 1], launch_ev_[w & 1]));
             lk.lock();
             st_.busy_ms += ms;
             completed_serial_ = w;
@@ -410,16 +413,16 @@ void Server::loop()
         HoloDev *hbuf = holos_h_[serial & 1];
         std::memcpy(hbuf, master_.data(), sizeof(HoloDev) * B);
         LaunchSlot *sd = slots_d_.as<LaunchSlot>() + (serial & 1) * B;
-        cudaMemcpyAsync(holos, hbuf, sizeof(HoloDev) * B, cudaMemcpyHostToDevice, stream_);
+        chk(cudaMemcpyAsync(holos, hbuf, sizeof(HoloDev) * B, cudaMemcpyHostToDevice, stream_));
         if (nprep) {
-            cudaMemcpyAsync(prep_d, prep_h, sizeof(HoloDev) * nprep, cudaMemcpyHostToDevice, stream_);
+            chk(cudaMemcpyAsync(prep_d, prep_h, sizeof(HoloDev) * nprep, cudaMemcpyHostToDevice, stream_));
             int pmax = 0;
             for (int i = 0; i < nprep; ++i) pmax = std::max(pmax, prep_h[i].N);
-            launch_prep_fp32(prep_d, nprep, pmax, stream_);
-            if (shape_.full_threads == kFullTc) launch_tc_const_tables(prep_d, nprep, p_->sm_count, stream_);
+            chk(launch_prep_fp32(prep_d, nprep, pmax, stream_));
+            if (shape_.full_threads == kFullTc) chk(launch_tc_const_tables(prep_d, nprep, p_->sm_count, stream_));
         }
-        cudaMemcpyAsync(sd, sbuf, sizeof(LaunchSlot) * nslots, cudaMemcpyHostToDevice, stream_);
-        cudaEventRecord(start_ev_[serial & 1], stream_);
+        chk(cudaMemcpyAsync(sd, sbuf, sizeof(LaunchSlot) * nslots, cudaMemcpyHostToDevice, stream_));
+        chk(cudaEventRecord(start_ev_[serial & 1], stream_));
         for (int kind = 0, first = 0; kind < 2; first += group_slots[kind], ++kind) {
             if (group_tiles[kind] == 0) continue;
             auto key = std::make_pair(kind, group_maxN[kind]);
@@ -427,18 +430,18 @@ void Server::loop()
             if (g == grid_for.end())
                 g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
             if (kind == kLaunchFull && shape_.full_threads == kFullTc)
-                launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, stream_);
-            shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
-                             queue, std::min(g->second, group_tiles[kind]), stream_);
+                chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, stream_));
+            chk(shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
+                             queue, std::min(g->second, group_tiles[kind]), stream_));
         }
         double *mh = met_h_ + (size_t)(serial & 1) * 2 * B;
         for (Req *r : finishing) {
-            cudaMemcpyAsync(mh + 2 * r->slot, r->dev.metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+            chk(cudaMemcpyAsync(mh + 2 * r->slot, r->dev.metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream_));
             r->finishing = true;
         }
         // the launches' status word (a timed-out wait inside a kernel sets it)
-        cudaMemcpyAsync(status_h_ + (serial & 1), queue + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_);
-        cudaEventRecord(launch_ev_[serial & 1], stream_);
+        chk(cudaMemcpyAsync(status_h_ + (serial & 1), queue + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, stream_));
+        chk(cudaEventRecord(launch_ev_[serial & 1], stream_));
         for (Req *r : order) {          // only the requests that took part advance
             r->L++;
             r->last_launch = serial;

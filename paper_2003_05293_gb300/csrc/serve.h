@@ -76,6 +76,11 @@ private:
     LaunchSlot *slots_h_[2] = {nullptr, nullptr};   // pinned, double-buffered (slots, then prep list)
     double *met_h_ = nullptr;                       // pinned: e, u per slot, double-buffered
     unsigned *status_h_ = nullptr;                  // pinned: the launches' status word, double-buffered
+    cudaError_t cuda_err_ = cudaSuccess;            // first failed CUDA call of the loop (sticky)
+    void note(cudaError_t e)
+    {
+        if (e != cudaSuccess && cuda_err_ == cudaSuccess) cuda_err_ = e;
+    }
     double *in_h_ = nullptr;                        // pinned: per-slot input staging (N x 4 doubles)
     cudaEvent_t launch_ev_[2] = {nullptr, nullptr};
     cudaEvent_t start_ev_[2] = {nullptr, nullptr};
