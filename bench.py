@@ -40,11 +40,13 @@ FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
 # DRAM bytes (read + write) per launch of the iteration kernels at the default
 # workload, from one ncu capture of this bench
 # (profiles/iter_kernels_b64_P1152_N100_launches.md): compressed launches, and
-# full-pixel launches (2 full iterations + the final pass, averaged).  Each is
+# full-pixel launches on the tensor cores (2 full iterations + the final pass,
+# averaged; the factor tables are read once per pass, the final pass writes the
+# phase maps).  Each is
 # reported only while the sources of its kernel hash to the value they had
 # when it was measured.
-TRAFFIC_MEASURED = {"sub": {"sha": "3bdfbecac4b139e7", "bytes": 335689},
-                    "full": {"sha": "3bdfbecac4b139e7", "bytes": 103352235}}
+TRAFFIC_MEASURED = {"sub": {"sha": "3bdfbecac4b139e7", "bytes": 332928},
+                    "full": {"sha": "f8a8ab6b82bc7cb0", "bytes": 317353557}}
 KERNEL_SOURCES = {"sub": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu"),
                   "full": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu", "kernels_tc.cu")}
 
