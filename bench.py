@@ -69,6 +69,21 @@ def measured_traffic(args):
     return tuple(out)
 
 
+# full_threads markers of the tensor-core kernels: kernel name, threads per block
+TC_KERNELS = {1: ("iter_full_tc_kernel", 512),
+              2: ("iter_full_tcws_kernel (warp-specialised: 8 epilogue warps + 1 control warp)", 288)}
+
+
+def launches_per_step(tile, n_sub, n_full):
+    """Kernel launches of one batch step: the per-spot preparation, the
+    tensor-core constant tables (once per hologram), every compressed
+    iteration, and per full pass the kernel plus, on the tensor cores, its R'
+    table kernel and, for the warp-specialised kernel, its tails kernel."""
+    ft = tile["full_threads"]
+    tc = ft in TC_KERNELS
+    return 1 + (1 if tc else 0) + n_sub + n_full * (1 + (1 if tc else 0) + (1 if ft == 2 else 0))
+
+
 def full_roofline(tile, achieved_tflops, fma_peak, sm_count, max_mhz, traffic, n_launches, full_ms):
     """Roofline of the full-iteration and final launches: the tensor-core kernel
     against the measured dense BF16 peak (its operands are BF16 halves), the
@@ -77,7 +92,7 @@ def full_roofline(tile, achieved_tflops, fma_peak, sm_count, max_mhz, traffic, n
     base = {"achieved": achieved_tflops, "unit": "TFLOP/s", "traffic": traffic,
             "flops_basis": "8 flops (complex multiply-add) per pixel-spot pair and pass",
             "ms_per_launch": full_ms / max(1, n_launches)}
-    if tile["full_threads"] == 1:
+    if tile["full_threads"] in TC_KERNELS:
         peak, basis = 1700.0, "fallback (sustained)"
         try:
             mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -86,11 +101,13 @@ def full_roofline(tile, achieved_tflops, fma_peak, sm_count, max_mhz, traffic, n
             pass
         base.update({"bound": "tensor", "pipe": "tcgen05 kind::f16 (BF16 in, FP32 accumulate)", "peak": peak,
                      "frac": achieved_tflops / peak, "peak_basis": "%s dense BF16 peak" % basis,
-                     "kernel": "iter_full_tc_kernel, full-iteration and final launches (%d per step)" % n_launches,
+                     "kernel": "%s, full-iteration and final launches (%d per step)"
+                               % (TC_KERNELS[tile["full_threads"]][0], n_launches),
                      "issued_tensor_flops_per_algorithmic": 3,
                      "note": "each real product is 3 BF16 products (hi hi + hi lo + lo hi) for FP32-class "
                              "accuracy, so the tensor pipe runs 3x the algorithmic flops",
-                     "tile": {"threads": 256, "blocks": tile["full_blocks"], "pixels": "128 rows x 64 columns"}})
+                     "tile": {"threads": TC_KERNELS[tile["full_threads"]][1], "blocks": tile["full_blocks"],
+                              "pixels": "128 rows x 64 columns"}})
     else:
         base.update({"bound": "alu", "pipe": "FP32 FMA", "peak": fma_peak, "frac": achieved_tflops / fma_peak,
                      "peak_basis": "%d SMs x %d lanes x 2 flops x %.0f MHz (of derived)"
@@ -503,7 +520,7 @@ def main():
                          "tile": {k: tile[k] for k in ("threads", "pixels_per_thread", "blocks")}},
             "roofline_full_passes": full_roofline(tile, fma_achieved, fma_peak, sm_count, max_mhz, TRAFFIC_FULL,
                                                   n_full_launches, full_ms),
-            "gpu_launches": args.steps * len(kts[0]),
+            "gpu_launches": args.steps * launches_per_step(tile, n_sub, n_full_launches),
             "kernel_times_from": "CUDA events recorded inside the graph around each launch, last timed step",
             "clocks": clk}
 

@@ -283,9 +283,11 @@ cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs
 /* Launch shapes of the batch's two iteration kernels, as chosen by the
  * autotuner: for compressed iterations threads per block and pixels per
  * thread; for full iterations and the final pass threads per block of the
- * CUDA-core kernel, or 1 for the tensor-core kernel (256 threads, tiles of
- * 128 x 64 pixels, split-BF16 products accumulated in FP32); and the
- * persistent blocks of each per launch.  Any pointer may be NULL. */
+ * CUDA-core kernel, or a tensor-core kernel (tiles of 128 x 64 pixels,
+ * split-BF16 products accumulated in FP32): 1 = every warp in every stage
+ * (512 threads), 2 = warp-specialised and pipelined across tiles (8 epilogue
+ * warps and one control warp); and the persistent blocks of each per launch.
+ * Any pointer may be NULL. */
 cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *full_threads,
                                     int *blocks, int *full_blocks);
 

@@ -80,13 +80,17 @@ struct LaunchSlot {
 struct TileShape {
     int threads;        // compressed iterations: threads per block
     int ppt;            // compressed iterations: pixels per thread
-    int full_threads;   // full iterations and final pass: threads per block, or kFullTc
+    int full_threads;   // full iterations and final pass: threads per block, or a kFullTc* kernel
     int fp16 = 0;       // compressed iterations use the half-precision sincos
 };
 
-// full_threads value that selects the tensor-core kernel for full iterations
-// and the final pass (kernels_tc.cu: 256 threads, 128 x 64-pixel tiles)
+// full_threads values that select a tensor-core kernel for full iterations and
+// the final pass (kernels_tc.cu, 128 x 64-pixel tiles): every warp in every
+// stage (512 threads), or warp-specialised and pipelined across tiles (8
+// epilogue warps and one control warp, the tails in a kernel of their own)
 constexpr int kFullTc = 1;
+constexpr int kFullTcWs = 2;
+inline bool is_full_tc(int full_threads) { return full_threads == kFullTc || full_threads == kFullTcWs; }
 
 // The two iteration kernels: compressed-iteration tiles, separable full-pass tiles.
 enum LaunchKind : int { kLaunchSubset = 0, kLaunchFull = 1 };
@@ -104,9 +108,9 @@ cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_
 // Tensor-core full-pass kernel (kernels_tc.cu).
 int full_tc_tiles(int P);
 size_t full_tc_smem(int maxN);
-int full_tc_max_grid(int maxN, int sm_count);
-cudaError_t launch_full_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
-                           unsigned *queue, int grid, cudaStream_t s);
+int full_tc_max_grid(int variant, int maxN, int sm_count);
+cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
+                           int maxN, unsigned *queue, int grid, cudaStream_t s);
 void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs);
 cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count, cudaStream_t s);
 cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
@@ -116,6 +120,7 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
 bool shape_supported(TileShape shape);
 int shape_max_grid(TileShape shape, int kind, int maxN, int sm_count);
 int shape_full_tiles(int P, TileShape shape);
+TileShape full_fallback(TileShape shape, int maxN, int sm_count);
 cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const LaunchSlot *slots, int nslots,
                          int total_tiles, int maxN, unsigned *queue, int grid, cudaStream_t s);
 

@@ -183,27 +183,25 @@ __device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.
 
 // Eight complex values -> the four BF16 component rows (re hi, re lo, im hi,
 // im lo), one 16-byte store each, at byte offset `off` of four tiles `stride`
-// bytes apart.
+// bytes apart.  Pairs are converted together (round to nearest): hi = bf16(v),
+// lo = bf16(v - hi).
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 h)
+{
+    return (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
+}
+
 __device__ __forceinline__ void put8(unsigned char *base, uint32_t stride, uint32_t off, const float2 *v)
 {
     uint32_t w[4][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float re[2], im[2];
-        __nv_bfloat16 rh[2], rl[2], ih[2], il[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            re[e] = v[2 * q + e].x;
-            im[e] = v[2 * q + e].y;
-            rh[e] = __float2bfloat16_rn(re[e]);
-            rl[e] = __float2bfloat16_rn(re[e] - __bfloat162float(rh[e]));
-            ih[e] = __float2bfloat16_rn(im[e]);
-            il[e] = __float2bfloat16_rn(im[e] - __bfloat162float(ih[e]));
-        }
-        w[0][q] = (uint32_t)__bfloat16_as_ushort(rh[0]) | ((uint32_t)__bfloat16_as_ushort(rh[1]) << 16);
-        w[1][q] = (uint32_t)__bfloat16_as_ushort(rl[0]) | ((uint32_t)__bfloat16_as_ushort(rl[1]) << 16);
-        w[2][q] = (uint32_t)__bfloat16_as_ushort(ih[0]) | ((uint32_t)__bfloat16_as_ushort(ih[1]) << 16);
-        w[3][q] = (uint32_t)__bfloat16_as_ushort(il[0]) | ((uint32_t)__bfloat16_as_ushort(il[1]) << 16);
+        const float2 a = v[2 * q], b = v[2 * q + 1];
+        const __nv_bfloat162 rh = __floats2bfloat162_rn(a.x, b.x), ih = __floats2bfloat162_rn(a.y, b.y);
+        const float2 rf = __bfloat1622float2(rh), jf = __bfloat1622float2(ih);
+        w[0][q] = bf16x2_bits(rh);
+        w[1][q] = bf16x2_bits(__floats2bfloat162_rn(a.x - rf.x, b.x - rf.y));
+        w[2][q] = bf16x2_bits(ih);
+        w[3][q] = bf16x2_bits(__floats2bfloat162_rn(a.y - jf.x, b.y - jf.y));
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c)
@@ -376,7 +374,7 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
         const int row = 32 * q + lane;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
         const int gy = y0 + row, yq = gy - half;
-        const int64_t R2 = (int64_t)half * half;
+        const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
         for (int xc = 0; xc < kCols / kGroups; xc += 16) {
             const int xs = (kCols / kGroups) * h + xc;
             float sr[16], si[16];
@@ -391,7 +389,7 @@ __device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int 
                 for (int e = 0; e < 8; ++e) {
                     const int j = 8 * g + e;
                     const int gx = x0 + xs + j, xq = gx - half;
-                    const int64_t rho2 = (int64_t)xq * xq + (int64_t)yq * yq;
+                    const int rho2 = xq * xq + yq2;
                     const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2);
                     const float a = sr[j], b = si[j];
                     const float n2 = a * a + b * b;
@@ -597,6 +595,504 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
     }
 }
 
+
+// ------------------------------------------------ warp-specialised variant --
+// The same tile, pipelined across tiles by warp roles: one control warp (its
+// lane 0 issues every bulk copy and MMA) and W epilogue warps.  Tensor memory
+// holds two S buffers (columns 256..383 and 384..511; tile k uses buffer
+// k & 1) and Z (columns 0..255).  The control warp issues GEMM 1 of tile k
+// before GEMM 2 of tile k - 1, so the tensor pipe computes the next tile's
+// back-propagation while the epilogue warps turn S into u; the epilogue warps
+// run epilogue 1 and epilogue 2 of each tile in order.  The per-hologram
+// tails (Eqs. 4-6, or the metrics) run in a small kernel right after the
+// launch, so tiles neither fence nor count arrivals.
+// Hand-overs, all mbarriers:
+//   ready[2]          control -> epilogue: work item k in info slot k & 1
+//   full[r], empty[r] GEMM 1 operand ring: copies landed / MMAs done
+//   s_full[2]         GEMM 1 of the tile in that S buffer is done
+//   s_empty[2]        the epilogue has read that S buffer and info slot
+//   u_full            the epilogue has written u
+//   cs_full           GEMM 2's C block has landed
+//   z_full            GEMM 2 of a spot block is done (C block buffer free)
+//   z_empty           the epilogue has read Z
+//   drain             the control's last commit, before tensor memory is freed
+// u is free for the next tile once the epilogue has seen z_full of a tile's
+// last spot block, which it does before it writes the next u.  Every wait is
+// bounded; a timeout ends the loop of the side that saw it and sets the
+// status word, and the other side's waits then run out in turn.
+namespace ws {
+
+constexpr int kRing = 4;
+constexpr uint32_t kS0 = 256;       // S buffers at columns 256 and 384, Z at 0
+constexpr int kTmemColsWs = 512;
+
+enum Bar {
+    kReady0 = 0,
+    kFull0 = 2,
+    kEmpty0 = kFull0 + kRing,
+    kSFull0 = kEmpty0 + kRing,
+    kSEmpty0 = kSFull0 + 2,
+    kUFull = kSEmpty0 + 2,
+    kCsFull,
+    kZFull,
+    kZEmpty,
+    kDrain,
+    kBarsWs
+};
+
+struct Info {
+    int item, slot, empty, done;
+};
+
+template <int W>
+struct Cfg {
+    static constexpr int kEpi = 32 * W;               // epilogue threads
+    static constexpr int kThreads = kEpi + 32;        // and the control warp
+    static constexpr int kGroups = W / 4;             // epilogue warps per TMEM lane quadrant
+    static constexpr int kColsPer = kCols / kGroups;  // epilogue 1: columns per thread
+    static constexpr int kRowsPer = kRows / kGroups;  // epilogue 2: rows per thread
+    static_assert(W % 4 == 0 && kColsPer % 16 == 0 && kRowsPer % 16 == 0, "epilogue split");
+};
+
+// Dynamic shared memory: the partial sums of epilogue 2, the GEMM 1 ring,
+// GEMM 2's C block and u (and 128 bytes to align the base; the no-swizzle
+// layouts and the bulk copies need 16).
+__host__ __device__ constexpr size_t smem_bytes_ws(int groups)
+{
+    return 128 + (size_t)(groups - 1) * kSpotBlock * sizeof(float2) + (size_t)kRing * kStage + 4 * (size_t)kCs +
+           4 * (size_t)kU;
+}
+
+struct SmemWs {
+    float2 *vh;
+    unsigned char *ring, *cs, *u;
+};
+
+__device__ __forceinline__ SmemWs carve_ws(unsigned char *raw, int groups)
+{
+    unsigned char *b = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~(uintptr_t)127);
+    SmemWs m;
+    m.vh = reinterpret_cast<float2 *>(b);
+    m.ring = b + (size_t)(groups - 1) * kSpotBlock * sizeof(float2);
+    m.cs = m.ring + kRing * kStage;
+    m.u = m.cs + 4 * kCs;
+    return m;
+}
+
+__device__ __forceinline__ void arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ bool wait_newest(uint32_t mbar, uint32_t given) { return wait(mbar, (given - 1u) & 1u); }
+
+// Named barrier 1 joins the epilogue warps only.
+template <int W>
+__device__ __forceinline__ void group_sync()
+{
+    asm volatile("bar.sync 1, %0;" :: "n"(Cfg<W>::kEpi) : "memory");
+}
+
+template <int W>
+__device__ __forceinline__ bool group_and(bool p)
+{
+    uint32_t r;
+    asm volatile("{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
+                 " selp.u32 %0, 1, 0, pout;\n}\n" : "=r"(r) : "r"((uint32_t)p), "n"(Cfg<W>::kEpi) : "memory");
+    return r != 0;
+}
+
+// Tile t of hologram H lies wholly outside the round pupil.
+__device__ __forceinline__ bool tile_outside(const HoloDev &H, int t)
+{
+    if (H.aperture == 0) return false;
+    const int P = H.P, half = P >> 1, col_tiles = (P + kCols - 1) / kCols;
+    const int y0 = (t / col_tiles) * kRows, x0 = (t % col_tiles) * kCols;
+    const int ylo = y0 - half, yhi = min(y0 + kRows, P) - 1 - half;
+    const int xlo = x0 - half, xhi = min(x0 + kCols, P) - 1 - half;
+    const int64_t dy = ylo > 0 ? ylo : (yhi < 0 ? yhi : 0);
+    const int64_t dx = xlo > 0 ? xlo : (xhi < 0 ? xhi : 0);
+    return dx * dx + dy * dy > (int64_t)half * half;
+}
+
+// Barrier i of the block's array, by shared-memory address.
+__device__ __forceinline__ uint32_t mbar_at(uint32_t base, int i) { return base + 8u * (uint32_t)i; }
+
+// One elected lane of a converged warp (the issuing lane of the control warp).
+__device__ __forceinline__ bool elect_one()
+{
+    uint32_t p;
+    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n selp.u32 %0, 1, 0, e;\n}\n" : "=r"(p));
+    return p != 0;
+}
+
+// Every lane's bounded wait for phase `parity`, voted across the warp.
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity)
+{
+    return __all_sync(0xffffffffu, wait(mbar, parity & 1u)) != 0;
+}
+
+// The control warp's pipeline state, the same in every lane and all scalars.
+// GEMM 1 chunks go round the ring in order, so chunk q (counted over the
+// block's tiles) is stage q % kRing's (q / kRing)-th use and both ring waits
+// take their parity from q; the other barriers count their phases.  The whole
+// warp runs the loop and waits; one elected lane issues the copies, MMAs,
+// commits and arrivals.
+struct Ctl {
+    uint32_t mb;      // barrier 0
+    uint32_t tmem;
+    uint32_t ring, cs, u;   // shared addresses of the ring, GEMM 2's C block and u
+    uint32_t ql;      // GEMM 1 chunks loaded
+    uint32_t qm;      // GEMM 1 chunks multiplied
+    uint32_t nz;      // GEMM 2 spot blocks issued
+    uint32_t ncs;     // GEMM 2 C blocks loaded
+    uint32_t nu;      // u hand-overs taken
+};
+
+// GEMM 1 of tile (rb, cb) of H into S buffer j: S = R' C^T over spot chunks,
+// operands streamed through the ring.  Chunk c's MMAs are queued before the
+// wait for chunk c - 1's, whose stage then takes chunk c - 1 + kRing.
+__device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, int j)
+{
+    const uint32_t id = idesc(kRows, kCols, 0), idn = idesc(kRows, kCols, 1);
+    const uint32_t s_re = C.tmem + kS0 + 2 * kCols * j, s_im = s_re + kCols;
+    const int nc = nchunks(H.N);
+    const uint64_t ring0 = desc(C.ring, 128, 256);
+    auto load = [&](int c) -> bool {
+        const uint32_t s = C.ql % kRing;
+        if (C.ql >= (uint32_t)kRing && !warp_wait(mbar_at(C.mb, kEmpty0 + s), C.ql / kRing - 1u)) return false;
+        if (elect_one()) {
+            const uint32_t stg = C.ring + s * kStage, full = mbar_at(C.mb, kFull0 + s);
+            expect_tx(full, kStage);
+            bulk_load(stg, H.rwtab + ((size_t)rb * nc + c) * (4 * kA1), 4 * kA1, full);
+            bulk_load(stg + 4 * kA1, H.ctab + ((size_t)cb * nc + c) * (4 * kB1), 4 * kB1, full);
+        }
+        __syncwarp();
+        C.ql++;
+        return true;
+    };
+    bool ok = true;
+    for (int c = 0; c < min(kRing, nc) && ok; ++c) ok = load(c);
+    for (int c = 0; c < nc && ok; ++c) {
+        const uint32_t s = C.qm % kRing;
+        ok = warp_wait(mbar_at(C.mb, kFull0 + s), C.qm / kRing);
+        if (!ok) break;
+        uint64_t a[4], b[4];
+        for (int q = 0; q < 4; ++q) {
+            a[q] = ring0 + ((uint64_t)(s * kStage + q * kA1) >> 4);
+            b[q] = ring0 + ((uint64_t)(s * kStage + 4 * kA1 + q * kB1) >> 4);
+        }
+        if (elect_one()) {
+            complex_mma(s_re, s_im, a, b, id, idn, c > 0 ? 1u : 0u, 0);
+            commit(mbar_at(C.mb, kEmpty0 + s));
+        }
+        __syncwarp();
+        C.qm++;
+        if (c >= 1 && c - 1 + kRing < nc) ok = load(c - 1 + kRing);
+    }
+    if (!ok) return false;
+    if (elect_one()) commit(mbar_at(C.mb, kSFull0 + j));   // covers this GEMM 1 and every MMA before it
+    __syncwarp();
+    return true;
+}
+
+// GEMM 2 of column block cb of H: Z = conj(C)^T u, one block of 128 spots at a
+// time, into columns 0..255.
+__device__ __forceinline__ bool gemm2(Ctl &C, const HoloDev &H, int cb)
+{
+    const uint32_t id = idesc(kSpotBlock, kRows, 0), idn = idesc(kSpotBlock, kRows, 1);
+    const uint32_t z_re = C.tmem, z_im = C.tmem + kRows;
+    const uint64_t cs0 = desc(C.cs, 128, (kCols / 8) * 128);
+    const uint64_t u0 = desc(C.u, 128, (kCols / 8) * 128);
+    const int nsb = nspotblocks(H.N);
+    for (int sb = 0; sb < nsb; ++sb) {
+        // the previous GEMM 2 is done with the C block buffer
+        if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZFull), C.nz - 1u)) return false;
+        if (elect_one()) {
+            const uint32_t full = mbar_at(C.mb, kCsFull);
+            expect_tx(full, 4 * kCs);
+            const unsigned char *src = H.cstab + ((size_t)cb * nsb + sb) * (4 * kCs);
+            for (int q = 0; q < 4; ++q) bulk_load(C.cs + q * kCs, src + q * kCs, kCs, full);
+        }
+        __syncwarp();
+        C.ncs++;
+        if (sb == 0) {
+            if (!warp_wait(mbar_at(C.mb, kUFull), C.nu)) return false;
+            C.nu++;
+        }
+        // the epilogue has read the previous Z
+        if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZEmpty), C.nz - 1u)) return false;
+        if (!warp_wait(mbar_at(C.mb, kCsFull), C.ncs - 1u)) return false;
+        fence_after();
+        for (int ks = 0; ks < kCols / 16; ++ks) {
+            uint64_t a[4], b[4];
+            for (int q = 0; q < 4; ++q) {
+                a[q] = cs0 + ((uint64_t)(q * kCs + ks * 256) >> 4);
+                b[q] = u0 + ((uint64_t)(q * kU + ks * 256) >> 4);
+            }
+            if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, ks > 0 ? 1u : 0u, 1);
+        }
+        if (elect_one()) commit(mbar_at(C.mb, kZFull));
+        __syncwarp();
+        C.nz++;
+    }
+    return true;
+}
+
+// The control warp: takes work items, publishes them, and issues GEMM 1 of each
+// tile and then GEMM 2 of the one before.
+__device__ __noinline__ void control(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
+                                     int nslots, int total_tiles, unsigned *queue, const SmemWs &m,
+                                     volatile Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
+{
+    Ctl C;
+    C.mb = mb;
+    C.tmem = tmem;
+    C.ring = saddr(m.ring);
+    C.cs = saddr(m.cs);
+    C.u = saddr(m.u);
+    C.ql = C.qm = C.nz = C.ncs = C.nu = 0u;
+    const bool lane0 = (threadIdx.x & 31) == 0;
+    const HoloDev *pend = nullptr;       // the tile whose GEMM 2 comes next
+    int pend_cb = 0;
+    bool ok = true;
+    for (uint32_t k = 0;; ++k) {
+        const int j = k & 1;
+        // S buffer j and info slot j are free once the epilogue has read tile k - 2's
+        if (k >= 2 && ok) ok = warp_wait(mbar_at(mb, kSEmpty0 + j), (k >> 1) - 1u);
+        int item = total_tiles;
+        if (ok && lane0) item = (int)atomicAdd(queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        const bool fin = item >= total_tiles;
+        const HoloDev *Hp = nullptr;
+        bool empty = true;
+        int rb = 0, cb = 0;
+        if (fin) {
+            if (lane0) info[j].done = 1;
+        } else {
+            int lo = 0, hi = nslots - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (slots[mid].tile_begin <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            Hp = &holos[slots[lo].holo];
+            const int t = item - slots[lo].tile_begin;
+            const int col_tiles = (Hp->P + kCols - 1) / kCols;
+            rb = t / col_tiles;
+            cb = t % col_tiles;
+            empty = tile_outside(*Hp, t);
+            if (lane0) {
+                info[j].item = item;
+                info[j].slot = lo;
+                info[j].empty = empty ? 1 : 0;
+                info[j].done = 0;
+            }
+        }
+        __syncwarp();
+        if (lane0) arrive(mbar_at(mb, kReady0 + j));
+        if (!empty && ok) {
+            fence_after();
+            ok = gemm1(C, *Hp, rb, cb, j);
+        }
+        if (pend && ok) ok = gemm2(C, *pend, pend_cb);
+        pend = empty ? nullptr : Hp;
+        pend_cb = cb;
+        if (fin || !ok) break;
+    }
+    // every MMA done before tensor memory is freed, every copy landed before
+    // shared memory is
+    if (elect_one()) commit(mbar_at(mb, kDrain));
+    __syncwarp();
+    bool drained = warp_wait(mbar_at(mb, kDrain), 0u);
+    for (uint32_t s = 0; s < (uint32_t)kRing; ++s) {
+        const uint32_t loads = (C.ql + kRing - 1u - s) / kRing;   // chunks q < ql with q % kRing == s
+        if (loads) drained &= warp_wait(mbar_at(mb, kFull0 + s), loads - 1u);
+    }
+    if (C.ncs) drained &= warp_wait(mbar_at(mb, kCsFull), C.ncs - 1u);
+    if ((!ok || !drained) && lane0) atomicOr(status, 1u);
+}
+
+// The epilogue warps: per tile, u = A S / |S| (with Phi and the gray level in
+// the final pass), then the tile's partial V_n = sum_y conj(R_n(y)) Z(n, y)
+// per spot block.
+template <int W>
+__device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
+                                         const SmemWs &m, const volatile Info *info, uint32_t mb,
+                                         uint32_t tmem, unsigned *status)
+{
+    using G = Cfg<W>;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, h = warp >> 2;
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    const uint32_t z_re = tmem, z_im = tmem + kRows;
+    uint32_t n_ready[2] = {0u, 0u}, n_s[2] = {0u, 0u}, n_z = 0u;
+    bool ok = true;
+    for (uint32_t k = 0;; ++k) {
+        const int j = k & 1;
+        n_ready[j]++;
+        ok = group_and<W>(wait_newest(mbar_at(mb, kReady0 + j), n_ready[j]));
+        if (!ok) break;
+        if (info[j].done) break;
+        const int item = info[j].item, slot = info[j].slot, empty = info[j].empty;
+        const LaunchSlot sl = slots[slot];
+        const HoloDev H = holos[sl.holo];   // by value: global stores below cannot alias it
+        const int t = item - sl.tile_begin;
+        const int P = H.P, N = H.N, half = P >> 1, pass = sl.pass;
+        const int col_tiles = (P + kCols - 1) / kCols;
+        const int y0 = (t / col_tiles) * kRows, x0 = (t % col_tiles) * kCols;
+        if (empty) {
+            // wholly outside the round pupil: zero partials; in the final pass
+            // phase 0 (gray lut[0]) over its grid pixels
+            __syncwarp();
+            if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
+            for (int n = tid; n < N; n += G::kEpi) {
+                if (pass == kPassFinal) H.part64[(size_t)t * N + n] = make_double2(0.0, 0.0);
+                else H.part[(size_t)t * N + n] = make_float2(0.f, 0.f);
+            }
+            if (pass == kPassFinal) {
+                const int rows = min(kRows, P - y0), cols = min(kCols, P - x0);
+                const uint8_t g0 = H.slm ? __ldg(H.lut) : 0;
+                for (int f = tid; f < rows * cols; f += G::kEpi) {
+                    const int r = y0 + f / cols, c = x0 + f % cols;
+                    if (H.phase_out) H.phase_out[(size_t)r * P + c] = 0.f;
+                    if (H.slm) H.slm[(size_t)r * H.slm_pitch + c] = g0;
+                }
+            }
+            continue;
+        }
+
+        // ---- epilogue 1: S -> u (GEMM 2's B operand), Phi and gray out.  S is
+        // released with u: the control warp reuses this S buffer only after
+        // u_full in any case.
+        n_s[j]++;
+        ok = group_and<W>(wait_newest(mbar_at(mb, kSFull0 + j), n_s[j]));
+        if (!ok) break;
+        fence_after();
+        {
+            const uint32_t s_re = tmem + kS0 + 2 * kCols * j, s_im = s_re + kCols;
+            const int row = 32 * q + lane, gy = y0 + row, yq = gy - half;
+            const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
+#pragma unroll 1
+            for (int xc = 0; xc < G::kColsPer; xc += 16) {
+                const int xs = G::kColsPer * h + xc;
+                float sr[16], si[16], o[16];
+                ld16(s_re + lanes + xs, sr);
+                ld16(s_im + lanes + xs, si);
+                ld_wait();
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    float2 u[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int jj = 8 * g + e;
+                        const int gx = x0 + xs + jj, xq = gx - half;
+                        const int rho2 = xq * xq + yq2;
+                        const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2);
+                        const float a = sr[jj], b = si[jj];
+                        const float n2 = a * a + b * b;
+                        if (pass == kPassFinal) {
+                            float ph = atan2f(b, a);
+                            ph = ph < 0.f ? ph + kTwoPiF : ph;
+                            o[jj] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
+                        }
+                        if (!valid) u[e] = make_float2(0.f, 0.f);
+                        else if (n2 > 0.f) {
+                            const float rs = rsqrtf(n2) * pupil_amp(H, (float)rho2);
+                            u[e] = make_float2(a * rs, b * rs);
+                        } else u[e] = make_float2(pupil_amp(H, (float)rho2), 0.f);
+                    }
+                    put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+                }
+                if (pass == kPassFinal && gy < P) {
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        const int col = x0 + xs + 4 * g;
+                        if (col >= P) break;
+                        if (H.phase_out) {
+                            float *dst = H.phase_out + (size_t)gy * P + col;
+                            if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                                *reinterpret_cast<float4 *>(dst) =
+                                    make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
+                            } else {
+                                for (int e = 0; e < 4; ++e)
+                                    if (col + e < P) dst[e] = o[4 * g + e];
+                            }
+                        }
+                        if (H.slm) write_gray4(H, gy, col, o + 4 * g);
+                    }
+                }
+            }
+        }
+        fence_before();
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            arrive(mbar_at(mb, kSEmpty0 + j));
+            arrive(mbar_at(mb, kUFull));
+        }
+
+        // ---- epilogue 2 per spot block: V_n = sum_y conj(R_n(y)) Z(n, y)
+        for (int sb = 0; sb * kSpotBlock < N; ++sb) {
+            n_z++;
+            ok = group_and<W>(wait_newest(mbar_at(mb, kZFull), n_z));
+            if (!ok) break;
+            fence_after();
+            const int nl = 32 * q + lane, n = sb * kSpotBlock + nl;
+            int4 cf = make_int4(0, 0, 0, 0);
+            if (n < N) cf = H.coef[n];
+            float vr = 0.f, vi = 0.f;
+#pragma unroll 1
+            for (int y16 = 0; y16 < G::kRowsPer; y16 += 16) {
+                const int ys = G::kRowsPer * h + y16;
+                float zr[16], zi[16];
+                ld16(z_re + lanes + ys, zr);
+                ld16(z_im + lanes + ys, zi);
+                float4 r4[8];
+                if (n < N) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float2 a = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e - half, kFixRound, 1.f);
+                        const float2 b = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e + 1 - half, kFixRound, 1.f);
+                        r4[e] = make_float4(a.x, a.y, b.x, b.y);
+                    }
+                }
+                ld_wait();
+                if (n < N) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        vr = fmaf(r4[e].x, zr[2 * e], fmaf(r4[e].y, zi[2 * e], vr));
+                        vi = fmaf(r4[e].x, zi[2 * e], fmaf(-r4[e].y, zr[2 * e], vi));
+                        vr = fmaf(r4[e].z, zr[2 * e + 1], fmaf(r4[e].w, zi[2 * e + 1], vr));
+                        vi = fmaf(r4[e].z, zi[2 * e + 1], fmaf(-r4[e].w, zr[2 * e + 1], vi));
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) arrive(mbar_at(mb, kZEmpty));
+            if (h > 0) m.vh[(h - 1) * kSpotBlock + nl] = make_float2(vr, vi);
+            group_sync<W>();
+            if (h == 0 && n < N) {
+#pragma unroll
+                for (int gg = 0; gg < G::kGroups - 1; ++gg) {
+                    const float2 o2 = m.vh[gg * kSpotBlock + nl];
+                    vr += o2.x;
+                    vi += o2.y;
+                }
+                const size_t off = (size_t)t * N + n;
+                if (pass == kPassFinal) H.part64[off] = make_double2((double)vr, (double)vi);
+                else H.part[off] = make_float2(vr, vi);
+            }
+            group_sync<W>();
+        }
+        if (!ok) break;
+    }
+    if (!ok && tid == 0) atomicOr(status, 1u);
+}
+
+}  // namespace ws
+
 }  // namespace tc
 
 __global__ void __launch_bounds__(tc::kThreads, 1)
@@ -667,12 +1163,106 @@ iter_full_tc_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restr
     }
 }
 
+template <int W>
+__global__ void __launch_bounds__(tc::ws::Cfg<W>::kThreads, 1)
+iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
+                      int total_tiles, unsigned *queue)
+{
+    using namespace tc::ws;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_mbar[kBarsWs];
+    __shared__ Info s_info[2];
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int b = 0; b < kBarsWs; ++b) {
+            // the epilogue's releases arrive once per warp
+            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1 || b == kUFull || b == kZEmpty) ? W : 1;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::saddr(&s_mbar[b])), "r"(cnt));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(tc::saddr(&s_tmem)), "r"(kTmemColsWs));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t mb = tc::saddr(&s_mbar[0]);
+    const SmemWs m = carve_ws(smem, W / 4);
+    unsigned *status = queue + 2;
+    if (warp == W) {
+        control(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
+    } else {
+        epilogue<W>(holos, slots, m, s_info, mb, s_tmem, status);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(s_tmem), "r"(kTmemColsWs));
+    if (tid == 0) {
+        unsigned done = atomicAdd(queue + 1, 1u);
+        if (done == gridDim.x - 1) {
+            queue[0] = 0u;
+            queue[1] = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// The per-hologram tails of a warp-specialised launch, one block per slot:
+// the weighted update (Eqs. 4-6) from the tile partials, or the metrics.
+__global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restrict__ holos,
+                                                         const LaunchSlot *__restrict__ slots)
+{
+    extern __shared__ float2 s_v[];
+    __shared__ double s_red[256 / 32];
+    const LaunchSlot sl = slots[blockIdx.x];
+    const HoloDev &H = holos[sl.holo];
+    if (sl.pass == kPassFinal) tail_metrics<256>(H, sl, s_red);
+    else tail_update<256>(H, sl, s_v, s_red);
+}
+
+template <int W>
+static int tcws_max_grid(int maxN, int sm_count)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, iter_full_tcws_kernel<W>) != cudaSuccess) return 0;
+    const size_t limit = 227 * 1024 - fa.sharedSizeBytes;
+    const size_t smem = tc::ws::smem_bytes_ws(W / 4);
+    if (smem > limit || (size_t)maxN * sizeof(float2) > 48 * 1024) return 0;
+    if (cudaFuncSetAttribute(iter_full_tcws_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) !=
+        cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iter_full_tcws_kernel<W>, tc::ws::Cfg<W>::kThreads,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return std::min(per_sm, 1) * sm_count;   // a block holds all 512 tensor-memory columns
+}
+
+template <int W>
+static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
+                               unsigned *queue, int grid, cudaStream_t s)
+{
+    (void)cudaGetLastError();
+    iter_full_tcws_kernel<W><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(W / 4), s>>>(
+        holos, slots, nslots, total_tiles, queue);
+    tcws_tails_kernel<<<nslots, 256, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
+    return cudaGetLastError();
+}
+
 int full_tc_tiles(int P) { return tc::tiles(P); }
 
 size_t full_tc_smem(int maxN) { return tc::smem_bytes(maxN); }
 
-int full_tc_max_grid(int maxN, int sm_count)
+int full_tc_max_grid(int variant, int maxN, int sm_count)
 {
+    if (variant == kFullTcWs) return tcws_max_grid<8>(maxN, sm_count);
+
     // the dynamic limit is the block's 227 KB less the kernel's static shared memory
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, iter_full_tc_kernel) != cudaSuccess) return 0;
@@ -717,9 +1307,11 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_full_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
-                           unsigned *queue, int grid, cudaStream_t s)
+cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
+                           int maxN, unsigned *queue, int grid, cudaStream_t s)
 {
+    if (variant == kFullTcWs) return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+
     (void)cudaGetLastError();
     iter_full_tc_kernel<<<grid, tc::kThreads, tc::smem_bytes(maxN), s>>>(holos, slots, nslots, total_tiles, maxN,
                                                                           queue);

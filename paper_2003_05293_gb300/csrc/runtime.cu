@@ -199,7 +199,7 @@ static int pass_count(const HoloSpec &h, int pass)
 
 bool shape_supported(TileShape shape)
 {
-    if (shape.full_threads != kFullTc) return tile_shape_supported(shape);
+    if (!is_full_tc(shape.full_threads)) return tile_shape_supported(shape);
     TileShape cuda_core = shape;
     cuda_core.full_threads = 256;
     return tile_shape_supported(cuda_core);
@@ -207,21 +207,33 @@ bool shape_supported(TileShape shape)
 
 int shape_max_grid(TileShape shape, int kind, int maxN, int sm_count)
 {
-    if (kind == kLaunchFull && shape.full_threads == kFullTc) return full_tc_max_grid(maxN, sm_count);
+    if (kind == kLaunchFull && is_full_tc(shape.full_threads))
+        return full_tc_max_grid(shape.full_threads, maxN, sm_count);
     return iter_fp32_max_grid(shape, kind, maxN, sm_count);
 }
 
 int shape_full_tiles(int P, TileShape shape)
 {
-    return shape.full_threads == kFullTc ? full_tc_tiles(P) : full_pass_tiles(P, shape.full_threads);
+    return is_full_tc(shape.full_threads) ? full_tc_tiles(P) : full_pass_tiles(P, shape.full_threads);
 }
 
 cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const LaunchSlot *slots, int nslots,
                          int total_tiles, int maxN, unsigned *queue, int grid, cudaStream_t s)
 {
-    if (kind == kLaunchFull && shape.full_threads == kFullTc)
-        return launch_full_tc(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+    if (kind == kLaunchFull && is_full_tc(shape.full_threads))
+        return launch_full_tc(shape.full_threads, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
     return launch_iter_fp32(shape, kind, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+}
+
+TileShape full_fallback(TileShape shape, int maxN, int sm_count)
+{
+    // a tensor-core kernel holds a spot table in shared memory; past its limit
+    // the next one down takes over: warp-specialised -> single-role -> CUDA cores
+    if (shape.full_threads == kFullTcWs &&
+        full_tc_max_grid(shape.full_threads, maxN, sm_count) <= 0)
+        shape.full_threads = kFullTc;
+    if (shape.full_threads == kFullTc && full_tc_max_grid(kFullTc, maxN, sm_count) <= 0) shape.full_threads = 256;
+    return shape;
 }
 
 int pass_tiles(int pass, int P, int Mp, TileShape shape)
@@ -252,12 +264,10 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     auto b = std::make_unique<Fp32Batch>();
     b->plan = p;
     b->specs = std::move(specs);
-    // the tensor-core full pass holds every spot table in shared memory; past
-    // its limit the batch keeps the CUDA-core kernel
-    if (shape.full_threads == kFullTc) {
+    {
         int mN = 1;
         for (auto &s : b->specs) mN = std::max(mN, s.N);
-        if (full_tc_max_grid(mN, p->sm_count) <= 0) shape.full_threads = 256;
+        shape = full_fallback(shape, mN, p->sm_count);
     }
     b->shape = shape;
     b->timing = timing;
@@ -293,7 +303,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         work += 256;                                                            // counter
         work += align256(sizeof(double) * (2 + s.N));                           // metrics
         if (host_out) work += align256(sizeof(float) * (size_t)M);              // own phase
-        if (shape.full_threads == kFullTc) {                                    // tensor-core factor tables
+        if (is_full_tc(shape.full_threads)) {                                    // tensor-core factor tables
             size_t rw, c, cs;
             full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
             work += align256(rw) + align256(c) + align256(cs);
@@ -356,7 +366,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             w += align256(sizeof(float) * (size_t)M);
         }
         H.phase_out = b->own_phase[h];
-        if (shape.full_threads == kFullTc) {
+        if (is_full_tc(shape.full_threads)) {
             size_t rw, c, cs;
             full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
             H.rwtab = reinterpret_cast<unsigned char *>(base + w);
@@ -516,7 +526,7 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s));
     if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, evflag));
     CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
-    const bool tc = b->shape.full_threads == kFullTc;
+    const bool tc = is_full_tc(b->shape.full_threads);
     if (tc) CSWGS_CUDA_TRY(launch_tc_const_tables(holos, count, b->plan->sm_count, s));
     const size_t steps = b->l_tiles.size() / 2;
     for (size_t L = 0; L < steps; ++L) {

@@ -146,7 +146,7 @@ size_t Server::footprint(const HoloSpec &s) const
     b += al256(sizeof(float2) * tiles * s.N) + al256(sizeof(double2) * tiles * s.N);
     b += 256 + al256(sizeof(double) * (2 + s.N));
     b += al256(sizeof(float) * M);   // phase map (the caller's device buffer is used when given)
-    if (shape_.full_threads == kFullTc) {
+    if (is_full_tc(shape_.full_threads)) {
         size_t rw, c, cs;
         full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
         b += al256(rw) + al256(c) + al256(cs);
@@ -198,7 +198,7 @@ void Server::place(Req &r)
     float *own = reinterpret_cast<float *>(b + o);
     o += al256(sizeof(float) * (size_t)s.P * s.P);
     H.phase_out = r.phase_dev ? r.phase_dev : own;
-    if (shape_.full_threads == kFullTc) {
+    if (is_full_tc(shape_.full_threads)) {
         size_t rw, c, cs;
         full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
         H.rwtab = reinterpret_cast<unsigned char *>(b + o);
@@ -230,10 +230,8 @@ cswgs_status Server::submit(const cswgs_request &q, uint64_t *ticket)
             std::lock_guard<std::mutex> pk(p_->mu);
             cudaSetDevice(p_->device);
             shape_ = tuned_shape(p_, v);
-            // the tensor-core full pass holds every spot table in shared memory:
-            // beyond its limit the serving loop keeps the CUDA-core kernel
-            if (shape_.full_threads == kFullTc && full_tc_max_grid(p_->desc.max_N, p_->sm_count) <= 0)
-                shape_.full_threads = 256;
+            // past a tensor-core kernel's spot limit the next one down takes over
+            shape_ = full_fallback(shape_, p_->desc.max_N, p_->sm_count);
         }
         shape_set_ = true;
         CSWGS_TRY(start());
@@ -419,7 +417,7 @@ void Server::loop()
             int pmax = 0;
             for (int i = 0; i < nprep; ++i) pmax = std::max(pmax, prep_h[i].N);
             chk(launch_prep_fp32(prep_d, nprep, pmax, stream_));
-            if (shape_.full_threads == kFullTc) chk(launch_tc_const_tables(prep_d, nprep, p_->sm_count, stream_));
+            if (is_full_tc(shape_.full_threads)) chk(launch_tc_const_tables(prep_d, nprep, p_->sm_count, stream_));
         }
         chk(cudaMemcpyAsync(sd, sbuf, sizeof(LaunchSlot) * nslots, cudaMemcpyHostToDevice, stream_));
         chk(cudaEventRecord(start_ev_[serial & 1], stream_));
@@ -429,7 +427,7 @@ void Server::loop()
             auto g = grid_for.find(key);
             if (g == grid_for.end())
                 g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
-            if (kind == kLaunchFull && shape_.full_threads == kFullTc)
+            if (kind == kLaunchFull && is_full_tc(shape_.full_threads))
                 chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, stream_));
             chk(shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
                              queue, std::min(g->second, group_tiles[kind]), stream_));

@@ -1,8 +1,10 @@
-"""The two kernels of the full iterations and the final pass, side by side:
-the tensor-core kernel (tcgen05, split-BF16 products accumulated in FP32) and
-the CUDA-core separable kernel.  Each plan is pinned to one of them through
-its tune cache; both are compared with the FP64 oracle (teacher-forced full
-iterations, the final pass, free-running solves) and with each other, over
+"""The kernels of the full iterations and the final pass, side by side: the
+tensor-core kernels (tcgen05, split-BF16 products accumulated in FP32; one
+with every warp in every stage, and the warp-specialised one, pipelined across
+tiles) and the CUDA-core separable kernel.
+Each plan is pinned to one of them through its tune cache; each tensor-core
+kernel is compared with the FP64 oracle (teacher-forced full iterations, the
+final pass, free-running solves) and with the CUDA-core kernel, over
 grid sides that do and do not divide into the 128 x 64 tiles, spot counts
 below and above the 128 of one spot block, the round pupil, and SLM frames."""
 import json
@@ -19,7 +21,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-TC, CUDA_CORE = 1, 256
+TC_KERNELS = {"tc": 1, "ws": 2}
+CUDA_CORE = 256
 
 
 def _plan(tmp_path, full):
@@ -34,13 +37,18 @@ def _plan(tmp_path, full):
 
 
 @pytest.fixture(scope="module")
-def plans(tmp_path_factory):
-    d = tmp_path_factory.mktemp("tc")
-    tc = _plan(d, TC)
-    cc = _plan(d, CUDA_CORE)
-    yield tc, cc
+def cuda_core_plan(tmp_path_factory):
+    plan = _plan(tmp_path_factory.mktemp("cc"), CUDA_CORE)
+    yield plan
+    plan.close()
+
+
+@pytest.fixture(scope="module", params=sorted(TC_KERNELS), ids=sorted(TC_KERNELS))
+def plans(request, tmp_path_factory, cuda_core_plan):
+    tc = _plan(tmp_path_factory.mktemp(request.param), TC_KERNELS[request.param])
+    tc.kernel = TC_KERNELS[request.param]
+    yield tc, cuda_core_plan
     tc.close()
-    cc.close()
 
 
 def _solve(plan, pb, **kw):
@@ -53,7 +61,7 @@ def _solve(plan, pb, **kw):
 def test_kernel_choice_is_reported(plans):
     tc, cc = plans
     pbs = [workloads.problem(256, 40, 5.0, 0.125, 4, seed=s) for s in range(4)]
-    for plan, want in ((tc, TC), (cc, CUDA_CORE)):
+    for plan, want in ((tc, tc.kernel), (cc, CUDA_CORE)):
         b = plan.batch(pbs)
         assert b.tile_shape()["full_threads"] == want
         b.close()
@@ -143,3 +151,30 @@ def test_batch_of_uneven_holograms(plans):
     for a, b, o1, o2 in zip(r1, r2, outs1, outs2):
         assert rms_wrapped(o1.cpu().numpy(), o2.cpu().numpy()) < 1e-4
         assert abs(a["e"] - b["e"]) < 1e-5 and abs(a["u"] - b["u"]) < 1e-4
+
+
+def test_many_tiles_per_block(plans):
+    # several hundred tiles over the persistent blocks, so that each block runs
+    # a long chain of tiles through its pipeline: spot counts over one, two and
+    # three spot blocks, round pupils (tiles that skip both products) beside
+    # square ones, and both kinds of pass
+    tc, cc = plans
+    pbs, kws = [], []
+    for i in range(24):
+        N = (40, 100, 200, 300)[i % 4]
+        pbs.append(workloads.problem(512, N, 5.0, 0.125, 4, seed=100 + i))
+        kws.append({"aperture": "round", "waist": 200.0} if i % 3 == 0 else {})
+    outs1 = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+    outs2 = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+    for pb, kw in zip(pbs, kws):
+        pb.extra = dict(kw, full_iterations=4)
+    r1 = tc.solve_batch(pbs, outs1)
+    r2 = cc.solve_batch(pbs, outs2)
+    for a, b, o1, o2 in zip(r1, r2, outs1, outs2):
+        assert rms_wrapped(o1.cpu().numpy(), o2.cpu().numpy()) < 1e-4
+        assert abs(a["e"] - b["e"]) < 1e-5 and abs(a["u"] - b["u"]) < 1e-4
+    # and one of them (two spot blocks, square pupil) against the oracle
+    pb = pbs[2]
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed, full_iterations=4)
+    assert rms_wrapped(outs1[2].cpu().numpy().astype(np.float64), ref["phase"]) < TOL_PHASE_RMS
+    assert abs(r1[2]["e"] - ref["e"]) < TOL_EU and abs(r1[2]["u"] - ref["u"]) < TOL_EU
