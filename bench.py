@@ -39,14 +39,15 @@ SFU_PER_CLK_PER_SM = 16       # sine/cosine results per clock per SM (CUDA arith
 FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
 # DRAM bytes (read + write) per launch of the iteration kernels at the default
 # workload, from one ncu capture of this bench
-# (profiles/iter_kernels_b64_P1152_N100_launches.md): compressed launches, and
-# full-pixel launches on the tensor cores (2 full iterations + the final pass,
-# averaged; the factor tables are read once per pass, the final pass writes the
-# phase maps).  Each is
-# reported only while the sources of its kernel hash to the value they had
-# when it was measured.
-TRAFFIC_MEASURED = {"sub": {"sha": "3bdfbecac4b139e7", "bytes": 332928},
-                    "full": {"sha": "f8a8ab6b82bc7cb0", "bytes": 317353557}}
+# (profiles/iter_kernels_b64_P1152_N100_launches.md), keyed by launch kind and
+# the kernel that ran it (the tile-shape marker): compressed launches on the
+# CUDA-core kernel (256 threads) or on the tensor cores, and full-pixel
+# launches on the warp-specialised tensor-core kernel (2 full iterations + the
+# final pass, averaged; the factor tables are read once per pass, the final
+# pass writes the phase maps).  Each is reported only while the sources of
+# its kernel hash to the value they had when it was measured.
+TRAFFIC_MEASURED = {("sub", 256): {"sha": "3bdfbecac4b139e7", "bytes": 332928},
+                    ("full", 2): {"sha": None, "bytes": 313525000}}
 KERNEL_SOURCES = {"sub": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu"),
                   "full": ("cswgs_device.cuh", "tile.cuh", "kernels_fp32.cu", "kernels_tc.cu")}
 
@@ -60,12 +61,13 @@ def kernel_sha(kind):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(args):
+def measured_traffic(args, tile):
     default = (args.batch, args.P, args.N, args.c, args.iters) == (64, 1152, 100, 0.125, 30)
     out = []
-    for kind in ("sub", "full"):
-        m = TRAFFIC_MEASURED[kind]
-        out.append(m["bytes"] if default and m["sha"] == kernel_sha(kind) else None)
+    for kind, marker in (("sub", tile["threads"]), ("full", tile["full_threads"])):
+        m = TRAFFIC_MEASURED.get((kind, marker))
+        src = "full" if kind == "sub" and marker == SUBSET_TC else kind
+        out.append(m["bytes"] if m and default and m["sha"] == kernel_sha(src) else None)
     return tuple(out)
 
 
@@ -74,14 +76,62 @@ TC_KERNELS = {1: ("iter_full_tc_kernel", 512),
               2: ("iter_full_tcws_kernel (warp-specialised: 8 epilogue warps + 1 control warp)", 288)}
 
 
+# threads marker of compressed iterations on the warp-specialised tensor-core
+# kernel (dense products, u zero outside the subset)
+SUBSET_TC = 1
+
+
+def tensor_peak():
+    """The measured sustained dense BF16 peak (TFLOP/s) and its basis."""
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp["bf16_tflops_sustained"]), "measured (cuBLAS BF16, sustained: timed inside the step)"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, "fallback (sustained)"
+
+
+def subset_roofline(tile, pairs_sub_launch, n_sub, sub_ms, full_ms, sm_count, max_mhz, probe, traffic, args):
+    """Roofline of the compressed-iteration launches.  On the CUDA-core kernel:
+    2 SFU results (sin, cos) per subset pixel-spot pair and pass against the
+    SFU peak.  On the tensor cores: algorithmic flops, 8 per subset pair and
+    pass (one complex multiply-add), against the dense BF16 peak; the kernel
+    runs every pixel (M / Mp times the subset) with 3 BF16 products per real
+    product."""
+    share = 100 * sub_ms / max(1e-9, sub_ms + full_ms)
+    if tile["threads"] == SUBSET_TC:
+        peak, basis = tensor_peak()
+        ach = 8.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e12 if n_sub else 0.0
+        Mp = math.floor(args.c * args.P * args.P)
+        return {"bound": "tensor", "pipe": "tcgen05 kind::f16 (BF16 in, FP32 accumulate)", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                "peak_basis": "%s dense BF16 peak" % basis,
+                "flops_basis": "8 flops (complex multiply-add) per subset pixel-spot pair and pass",
+                "kernel": "iter_full_tcws_kernel on compressed launches: every pixel through both products, u zero "
+                          "outside the subset (%d per step, %.1f%% of the step)" % (n_sub, share),
+                "issued_tensor_flops_per_algorithmic": 3.0 * args.P * args.P / max(1, Mp),
+                "ms_per_launch": sub_ms / max(1, n_sub),
+                "tile": {"threads": 288, "blocks": tile["blocks"], "pixels": "128 rows x 64 columns"}}
+    sfu_peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9           # G sin-or-cos/s
+    ach = 2.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e9 if n_sub else 0.0
+    return {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": ach, "peak": sfu_peak,
+            "unit": "G sincos/s", "frac": ach / sfu_peak, "traffic": traffic,
+            "kernel": "iter_kernel, compressed-iteration launches (%d per step, %.1f%% of the step)" % (n_sub, share),
+            "peak_basis": "%d SMs x %d/clk x %.0f MHz (of derived; probe measured %.0f G/s)"
+                          % (sm_count, SFU_PER_CLK_PER_SM, max_mhz, probe / 1e9),
+            "ms_per_launch": sub_ms / max(1, n_sub),
+            "tile": {k: tile[k] for k in ("threads", "pixels_per_thread", "blocks")}}
+
+
 def launches_per_step(tile, n_sub, n_full):
     """Kernel launches of one batch step: the per-spot preparation, the
     tensor-core constant tables (once per hologram), every compressed
     iteration, and per full pass the kernel plus, on the tensor cores, its R'
     table kernel and, for the warp-specialised kernel, its tails kernel."""
     ft = tile["full_threads"]
-    tc = ft in TC_KERNELS
-    return 1 + (1 if tc else 0) + n_sub + n_full * (1 + (1 if tc else 0) + (1 if ft == 2 else 0))
+    sub_tc = tile["threads"] == SUBSET_TC
+    tc = ft in TC_KERNELS or sub_tc
+    per_sub = 3 if sub_tc else 1      # tables + mask, the kernel, the tails
+    return 1 + (1 if tc else 0) + n_sub * per_sub + n_full * (1 + (1 if ft in TC_KERNELS else 0) + (1 if ft == 2 else 0))
 
 
 def full_roofline(tile, achieved_tflops, fma_peak, sm_count, max_mhz, traffic, n_launches, full_ms):
@@ -93,12 +143,7 @@ def full_roofline(tile, achieved_tflops, fma_peak, sm_count, max_mhz, traffic, n
             "flops_basis": "8 flops (complex multiply-add) per pixel-spot pair and pass",
             "ms_per_launch": full_ms / max(1, n_launches)}
     if tile["full_threads"] in TC_KERNELS:
-        peak, basis = 1700.0, "fallback (sustained)"
-        try:
-            mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-            peak, basis = float(mp["bf16_tflops_sustained"]), "measured (cuBLAS BF16, sustained: timed inside the step)"
-        except (OSError, ValueError, KeyError):
-            pass
+        peak, basis = tensor_peak()
         base.update({"bound": "tensor", "pipe": "tcgen05 kind::f16 (BF16 in, FP32 accumulate)", "peak": peak,
                      "frac": achieved_tflops / peak, "peak_basis": "%s dense BF16 peak" % basis,
                      "kernel": "%s, full-iteration and final launches (%d per step)"
@@ -491,12 +536,10 @@ def main():
     sub_ms = sum(sum(k[1:1 + n_sub]) for k in kts) / len(kts)
     full_ms = sum(sum(k[1 + n_sub:]) for k in kts) / len(kts)
     n_full_launches = len(kts[0]) - 1 - n_sub
-    sfu_peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9           # G sin-or-cos/s
     fma_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12       # TFLOP/s
-    sfu_achieved = 2.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e9 if n_sub else 0.0
     fma_achieved = 8.0 * pairs_full_launch * n_full_launches / (full_ms * 1e-3) / 1e12
     probe, probe_mhz = plan.sincos_peak()
-    TRAFFIC_SUB, TRAFFIC_FULL = measured_traffic(args)
+    TRAFFIC_SUB, TRAFFIC_FULL = measured_traffic(args, tile)
 
     eu = [(r["e"], r["u"]) for r in res]
     line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
@@ -510,14 +553,8 @@ def main():
                                    "of the batch): a hologram submitted with its batch is done after it"},
             "quality": {"e_mean": float(np.mean([a for a, _ in eu])), "u_mean": float(np.mean([b for _, b in eu])),
                         "u_min": float(np.min([b for _, b in eu])), "e_min": float(np.min([a for a, _ in eu]))},
-            "roofline": {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": sfu_achieved, "peak": sfu_peak,
-                         "unit": "G sincos/s", "frac": sfu_achieved / sfu_peak, "traffic": TRAFFIC_SUB,
-                         "kernel": "iter_kernel, compressed-iteration launches (%d per step, %.1f%% of the step)"
-                                   % (n_sub, 100 * sub_ms / (sub_ms + full_ms)),
-                         "peak_basis": "%d SMs x %d/clk x %.0f MHz (of derived; probe measured %.0f G/s)"
-                                       % (sm_count, SFU_PER_CLK_PER_SM, max_mhz, probe / 1e9),
-                         "ms_per_launch": sub_ms / max(1, n_sub),
-                         "tile": {k: tile[k] for k in ("threads", "pixels_per_thread", "blocks")}},
+            "roofline": subset_roofline(tile, pairs_sub_launch, n_sub, sub_ms, full_ms, sm_count, max_mhz, probe,
+                                        TRAFFIC_SUB, args),
             "roofline_full_passes": full_roofline(tile, fma_achieved, fma_peak, sm_count, max_mhz, TRAFFIC_FULL,
                                                   n_full_launches, full_ms),
             "gpu_launches": args.steps * launches_per_step(tile, n_sub, n_full_launches),

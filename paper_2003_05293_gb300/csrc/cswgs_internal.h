@@ -64,6 +64,11 @@ struct HoloDev {
     unsigned char *rwtab;   // R' = w a e^{i theta} R blocks, remade before every full pass
     unsigned char *ctab;    // C blocks (GEMM 1 operand), made once
     unsigned char *cstab;   // C blocks for GEMM 2, made once
+    // subset mask of compressed passes on the tensor cores (nullptr: not used):
+    // P rows of mask_words words, bit c % 32 of word c / 32 for pixel column c
+    uint32_t *mask;
+    int mask_words;
+    int pad3;
 };
 
 // One hologram's share of one persistent launch.
@@ -78,7 +83,7 @@ struct LaunchSlot {
 
 // Tile shapes of the two FP32 iteration kernels.
 struct TileShape {
-    int threads;        // compressed iterations: threads per block
+    int threads;        // compressed iterations: threads per block, or kSubsetTc
     int ppt;            // compressed iterations: pixels per thread
     int full_threads;   // full iterations and final pass: threads per block, or a kFullTc* kernel
     int fp16 = 0;       // compressed iterations use the half-precision sincos
@@ -92,8 +97,23 @@ constexpr int kFullTc = 1;
 constexpr int kFullTcWs = 2;
 inline bool is_full_tc(int full_threads) { return full_threads == kFullTc || full_threads == kFullTcWs; }
 
+// threads value that runs the compressed iterations on the warp-specialised
+// tensor-core kernel: every pixel through both products, u zero outside the
+// subset S_j (a bit mask made before each launch), so the sums are those of
+// Eqs. 1 and 3 over S_j
+constexpr int kSubsetTc = 1;
+
 // The two iteration kernels: compressed-iteration tiles, separable full-pass tiles.
 enum LaunchKind : int { kLaunchSubset = 0, kLaunchFull = 1 };
+
+// Whether a batch needs the tensor-core factor tables, and whether a launch of
+// a kind runs on a tensor-core kernel.
+inline bool uses_tc(TileShape s) { return is_full_tc(s.full_threads) || s.threads == kSubsetTc; }
+inline bool launch_uses_tc(TileShape s, int kind)
+{
+    return kind == kLaunchSubset ? s.threads == kSubsetTc : is_full_tc(s.full_threads);
+}
+inline int mask_words_of(int P) { return (P + 31) / 32; }
 
 // Kernel launchers (kernels_fp32.cu).
 cudaError_t launch_prep_fp32(const HoloDev *holos, int count, int maxN, cudaStream_t s);
@@ -111,6 +131,8 @@ size_t full_tc_smem(int maxN);
 int full_tc_max_grid(int variant, int maxN, int sm_count);
 cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
                            int maxN, unsigned *queue, int grid, cudaStream_t s);
+cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
+                             unsigned *queue, int grid, cudaStream_t s);
 void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs);
 cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count, cudaStream_t s);
 cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,

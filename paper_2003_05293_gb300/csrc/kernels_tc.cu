@@ -565,13 +565,24 @@ __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__rest
 }
 
 // R' = w a e^{i theta} R (GEMM 1's A: 128 rows x 16 spots per block) of the
-// hologram of each full-pass slot, from its current spot state.
+// hologram of each slot, from its current spot state; for a compressed pass
+// also the subset mask: bit c of word r * mask_words + c / 32 is set when pixel
+// r P + c belongs to S_j (each of the Mp draws of Section 3 sets its pixel's
+// bit; the mask was cleared after its last use).
 __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restrict__ holos,
                                                         const LaunchSlot *__restrict__ slots)
 {
     const LaunchSlot sl = slots[blockIdx.y];
     const HoloDev H = holos[sl.holo];
-    if (!H.rwtab || sl.pass == kPassSubset) return;
+    if (!H.rwtab) return;
+    if (sl.pass == kPassSubset && H.mask) {
+        const SubsetDraw d = subset_draw(H, sl.j);
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H.Mp; k += gridDim.x * blockDim.x) {
+            const uint32_t m = subset_pixel(H, d, (uint32_t)k);
+            const uint32_t r = m / (uint32_t)H.P, c = m - r * (uint32_t)H.P;
+            atomicOr(H.mask + (size_t)r * H.mask_words + (c >> 5), 1u << (c & 31));
+        }
+    }
     const int P = H.P, N = H.N, half = P >> 1, nc = nchunks(N);
     const int items = ((P + kRows - 1) / kRows) * nc * 256;      // (block, 128 rows x 2 groups)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items; i += gridDim.x * blockDim.x) {
@@ -640,8 +651,13 @@ enum Bar {
     kBarsWs
 };
 
+// A published work item: the tile, and copies of its launch slot and its
+// hologram's descriptor (staged by the control warp so that the epilogue
+// warps read them from shared memory).
 struct Info {
-    int item, slot, empty, done;
+    int item, empty, done, pad;
+    LaunchSlot sl;
+    HoloDev H;
 };
 
 template <int W>
@@ -652,6 +668,7 @@ struct Cfg {
     static constexpr int kColsPer = kCols / kGroups;  // epilogue 1: columns per thread
     static constexpr int kRowsPer = kRows / kGroups;  // epilogue 2: rows per thread
     static_assert(W % 4 == 0 && kColsPer % 16 == 0 && kRowsPer % 16 == 0, "epilogue split");
+    static_assert(kColsPer <= 32, "a thread's columns lie in one mask word");
 };
 
 // Dynamic shared memory: the partial sums of epilogue 2, the GEMM 1 ring,
@@ -843,7 +860,7 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const HoloDev &H, int cb)
 // tile and then GEMM 2 of the one before.
 __device__ __noinline__ void control(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
                                      int nslots, int total_tiles, unsigned *queue, const SmemWs &m,
-                                     volatile Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
+                                     Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
 {
     Ctl C;
     C.mb = mb;
@@ -884,10 +901,13 @@ __device__ __noinline__ void control(const HoloDev *__restrict__ holos, const La
             empty = tile_outside(*Hp, t);
             if (lane0) {
                 info[j].item = item;
-                info[j].slot = lo;
                 info[j].empty = empty ? 1 : 0;
                 info[j].done = 0;
+                info[j].sl = slots[lo];
             }
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(Hp);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&info[j].H);
+            for (int w = threadIdx.x & 31; w < (int)(sizeof(HoloDev) / 4); w += 32) dst[w] = __ldg(src + w);
         }
         __syncwarp();
         if (lane0) arrive(mbar_at(mb, kReady0 + j));
@@ -918,7 +938,7 @@ __device__ __noinline__ void control(const HoloDev *__restrict__ holos, const La
 // per spot block.
 template <int W>
 __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
-                                         const SmemWs &m, const volatile Info *info, uint32_t mb,
+                                         const SmemWs &m, const Info *info, uint32_t mb,
                                          uint32_t tmem, unsigned *status)
 {
     using G = Cfg<W>;
@@ -926,17 +946,18 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
     const int q = warp & 3, h = warp >> 2;
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
     const uint32_t z_re = tmem, z_im = tmem + kRows;
-    uint32_t n_ready[2] = {0u, 0u}, n_s[2] = {0u, 0u}, n_z = 0u;
+    // phases seen: ready[j] once per tile of slot j (tile k is its (k >> 1)-th),
+    // s_full[j] once per tile with products (low half: j = 0, high half: j = 1)
+    uint32_t n_s = 0u, n_z = 0u;
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
-        n_ready[j]++;
-        ok = group_and<W>(wait_newest(mbar_at(mb, kReady0 + j), n_ready[j]));
+        ok = group_and<W>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
         if (!ok) break;
         if (info[j].done) break;
-        const int item = info[j].item, slot = info[j].slot, empty = info[j].empty;
-        const LaunchSlot sl = slots[slot];
-        const HoloDev H = holos[sl.holo];   // by value: global stores below cannot alias it
+        const int item = info[j].item, empty = info[j].empty;
+        const LaunchSlot sl = info[j].sl;
+        const HoloDev H = info[j].H;   // by value: global stores below cannot alias it
         const int t = item - sl.tile_begin;
         const int P = H.P, N = H.N, half = P >> 1, pass = sl.pass;
         const int col_tiles = (P + kCols - 1) / kCols;
@@ -964,9 +985,16 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
 
         // ---- epilogue 1: S -> u (GEMM 2's B operand), Phi and gray out.  S is
         // released with u: the control warp reuses this S buffer only after
-        // u_full in any case.
-        n_s[j]++;
-        ok = group_and<W>(wait_newest(mbar_at(mb, kSFull0 + j), n_s[j]));
+        // u_full in any case.  A compressed pass reads the subset mask bits of
+        // the thread's columns first (a multiple of 16 columns from a multiple
+        // of 16: within one word per 32), before the wait for S.
+        uint32_t mword = 0xFFFFFFFFu;
+        if (pass == kPassSubset) {
+            const int gy = y0 + 32 * q + lane, c0 = x0 + G::kColsPer * h;
+            mword = (gy < P && c0 < P) ? __ldg(H.mask + (size_t)gy * H.mask_words + (c0 >> 5)) >> (c0 & 31) : 0u;
+        }
+        n_s += 1u << (16 * j);
+        ok = group_and<W>(wait_newest(mbar_at(mb, kSFull0 + j), (n_s >> (16 * j)) & 0xFFFFu));
         if (!ok) break;
         fence_after();
         {
@@ -976,6 +1004,8 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
 #pragma unroll 1
             for (int xc = 0; xc < G::kColsPer; xc += 16) {
                 const int xs = G::kColsPer * h + xc;
+                // compressed pass: only the pixels of S_j carry u (the rest add nothing to Eq. 3's sum)
+                const uint32_t bits = (mword >> xc) & 0xFFFFu;
                 float sr[16], si[16], o[16];
                 ld16(s_re + lanes + xs, sr);
                 ld16(s_im + lanes + xs, si);
@@ -988,7 +1018,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                         const int jj = 8 * g + e;
                         const int gx = x0 + xs + jj, xq = gx - half;
                         const int rho2 = xq * xq + yq2;
-                        const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2);
+                        const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2) && ((bits >> jj) & 1u);
                         const float a = sr[jj], b = si[jj];
                         const float n2 = a * a + b * b;
                         if (pass == kPassFinal) {
@@ -1213,8 +1243,10 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     }
 }
 
-// The per-hologram tails of a warp-specialised launch, one block per slot:
-// the weighted update (Eqs. 4-6) from the tile partials, or the metrics.
+// The per-hologram tails of a warp-specialised launch, one block per slot
+// (blockIdx.y == 0): the weighted update (Eqs. 4-6) from the tile partials, or
+// the metrics.  The other blocks of a compressed slot clear its subset mask
+// for the next draw.
 __global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restrict__ holos,
                                                          const LaunchSlot *__restrict__ slots)
 {
@@ -1222,6 +1254,15 @@ __global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restri
     __shared__ double s_red[256 / 32];
     const LaunchSlot sl = slots[blockIdx.x];
     const HoloDev &H = holos[sl.holo];
+    if (blockIdx.y > 0) {
+        if (sl.pass == kPassSubset && H.mask) {
+            const size_t words = (size_t)H.P * H.mask_words;
+            for (size_t i = (size_t)(blockIdx.y - 1) * blockDim.x + threadIdx.x; i < words;
+                 i += (size_t)(gridDim.y - 1) * blockDim.x)
+                H.mask[i] = 0u;
+        }
+        return;
+    }
     if (sl.pass == kPassFinal) tail_metrics<256>(H, sl, s_red);
     else tail_update<256>(H, sl, s_v, s_red);
 }
@@ -1246,12 +1287,14 @@ static int tcws_max_grid(int maxN, int sm_count)
 
 template <int W>
 static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
-                               unsigned *queue, int grid, cudaStream_t s)
+                               unsigned *queue, int grid, bool subset, cudaStream_t s)
 {
     (void)cudaGetLastError();
     iter_full_tcws_kernel<W><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(W / 4), s>>>(
         holos, slots, nslots, total_tiles, queue);
-    tcws_tails_kernel<<<nslots, 256, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
+    // one tail block per slot, plus (compressed launches) blocks that clear the masks
+    const dim3 tails((unsigned)nslots, 1u + (subset ? 8u : 0u));
+    tcws_tails_kernel<<<tails, 256, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
     return cudaGetLastError();
 }
 
@@ -1302,15 +1345,22 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
 {
     if (nslots <= 0) return cudaSuccess;
     (void)cudaGetLastError();
-    dim3 grid((unsigned)std::max(1, 2 * sm_count / std::max(1, nslots)), (unsigned)nslots);
+    // a wide grid: the subset masks' scattered bit sets are latency-bound
+    dim3 grid((unsigned)std::max(1, 16 * sm_count / std::max(1, nslots)), (unsigned)nslots);
     tc::rw_tables_kernel<<<grid, 256, 0, s>>>(holos, slots);
     return cudaGetLastError();
+}
+
+cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
+                             unsigned *queue, int grid, cudaStream_t s)
+{
+    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, true, s);
 }
 
 cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
                            int maxN, unsigned *queue, int grid, cudaStream_t s)
 {
-    if (variant == kFullTcWs) return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+    if (variant == kFullTcWs) return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, false, s);
 
     (void)cudaGetLastError();
     iter_full_tc_kernel<<<grid, tc::kThreads, tc::smem_bytes(maxN), s>>>(holos, slots, nslots, total_tiles, maxN,

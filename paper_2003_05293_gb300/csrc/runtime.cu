@@ -199,9 +199,14 @@ static int pass_count(const HoloSpec &h, int pass)
 
 bool shape_supported(TileShape shape)
 {
-    if (!is_full_tc(shape.full_threads)) return tile_shape_supported(shape);
+    // the CUDA-core kernels the shape names, with stand-ins for the tensor-core ones
     TileShape cuda_core = shape;
-    cuda_core.full_threads = 256;
+    if (shape.threads == kSubsetTc) {
+        if (shape.fp16) return false;   // the half-precision sincos belongs to the CUDA-core kernel
+        cuda_core.threads = 256;
+        cuda_core.ppt = 4;
+    }
+    if (is_full_tc(shape.full_threads)) cuda_core.full_threads = 256;
     return tile_shape_supported(cuda_core);
 }
 
@@ -209,6 +214,7 @@ int shape_max_grid(TileShape shape, int kind, int maxN, int sm_count)
 {
     if (kind == kLaunchFull && is_full_tc(shape.full_threads))
         return full_tc_max_grid(shape.full_threads, maxN, sm_count);
+    if (kind == kLaunchSubset && shape.threads == kSubsetTc) return full_tc_max_grid(kFullTcWs, maxN, sm_count);
     return iter_fp32_max_grid(shape, kind, maxN, sm_count);
 }
 
@@ -222,6 +228,8 @@ cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const 
 {
     if (kind == kLaunchFull && is_full_tc(shape.full_threads))
         return launch_full_tc(shape.full_threads, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+    if (kind == kLaunchSubset && shape.threads == kSubsetTc)
+        return launch_subset_tc(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
     return launch_iter_fp32(shape, kind, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
 }
 
@@ -233,13 +241,19 @@ TileShape full_fallback(TileShape shape, int maxN, int sm_count)
         full_tc_max_grid(shape.full_threads, maxN, sm_count) <= 0)
         shape.full_threads = kFullTc;
     if (shape.full_threads == kFullTc && full_tc_max_grid(kFullTc, maxN, sm_count) <= 0) shape.full_threads = 256;
+    if (shape.threads == kSubsetTc && full_tc_max_grid(kFullTcWs, maxN, sm_count) <= 0) {
+        shape.threads = 256;
+        shape.ppt = 4;
+    }
     return shape;
 }
 
 int pass_tiles(int pass, int P, int Mp, TileShape shape)
 {
+    if (pass != kPassSubset) return shape_full_tiles(P, shape);
+    if (shape.threads == kSubsetTc) return full_tc_tiles(P);
     const int tp = shape.threads * shape.ppt;
-    return pass == kPassSubset ? (Mp + tp - 1) / tp : shape_full_tiles(P, shape);
+    return (Mp + tp - 1) / tp;
 }
 
 int max_pass_tiles(const HoloSpec &h, TileShape shape)
@@ -303,13 +317,22 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         work += 256;                                                            // counter
         work += align256(sizeof(double) * (2 + s.N));                           // metrics
         if (host_out) work += align256(sizeof(float) * (size_t)M);              // own phase
-        if (is_full_tc(shape.full_threads)) {                                    // tensor-core factor tables
+        if (uses_tc(shape)) {                                                    // tensor-core factor tables
             size_t rw, c, cs;
             full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
             work += align256(rw) + align256(c) + align256(cs);
         }
         b->maxN = std::max(b->maxN, s.N);
     }
+    // subset masks of compressed passes on the tensor cores, one block for all
+    std::vector<size_t> m_off(count, 0);
+    b->mask_begin = work;
+    if (shape.threads == kSubsetTc)
+        for (int h = 0; h < count; ++h) {
+            m_off[h] = work;
+            work += align256(sizeof(uint32_t) * (size_t)b->specs[h].P * mask_words_of(b->specs[h].P));
+        }
+    b->mask_bytes = work - b->mask_begin;
     CSWGS_TRY(b->mem.ensure(work));
     CSWGS_CUDA_TRY(cudaMallocHost(&b->staging, std::max<size_t>(in, 256)));
 
@@ -366,7 +389,11 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             w += align256(sizeof(float) * (size_t)M);
         }
         H.phase_out = b->own_phase[h];
-        if (is_full_tc(shape.full_threads)) {
+        if (shape.threads == kSubsetTc) {
+            H.mask = reinterpret_cast<uint32_t *>(base + m_off[h]);
+            H.mask_words = mask_words_of(s.P);
+        }
+        if (uses_tc(shape)) {
             size_t rw, c, cs;
             full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
             H.rwtab = reinterpret_cast<unsigned char *>(base + w);
@@ -524,10 +551,10 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     unsigned *queue = b->queue_d.as<unsigned>();
     const int count = (int)b->holos.size();
     CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s));
+    if (b->mask_bytes) CSWGS_CUDA_TRY(cudaMemsetAsync(b->mem.as<char>() + b->mask_begin, 0, b->mask_bytes, s));
     if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, evflag));
     CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
-    const bool tc = is_full_tc(b->shape.full_threads);
-    if (tc) CSWGS_CUDA_TRY(launch_tc_const_tables(holos, count, b->plan->sm_count, s));
+    if (uses_tc(b->shape)) CSWGS_CUDA_TRY(launch_tc_const_tables(holos, count, b->plan->sm_count, s));
     const size_t steps = b->l_tiles.size() / 2;
     for (size_t L = 0; L < steps; ++L) {
         if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[L + 1], s, evflag));
@@ -536,7 +563,7 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
             const int tiles = b->l_tiles[i];
             if (tiles == 0) continue;
             const int grid = std::min(b->grid[kind], tiles);
-            if (tc && kind == kLaunchFull)
+            if (launch_uses_tc(b->shape, kind))
                 CSWGS_CUDA_TRY(launch_tc_rw_tables(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count, s));
             CSWGS_CUDA_TRY(shape_launch(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
                                             b->l_maxN[i], queue, grid, s));

@@ -122,6 +122,7 @@ struct Fp32Batch {
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaEvent_t> events;      // launch boundaries (timing)
     double pairs_total = 0.0, pairs_iter = 0.0;
+    size_t mask_begin = 0, mask_bytes = 0;   // subset masks (cleared at the start of every run)
     ~Fp32Batch();
 };
 

@@ -146,11 +146,12 @@ size_t Server::footprint(const HoloSpec &s) const
     b += al256(sizeof(float2) * tiles * s.N) + al256(sizeof(double2) * tiles * s.N);
     b += 256 + al256(sizeof(double) * (2 + s.N));
     b += al256(sizeof(float) * M);   // phase map (the caller's device buffer is used when given)
-    if (is_full_tc(shape_.full_threads)) {
+    if (uses_tc(shape_)) {
         size_t rw, c, cs;
         full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
         b += al256(rw) + al256(c) + al256(cs);
     }
+    if (shape_.threads == kSubsetTc) b += al256(sizeof(uint32_t) * (size_t)s.P * mask_words_of(s.P));
     return b;
 }
 
@@ -198,7 +199,7 @@ void Server::place(Req &r)
     float *own = reinterpret_cast<float *>(b + o);
     o += al256(sizeof(float) * (size_t)s.P * s.P);
     H.phase_out = r.phase_dev ? r.phase_dev : own;
-    if (is_full_tc(shape_.full_threads)) {
+    if (uses_tc(shape_)) {
         size_t rw, c, cs;
         full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
         H.rwtab = reinterpret_cast<unsigned char *>(b + o);
@@ -207,6 +208,14 @@ void Server::place(Req &r)
         o += al256(c);
         H.cstab = reinterpret_cast<unsigned char *>(b + o);
         o += al256(cs);
+    }
+    if (shape_.threads == kSubsetTc) {
+        // the subset mask starts clear (each compressed launch's tails clear it again)
+        H.mask = reinterpret_cast<uint32_t *>(b + o);
+        H.mask_words = mask_words_of(s.P);
+        const size_t bytes = sizeof(uint32_t) * (size_t)s.P * H.mask_words;
+        o += al256(bytes);
+        note(cudaMemsetAsync(H.mask, 0, bytes, stream_));
     }
 }
 
@@ -417,7 +426,7 @@ void Server::loop()
             int pmax = 0;
             for (int i = 0; i < nprep; ++i) pmax = std::max(pmax, prep_h[i].N);
             chk(launch_prep_fp32(prep_d, nprep, pmax, stream_));
-            if (is_full_tc(shape_.full_threads)) chk(launch_tc_const_tables(prep_d, nprep, p_->sm_count, stream_));
+            if (uses_tc(shape_)) chk(launch_tc_const_tables(prep_d, nprep, p_->sm_count, stream_));
         }
         chk(cudaMemcpyAsync(sd, sbuf, sizeof(LaunchSlot) * nslots, cudaMemcpyHostToDevice, stream_));
         chk(cudaEventRecord(start_ev_[serial & 1], stream_));
@@ -427,7 +436,7 @@ void Server::loop()
             auto g = grid_for.find(key);
             if (g == grid_for.end())
                 g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
-            if (kind == kLaunchFull && is_full_tc(shape_.full_threads))
+            if (launch_uses_tc(shape_, kind))
                 chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, stream_));
             chk(shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
                              queue, std::min(g->second, group_tiles[kind]), stream_));
