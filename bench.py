@@ -72,8 +72,7 @@ def measured_traffic(args, tile):
 
 
 # full_threads markers of the tensor-core kernels: kernel name, threads per block
-TC_KERNELS = {1: ("iter_full_tc_kernel", 512),
-              2: ("iter_full_tcws_kernel (warp-specialised: 8 epilogue warps + 1 control warp)", 288)}
+TC_KERNELS = {2: ("iter_full_tcws_kernel (warp-specialised: 8 epilogue warps + 1 control warp)", 288)}
 
 
 # threads marker of compressed iterations on the warp-specialised tensor-core

@@ -284,10 +284,11 @@ cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs
  * autotuner: for compressed iterations threads per block and pixels per
  * thread; for full iterations and the final pass threads per block of the
  * CUDA-core kernel, or a tensor-core kernel (tiles of 128 x 64 pixels,
- * split-BF16 products accumulated in FP32): 1 = every warp in every stage
- * (512 threads), 2 = warp-specialised and pipelined across tiles (8 epilogue
- * warps and one control warp); and the persistent blocks of each per launch.
- * Any pointer may be NULL. */
+ * split-BF16 products accumulated in FP32): 2 = the warp-specialised kernel,
+ * pipelined across tiles (8 epilogue warps and one control warp); compressed
+ * iterations report threads = 1 when they run on that kernel too (u zero
+ * outside the subset); and the persistent blocks of each per launch.  Any
+ * pointer may be NULL. */
 cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per_thread, int *full_threads,
                                     int *blocks, int *full_blocks);
 

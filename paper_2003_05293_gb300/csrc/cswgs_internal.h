@@ -85,17 +85,16 @@ struct LaunchSlot {
 struct TileShape {
     int threads;        // compressed iterations: threads per block, or kSubsetTc
     int ppt;            // compressed iterations: pixels per thread
-    int full_threads;   // full iterations and final pass: threads per block, or a kFullTc* kernel
+    int full_threads;   // full iterations and final pass: threads per block, or kFullTcWs
     int fp16 = 0;       // compressed iterations use the half-precision sincos
 };
 
-// full_threads values that select a tensor-core kernel for full iterations and
-// the final pass (kernels_tc.cu, 128 x 64-pixel tiles): every warp in every
-// stage (512 threads), or warp-specialised and pipelined across tiles (8
-// epilogue warps and one control warp, the tails in a kernel of their own)
-constexpr int kFullTc = 1;
+// full_threads value that selects the tensor-core kernel for full iterations
+// and the final pass (kernels_tc.cu, 128 x 64-pixel tiles; warp-specialised
+// and pipelined across tiles: 8 epilogue warps and one control warp, the
+// tails in a kernel of their own)
 constexpr int kFullTcWs = 2;
-inline bool is_full_tc(int full_threads) { return full_threads == kFullTc || full_threads == kFullTcWs; }
+inline bool is_full_tc(int full_threads) { return full_threads == kFullTcWs; }
 
 // threads value that runs the compressed iterations on the warp-specialised
 // tensor-core kernel: every pixel through both products, u zero outside the
@@ -127,7 +126,6 @@ cudaError_t launch_subset_kernel(int P, int64_t Mp, uint64_t seed, int j, int32_
                                  cudaStream_t s);
 // Tensor-core full-pass kernel (kernels_tc.cu).
 int full_tc_tiles(int P);
-size_t full_tc_smem(int maxN);
 int full_tc_max_grid(int variant, int maxN, int sm_count);
 cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
                            int maxN, unsigned *queue, int grid, cudaStream_t s);

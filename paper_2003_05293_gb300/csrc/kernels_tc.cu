@@ -1,4 +1,4 @@
-// Full iterations and the final pass on the tensor cores (tcgen05, sm_103a).
+// Both passes of an iteration on the tensor cores (tcgen05, sm_103a).
 //
 // The lens-and-prism phase (Eq. 2) is separable, e^{i phi_n(x', y')} =
 // C_n(x') R_n(y'), so over a tile of 128 rows x 64 columns both passes are
@@ -8,22 +8,27 @@
 //   forward projection (Eq. 3): Z(n, y) = sum_x conj(C_n(x)) u(y, x),
 //                               u = A e^{i Phi} = A S / |S|               [GEMM 2]
 //                               V_n  = sum_y conj(R_n(y)) Z(n, y)         [per spot, CUDA cores]
-// GEMM 1 is M = 128 rows x N = 64 columns x K = 16 spots per instruction,
-// GEMM 2 is M = 128 spots x N = 128 rows x K = 16 columns.  The complex
-// products become real ones (re re - im im, re im + im re), and every FP32
-// operand is split into two BF16 halves, v = hi + lo, with the product kept as
-// hi hi + hi lo + lo hi: 2^-16 relative per product, FP32-class phases.  The
-// accumulators (FP32) live in tensor memory.
+// A compressed iteration is the same computation with u zero outside the
+// subset S_j, so the sums run over S_j as Eqs. 1 and 3 ask.
+// Every FP32 operand is split into two BF16 halves, v = hi + lo, and each
+// real product is kept as hi hi + hi lo + lo hi: 2^-16 relative per product,
+// FP32-class phases; the accumulators (FP32) live in tensor memory.
+// GEMM 1 runs its complex product as two real ones stacked along N (M = 128
+// rows, N = 128, K = 16 spots):
+//   [S_re | S_im] = R'_re [C_re | C_im] + R'_im [-C_im | C_re],
+// with the two B operands as two 128-row windows of one 192-row tile
+// [-C_im | C_re | C_im]; GEMM 2 is M = 128 spots x N = 128 rows x K = 16
+// columns per instruction, real and imaginary parts apart.
 //
 // The operands are factor tables in global memory, laid out block by block
 // exactly as the MMAs read them from shared memory (no-swizzle K-major core
 // matrices, 8 rows x 16 bytes): C (per 64 columns and 16 spots) and C for
 // GEMM 2 (per 64 columns and 128 spots) depend on the spots only and are made
 // once per hologram; R' (per 128 rows and 16 spots) carries w and theta and is
-// remade before every full pass.  A tile streams its blocks into shared memory
+// remade before every launch.  A tile streams its blocks into shared memory
 // with bulk copies (cp.async.bulk, completion counted on an mbarrier) through
-// a four-stage ring, so the tile's threads only run the two epilogues.  One
-// thread issues copies and MMAs and commits them to mbarriers; every wait is
+// a ring; one control warp issues copies and MMAs and commits them to
+// mbarriers, eight epilogue warps run the CUDA-core stages.  Every wait is
 // bounded and a timeout is recorded in the launch's status word instead of
 // hanging.
 #include <cuda_bf16.h>
@@ -36,34 +41,18 @@ namespace cswgs {
 namespace tc {
 
 constexpr int kRows = 128;          // tile rows (GEMM 1 M, GEMM 2 N)
-constexpr int kCols = 64;           // tile columns (GEMM 1 N, GEMM 2 K)
-constexpr int kThreads = 512;
-constexpr int kGroups = kThreads / 128;   // warps per TMEM lane quadrant: the epilogues split columns among them
+constexpr int kCols = 64;           // tile columns (GEMM 2 K; GEMM 1 N is re and im of them)
 constexpr int kChunk = 16;          // spots per GEMM 1 instruction (K)
 constexpr int kSpotBlock = 128;     // spots per GEMM 2 instruction (M)
-constexpr int kTmemCols = 256;      // S (cols 0..127) and then Z (cols 0..255)
-constexpr int kStages = 4;          // GEMM 1 ring (the ring also takes GEMM 2's C blocks)
 constexpr uint32_t kWaitPolls = 1u << 20;
 
 // component tiles (bytes): GEMM 1 operands per stage, GEMM 2 operands
 constexpr uint32_t kA1 = kRows * kChunk * 2;        // R' component [128 rows][16 spots]
-constexpr uint32_t kB1 = kCols * kChunk * 2;        // C component [64 columns][16 spots]
-constexpr uint32_t kStage = 4 * kA1 + 4 * kB1;      // one GEMM 1 stage
+constexpr uint32_t kB1 = 3 * kCols * kChunk * 2;    // stacked C half [-C_im | C_re | C_im][16 spots]
+constexpr uint32_t kB1Win = kCols * kChunk * 2;     // byte offset of the [C_re | C_im] window
+constexpr uint32_t kStage = 4 * kA1 + 2 * kB1;      // one GEMM 1 stage: R' (4 components), C (hi, lo)
 constexpr uint32_t kU = kRows * kCols * 2;          // u component [128 rows][64 columns]
 constexpr uint32_t kCs = kSpotBlock * kCols * 2;    // C component [128 spots][64 columns]
-
-__host__ __device__ constexpr size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
-
-static_assert(kStages * kStage >= 4 * kCs, "the GEMM 1 ring holds GEMM 2's C block");
-
-// Dynamic shared memory: tail scratch, the GEMM 1 ring (which also receives
-// GEMM 2's C block), u, the half sums of the last epilogue (and 1 KB to align
-// the base).
-__host__ __device__ constexpr size_t smem_bytes(int maxN)
-{
-    return 1024 + align1k((size_t)maxN * sizeof(float2)) + (size_t)kStages * kStage + 4 * (size_t)kU +
-           (kGroups - 1) * kSpotBlock * sizeof(float2);
-}
 
 __host__ __device__ inline int tiles(int P) { return ((P + kRows - 1) / kRows) * ((P + kCols - 1) / kCols); }
 
@@ -72,30 +61,10 @@ __host__ __device__ inline int tiles(int P) { return ((P + kRows - 1) / kRows) *
 __host__ __device__ inline int nchunks(int N) { return (N + kChunk - 1) / kChunk; }
 __host__ __device__ inline int nspotblocks(int N) { return (N + kSpotBlock - 1) / kSpotBlock; }
 __host__ __device__ inline size_t rw_table_bytes(int P, int N) { return (size_t)((P + kRows - 1) / kRows) * nchunks(N) * 4 * kA1; }
-__host__ __device__ inline size_t c_table_bytes(int P, int N) { return (size_t)((P + kCols - 1) / kCols) * nchunks(N) * 4 * kB1; }
+__host__ __device__ inline size_t c_table_bytes(int P, int N) { return (size_t)((P + kCols - 1) / kCols) * nchunks(N) * 2 * kB1; }
 __host__ __device__ inline size_t cs_table_bytes(int P, int N)
 {
     return (size_t)((P + kCols - 1) / kCols) * nspotblocks(N) * 4 * kCs;
-}
-
-
-struct Smem {
-    float2 *v;                  // tail scratch (maxN)
-    unsigned char *ring;        // kStages x kStage: R' block (4 x kA1) then C block (4 x kB1)
-    unsigned char *u;           // 4 x kU: u re hi, re lo, im hi, im lo
-    float2 *vh;                 // (kGroups - 1) x kSpotBlock partial sums
-};
-
-__device__ __forceinline__ Smem carve(unsigned char *raw, int maxN)
-{
-    unsigned char *b = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
-    Smem m;
-    m.v = reinterpret_cast<float2 *>(b);
-    b += align1k((size_t)maxN * sizeof(float2));
-    m.ring = b;
-    m.u = b + kStages * kStage;
-    m.vh = reinterpret_cast<float2 *>(m.u + 4 * kU);
-    return m;
 }
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -208,18 +177,6 @@ __device__ __forceinline__ void put8(unsigned char *base, uint32_t stride, uint3
         *reinterpret_cast<uint4 *>(base + c * stride + off) = make_uint4(w[c][0], w[c][1], w[c][2], w[c][3]);
 }
 
-// Per-block state that lives across tiles: tensor memory, the barriers and how
-// many phases each has been given (a wait always targets the newest phase, so
-// its parity is (issued - 1) & 1).  Every thread keeps the same counts.
-enum Bar { kLd0 = 0, kMma0 = kStages, kLdCs = 2 * kStages, kMma2 = 2 * kStages + 1, kBars = 2 * kStages + 2 };
-
-struct State {
-    uint32_t tmem;
-    uint32_t mbar[kBars];
-    uint32_t issued[kBars];
-    bool failed;
-};
-
 // Issues the 12 MMAs of a complex product with split operands:
 //   D_re += Ar Br - Ai Bi,  D_im += Ar Bi + Ai Br   (conj_a = 0)
 //   D_re += Ar Br + Ai Bi,  D_im += Ar Bi - Ai Br   (conj_a = 1)
@@ -243,284 +200,44 @@ __device__ __forceinline__ void complex_mma(uint32_t d_re, uint32_t d_im, const 
     mma(d_im, a[3], b[0], id_ir, 1u);
 }
 
-// Thread 0's wait for the newest phase of barrier b; a timeout marks the block
-// failed in shared memory (read by everyone after the next __syncthreads).
-__device__ __forceinline__ void wait0(State &st, int b, int *s_fail)
-{
-    if (*s_fail) return;
-    if (!wait(st.mbar[b], (st.issued[b] - 1u) & 1u)) *s_fail = 1;
-}
-
-// Every thread's wait for the newest phase of barrier b, voted across the block.
-__device__ __forceinline__ void wait_all(State &st, int b, int *s_fail, unsigned *status)
-{
-    bool ok = true;
-    if (!st.failed) ok = wait(st.mbar[b], (st.issued[b] - 1u) & 1u);
-    ok = __syncthreads_and(ok && !*s_fail) != 0;
-    if (!ok) {
-        if (!st.failed && threadIdx.x == 0) atomicOr(status, 1u);
-        st.failed = true;
-    }
-}
-
-// GEMM 1's operand blocks of spot chunk c into ring stage s.
-__device__ __forceinline__ void load_chunk(const HoloDev &H, State &st, const Smem &m, int rb, int cb, int c, int s)
-{
-    const int nc = nchunks(H.N);
-    unsigned char *stg = m.ring + s * kStage;
-    const uint32_t bar = st.mbar[kLd0 + s];
-    expect_tx(bar, kStage);
-    bulk_load(saddr(stg), H.rwtab + ((size_t)rb * nc + c) * (4 * kA1), 4 * kA1, bar);
-    bulk_load(saddr(stg + 4 * kA1), H.ctab + ((size_t)cb * nc + c) * (4 * kB1), 4 * kB1, bar);
-}
-
-// One tile of a full iteration or the final pass.
-__device__ void process_tile(const HoloDev &H, const LaunchSlot &sl, int t, int maxN, unsigned char *raw,
-                             double *s_red, int *s_last, int *s_fail, State &st, unsigned *status)
-{
-    const Smem m = carve(raw, maxN);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int P = H.P, N = H.N, half = P >> 1;
-    const int pass = sl.pass;
-    const int col_tiles = (P + kCols - 1) / kCols;
-    const int rb = t / col_tiles, cb = t % col_tiles;
-    const int y0 = rb * kRows, x0 = cb * kCols;
-
-    // a tile wholly outside the round pupil: zero partials; in the final pass
-    // phase 0 (gray lut[0]) over its grid pixels.  After a timed-out wait the
-    // block does the same for its remaining tiles, so every hologram's tiles
-    // still arrive.
-    bool empty = st.failed;
-    if (H.aperture != 0) {
-        const int ylo = y0 - half, yhi = min(y0 + kRows, P) - 1 - half;
-        const int xlo = x0 - half, xhi = min(x0 + kCols, P) - 1 - half;
-        const int64_t dy = ylo > 0 ? ylo : (yhi < 0 ? yhi : 0);
-        const int64_t dx = xlo > 0 ? xlo : (xhi < 0 ? xhi : 0);
-        empty |= dx * dx + dy * dy > (int64_t)half * half;
-    }
-    if (empty) {
-        for (int n = tid; n < N; n += kThreads) {
-            if (pass == kPassFinal) H.part64[(size_t)t * N + n] = make_double2(0.0, 0.0);
-            else H.part[(size_t)t * N + n] = make_float2(0.f, 0.f);
-        }
-        if (pass == kPassFinal) {
-            const int rows = min(kRows, P - y0), cols = min(kCols, P - x0);
-            const uint8_t g0 = H.slm ? __ldg(H.lut) : 0;
-            for (int f = tid; f < rows * cols; f += kThreads) {
-                const int r = y0 + f / cols, c = x0 + f % cols;
-                if (H.phase_out) H.phase_out[(size_t)r * P + c] = 0.f;
-                if (H.slm) H.slm[(size_t)r * H.slm_pitch + c] = g0;
-            }
-        }
-        finish_tile<kThreads>(H, sl, m.v, s_red, s_last);
-        return;
-    }
-
-    const uint32_t id1 = idesc(kRows, kCols, 0), id1n = idesc(kRows, kCols, 1);
-    const uint32_t id2 = idesc(kSpotBlock, kRows, 0), id2n = idesc(kSpotBlock, kRows, 1);
-    const uint32_t t_re = st.tmem, t_im1 = st.tmem + kCols, t_im2 = st.tmem + kRows;
-
-    // ---- GEMM 1: S = R' C^T over spot chunks, operands streamed through the ring.
-    // Chunk c's MMAs are queued before thread 0 waits for chunk c - 1's, whose
-    // stage then takes chunk c - 1 + kStages: the tensor pipe always has work.
-    const int nchunk = nchunks(N);
-    const int pre = min(kStages, nchunk);
-    if (tid == 0 && !st.failed)
-        for (int c = 0; c < pre; ++c) load_chunk(H, st, m, rb, cb, c, c);
-    for (int c = 0; c < pre; ++c) st.issued[kLd0 + c]++;
-    // descriptors of stage 0; stage s and component q are a start-address offset
-    // ((s kStage + q kA1) / 16 for A, (s kStage + 4 kA1 + q kB1) / 16 for B)
-    const uint64_t a0 = desc(saddr(m.ring), 128, 256);
-    for (int c = 0; c < nchunk; ++c) {
-        const int s = c % kStages;
-        if (tid == 0 && !st.failed) {
-            wait0(st, kLd0 + s, s_fail);
-            if (!*s_fail) {
-                uint64_t a[4], b[4];
-                for (int q = 0; q < 4; ++q) {
-                    a[q] = a0 + ((uint64_t)(s * kStage + q * kA1) >> 4);
-                    b[q] = a0 + ((uint64_t)(s * kStage + 4 * kA1 + q * kB1) >> 4);
-                }
-                complex_mma(t_re, t_im1, a, b, id1, id1n, c > 0 ? 1u : 0u, 0);
-                commit(st.mbar[kMma0 + s]);
-            }
-        }
-        st.issued[kMma0 + s]++;
-        const int cr = c - 1;   // the chunk whose stage is refilled now
-        if (cr >= 0 && cr + kStages < nchunk) {
-            const int sr = cr % kStages;
-            if (tid == 0 && !st.failed) {
-                wait0(st, kMma0 + sr, s_fail);
-                if (!*s_fail) load_chunk(H, st, m, rb, cb, cr + kStages, sr);
-            }
-            st.issued[kLd0 + sr]++;
-        }
-    }
-    // the last chunk's commit covers every MMA before it
-    wait_all(st, kMma0 + (nchunk - 1) % kStages, s_fail, status);
-    fence_after();
-
-    // ---- epilogue 1: u = A S / |S| into GEMM 2's B operand; Phi and gray out --
-    // (meanwhile the first spot block's GEMM 2 operand streams into the ring)
-    if (tid == 0 && !st.failed) {
-        const uint32_t bar = st.mbar[kLdCs];
-        expect_tx(bar, 4 * kCs);
-        const unsigned char *src = H.cstab + ((size_t)cb * nspotblocks(N)) * (4 * kCs);
-        for (int q = 0; q < 4; ++q) bulk_load(saddr(m.ring + q * kCs), src + q * kCs, kCs, bar);
-    }
-    st.issued[kLdCs]++;
-    {
-        const int q = warp & 3, h = warp >> 2;
-        const int row = 32 * q + lane;
-        const uint32_t lanes = (uint32_t)(32 * q) << 16;
-        const int gy = y0 + row, yq = gy - half;
-        const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
-        for (int xc = 0; xc < kCols / kGroups; xc += 16) {
-            const int xs = (kCols / kGroups) * h + xc;
-            float sr[16], si[16];
-            ld16(t_re + lanes + xs, sr);
-            ld16(t_im1 + lanes + xs, si);
-            ld_wait();
-            float o[16];
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                float2 u[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int j = 8 * g + e;
-                    const int gx = x0 + xs + j, xq = gx - half;
-                    const int rho2 = xq * xq + yq2;
-                    const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2);
-                    const float a = sr[j], b = si[j];
-                    const float n2 = a * a + b * b;
-                    if (pass == kPassFinal) {
-                        float ph = atan2f(b, a);
-                        ph = ph < 0.f ? ph + kTwoPiF : ph;
-                        o[j] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
-                    }
-                    if (!valid) u[e] = make_float2(0.f, 0.f);
-                    else if (n2 > 0.f) {
-                        const float rs = rsqrtf(n2) * pupil_amp(H, (float)rho2);
-                        u[e] = make_float2(a * rs, b * rs);
-                    } else u[e] = make_float2(pupil_amp(H, (float)rho2), 0.f);
-                }
-                put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
-            }
-            if (pass == kPassFinal && gy < P) {
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const int col = x0 + xs + 4 * g;
-                    if (col >= P) break;
-                    if (H.phase_out) {
-                        float *dst = H.phase_out + (size_t)gy * P + col;
-                        if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-                            *reinterpret_cast<float4 *>(dst) = make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
-                        } else {
-                            for (int e = 0; e < 4; ++e)
-                                if (col + e < P) dst[e] = o[4 * g + e];
-                        }
-                    }
-                    if (H.slm) write_gray4(H, gy, col, o + 4 * g);
-                }
-            }
-        }
-    }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-
-    // ---- GEMM 2 per block of 128 spots, then V_n = sum_y conj(R_n(y)) Z(n, y) --
-    const int nsb = nspotblocks(N);
-    for (int sb = 0; sb < nsb; ++sb) {
-        if (sb > 0) {
-            // the previous block's MMAs are done (waited below): stream this block's C
-            if (tid == 0 && !st.failed) {
-                const uint32_t bar = st.mbar[kLdCs];
-                expect_tx(bar, 4 * kCs);
-                const unsigned char *src = H.cstab + ((size_t)cb * nsb + sb) * (4 * kCs);
-                for (int q = 0; q < 4; ++q) bulk_load(saddr(m.ring + q * kCs), src + q * kCs, kCs, bar);
-            }
-            st.issued[kLdCs]++;
-        }
-        if (tid == 0 && !st.failed) {
-            wait0(st, kLdCs, s_fail);
-            if (!*s_fail) {
-                const uint64_t ca = desc(saddr(m.ring), 128, (kCols / 8) * 128);
-                const uint64_t ua = desc(saddr(m.u), 128, (kCols / 8) * 128);
-                for (int ks = 0; ks < kCols / 16; ++ks) {
-                    uint64_t a[4], b[4];
-                    for (int q = 0; q < 4; ++q) {
-                        a[q] = ca + ((uint64_t)(q * kCs + ks * 256) >> 4);
-                        b[q] = ua + ((uint64_t)(q * kU + ks * 256) >> 4);
-                    }
-                    complex_mma(t_re, t_im2, a, b, id2, id2n, ks > 0 ? 1u : 0u, 1);
-                }
-                commit(st.mbar[kMma2]);
-            }
-        }
-        st.issued[kMma2]++;
-        wait_all(st, kMma2, s_fail, status);
-        fence_after();
-        {
-            const int q = warp & 3, h = warp >> 2;
-            const int nl = 32 * q + lane, n = sb * kSpotBlock + nl;
-            const uint32_t lanes = (uint32_t)(32 * q) << 16;
-            int4 cf = make_int4(0, 0, 0, 0);
-            if (n < N) cf = H.coef[n];
-            float vr = 0.f, vi = 0.f;
-            for (int y16 = 0; y16 < kRows / kGroups; y16 += 16) {
-                const int ys = (kRows / kGroups) * h + y16;
-                float zr[16], zi[16];
-                ld16(t_re + lanes + ys, zr);
-                ld16(t_im2 + lanes + ys, zi);
-                float4 r4[8];
-                if (n < N) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float2 a = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e - half, kFixRound, 1.f);
-                        const float2 b = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e + 1 - half, kFixRound, 1.f);
-                        r4[e] = make_float4(a.x, a.y, b.x, b.y);
-                    }
-                }
-                ld_wait();
-                if (n < N) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        vr = fmaf(r4[e].x, zr[2 * e], fmaf(r4[e].y, zi[2 * e], vr));
-                        vi = fmaf(r4[e].x, zi[2 * e], fmaf(-r4[e].y, zr[2 * e], vi));
-                        vr = fmaf(r4[e].z, zr[2 * e + 1], fmaf(r4[e].w, zi[2 * e + 1], vr));
-                        vi = fmaf(r4[e].z, zi[2 * e + 1], fmaf(-r4[e].w, zr[2 * e + 1], vi));
-                    }
-                }
-            }
-            if (h > 0) m.vh[(h - 1) * kSpotBlock + nl] = make_float2(vr, vi);
-            fence_before();
-            __syncthreads();
-            if (h == 0 && n < N) {
-#pragma unroll
-                for (int g = 0; g < kGroups - 1; ++g) {
-                    const float2 o2 = m.vh[g * kSpotBlock + nl];
-                    vr += o2.x;
-                    vi += o2.y;
-                }
-                const size_t off = (size_t)t * N + n;
-                if (pass == kPassFinal) H.part64[off] = make_double2((double)vr, (double)vi);
-                else H.part[off] = make_float2(vr, vi);
-            }
-        }
-        __syncthreads();
-        fence_after();
-    }
-    finish_tile<kThreads>(H, sl, m.v, s_red, s_last);
-}
-
 // ------------------------------------------------------------- factor tables --
 // Items of eight phasors; consecutive threads take consecutive rows of one
 // core matrix, so a warp's 16-byte stores fill whole 128-byte lines.
 
-// C (GEMM 1's B: 64 columns x 16 spots per block) and C for GEMM 2 (128 spots
-// x 64 columns per block) of hologram blockIdx.y, from its spot coefficients.
+// Eight values -> rows of the two BF16 halves (hi, lo) of a stacked C block:
+// hi at base, lo at base + kB1, row offsets re_off, im_off (C_im) and
+// neg_off (-C_im); each a 16-byte store.
+__device__ __forceinline__ void put8_stacked(unsigned char *base, uint32_t re_off, uint32_t im_off,
+                                             uint32_t neg_off, const float2 *v)
+{
+    uint32_t w[6][4];   // re hi, re lo, im hi, im lo, -im hi, -im lo
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 a = v[2 * q], b = v[2 * q + 1];
+        const __nv_bfloat162 rh = __floats2bfloat162_rn(a.x, b.x), ih = __floats2bfloat162_rn(a.y, b.y);
+        const float2 rf = __bfloat1622float2(rh), jf = __bfloat1622float2(ih);
+        const __nv_bfloat162 rl = __floats2bfloat162_rn(a.x - rf.x, b.x - rf.y);
+        const __nv_bfloat162 il = __floats2bfloat162_rn(a.y - jf.x, b.y - jf.y);
+        w[0][q] = bf16x2_bits(rh);
+        w[1][q] = bf16x2_bits(rl);
+        w[2][q] = bf16x2_bits(ih);
+        w[3][q] = bf16x2_bits(il);
+        w[4][q] = bf16x2_bits(__hneg2(ih));   // the split of -v is -(hi), -(lo): exact
+        w[5][q] = bf16x2_bits(__hneg2(il));
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned char *t = base + h * kB1;
+        *reinterpret_cast<uint4 *>(t + re_off) = make_uint4(w[h][0], w[h][1], w[h][2], w[h][3]);
+        *reinterpret_cast<uint4 *>(t + im_off) = make_uint4(w[2 + h][0], w[2 + h][1], w[2 + h][2], w[2 + h][3]);
+        *reinterpret_cast<uint4 *>(t + neg_off) = make_uint4(w[4 + h][0], w[4 + h][1], w[4 + h][2], w[4 + h][3]);
+    }
+}
+
+// C (GEMM 1's B: per block of 64 columns and 16 spots, each half a 192-row
+// tile [-C_im | C_re | C_im] with row = column within each third) and C for
+// GEMM 2 (128 spots x 64 columns per block) of hologram blockIdx.y, from its
+// spot coefficients.
 __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__restrict__ holos, int count)
 {
     const HoloDev H = holos[blockIdx.y];
@@ -545,7 +262,8 @@ __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__rest
                     v[e] = make_float2(0.f, 0.f);
                 }
             }
-            put8(H.ctab + (size_t)blk * (4 * kB1), kB1, core_off(col, 8 * g, kChunk), v);
+            put8_stacked(H.ctab + (size_t)blk * (2 * kB1), core_off(kCols + col, 8 * g, kChunk),
+                         core_off(2 * kCols + col, 8 * g, kChunk), core_off(col, 8 * g, kChunk), v);
         } else {
             const int k = i - items_c, blk = k >> 10, j = k & 1023;
             const int cb = blk / nsb, sb = blk % nsb;
@@ -633,7 +351,7 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 // status word, and the other side's waits then run out in turn.
 namespace ws {
 
-constexpr int kRing = 4;
+constexpr int kRing = 3;
 constexpr uint32_t kS0 = 256;       // S buffers at columns 256 and 384, Z at 0
 constexpr int kTmemColsWs = 512;
 
@@ -771,8 +489,8 @@ struct Ctl {
 // wait for chunk c - 1's, whose stage then takes chunk c - 1 + kRing.
 __device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, int j)
 {
-    const uint32_t id = idesc(kRows, kCols, 0), idn = idesc(kRows, kCols, 1);
-    const uint32_t s_re = C.tmem + kS0 + 2 * kCols * j, s_im = s_re + kCols;
+    const uint32_t id = idesc(kRows, 2 * kCols, 0);
+    const uint32_t s_acc = C.tmem + kS0 + 2 * kCols * j;   // [S_re | S_im]
     const int nc = nchunks(H.N);
     const uint64_t ring0 = desc(C.ring, 128, 256);
     auto load = [&](int c) -> bool {
@@ -782,7 +500,7 @@ __device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, 
             const uint32_t stg = C.ring + s * kStage, full = mbar_at(C.mb, kFull0 + s);
             expect_tx(full, kStage);
             bulk_load(stg, H.rwtab + ((size_t)rb * nc + c) * (4 * kA1), 4 * kA1, full);
-            bulk_load(stg + 4 * kA1, H.ctab + ((size_t)cb * nc + c) * (4 * kB1), 4 * kB1, full);
+            bulk_load(stg + 4 * kA1, H.ctab + ((size_t)cb * nc + c) * (2 * kB1), 2 * kB1, full);
         }
         __syncwarp();
         C.ql++;
@@ -794,13 +512,18 @@ __device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, 
         const uint32_t s = C.qm % kRing;
         ok = warp_wait(mbar_at(C.mb, kFull0 + s), C.qm / kRing);
         if (!ok) break;
-        uint64_t a[4], b[4];
-        for (int q = 0; q < 4; ++q) {
-            a[q] = ring0 + ((uint64_t)(s * kStage + q * kA1) >> 4);
-            b[q] = ring0 + ((uint64_t)(s * kStage + 4 * kA1 + q * kB1) >> 4);
-        }
+        // A: R' re hi, re lo, im hi, im lo; B: [C_re | C_im] and [-C_im | C_re] windows, hi and lo
+        const uint64_t st = ring0 + ((uint64_t)(s * kStage) >> 4);
+        const uint64_t arh = st, arl = st + (kA1 >> 4), aih = st + (2 * kA1 >> 4), ail = st + (3 * kA1 >> 4);
+        const uint64_t bh = st + (4 * kA1 >> 4), bl = bh + (kB1 >> 4);
+        const uint64_t b1h = bh + (kB1Win >> 4), b1l = bl + (kB1Win >> 4);
         if (elect_one()) {
-            complex_mma(s_re, s_im, a, b, id, idn, c > 0 ? 1u : 0u, 0);
+            mma(s_acc, arh, b1h, id, c > 0 ? 1u : 0u);
+            mma(s_acc, arh, b1l, id, 1u);
+            mma(s_acc, arl, b1h, id, 1u);
+            mma(s_acc, aih, bh, id, 1u);
+            mma(s_acc, aih, bl, id, 1u);
+            mma(s_acc, ail, bh, id, 1u);
             commit(mbar_at(C.mb, kEmpty0 + s));
         }
         __syncwarp();
@@ -1125,74 +848,6 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
 
 }  // namespace tc
 
-__global__ void __launch_bounds__(tc::kThreads, 1)
-iter_full_tc_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
-                    int total_tiles, int maxN, unsigned *queue)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ double s_red[tc::kThreads / 32];
-    __shared__ int s_last, s_item, s_slot, s_fail;
-    __shared__ __align__(8) uint64_t s_mbar[tc::kBars];
-    __shared__ uint32_t s_tmem;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int b = 0; b < tc::kBars; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc::saddr(&s_mbar[b])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
-    }
-    if ((tid >> 5) == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(tc::saddr(&s_tmem)), "r"(tc::kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    tc::State st;
-    st.tmem = s_tmem;
-    for (int b = 0; b < tc::kBars; ++b) {
-        st.mbar[b] = tc::saddr(&s_mbar[b]);
-        st.issued[b] = 0u;
-    }
-    st.failed = false;
-    unsigned *status = queue + 2;
-
-    for (;;) {
-        if (tid == 0) {
-            int item = (int)atomicAdd(queue, 1u);
-            s_item = item;
-            if (item < total_tiles) {
-                int lo = 0, hi = nslots - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (slots[mid].tile_begin <= item) lo = mid;
-                    else hi = mid - 1;
-                }
-                s_slot = lo;
-            }
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total_tiles) break;
-        const LaunchSlot sl = slots[s_slot];
-        const HoloDev H = holos[sl.holo];
-        tc::process_tile(H, sl, item - sl.tile_begin, maxN, smem, s_red, &s_last, &s_fail, st, status);
-    }
-    tc::fence_before();
-    __syncthreads();
-    if ((tid >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(st.tmem), "r"(tc::kTmemCols));
-    if (tid == 0) {
-        unsigned done = atomicAdd(queue + 1, 1u);
-        if (done == gridDim.x - 1) {
-            queue[0] = 0u;
-            queue[1] = 0u;
-            __threadfence();
-        }
-    }
-}
-
 template <int W>
 __global__ void __launch_bounds__(tc::ws::Cfg<W>::kThreads, 1)
 iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
@@ -1300,28 +955,9 @@ static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, in
 
 int full_tc_tiles(int P) { return tc::tiles(P); }
 
-size_t full_tc_smem(int maxN) { return tc::smem_bytes(maxN); }
-
 int full_tc_max_grid(int variant, int maxN, int sm_count)
 {
-    if (variant == kFullTcWs) return tcws_max_grid<8>(maxN, sm_count);
-
-    // the dynamic limit is the block's 227 KB less the kernel's static shared memory
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, iter_full_tc_kernel) != cudaSuccess) return 0;
-    const size_t limit = 227 * 1024 - fa.sharedSizeBytes;
-    const size_t smem = tc::smem_bytes(maxN);
-    if (smem > limit) return 0;
-    if (cudaFuncSetAttribute(iter_full_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) !=
-        cudaSuccess)
-        return 0;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iter_full_tc_kernel, tc::kThreads, smem) !=
-        cudaSuccess)
-        return 0;
-    // tensor memory: each block holds kTmemCols of the SM's 512 columns
-    per_sm = min(per_sm, 512 / tc::kTmemCols);
-    return per_sm * sm_count;
+    return variant == kFullTcWs ? tcws_max_grid<8>(maxN, sm_count) : 0;
 }
 
 void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs)
@@ -1360,12 +996,8 @@ cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int 
 cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
                            int maxN, unsigned *queue, int grid, cudaStream_t s)
 {
-    if (variant == kFullTcWs) return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, false, s);
-
-    (void)cudaGetLastError();
-    iter_full_tc_kernel<<<grid, tc::kThreads, tc::smem_bytes(maxN), s>>>(holos, slots, nslots, total_tiles, maxN,
-                                                                          queue);
-    return cudaGetLastError();
+    if (variant != kFullTcWs) return cudaErrorInvalidValue;
+    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, false, s);
 }
 
 }  // namespace cswgs

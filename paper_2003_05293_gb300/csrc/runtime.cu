@@ -235,12 +235,9 @@ cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const 
 
 TileShape full_fallback(TileShape shape, int maxN, int sm_count)
 {
-    // a tensor-core kernel holds a spot table in shared memory; past its limit
-    // the next one down takes over: warp-specialised -> single-role -> CUDA cores
-    if (shape.full_threads == kFullTcWs &&
-        full_tc_max_grid(shape.full_threads, maxN, sm_count) <= 0)
-        shape.full_threads = kFullTc;
-    if (shape.full_threads == kFullTc && full_tc_max_grid(kFullTc, maxN, sm_count) <= 0) shape.full_threads = 256;
+    // past the tensor-core kernel's spot limit the CUDA-core kernels take over
+    if (shape.full_threads == kFullTcWs && full_tc_max_grid(kFullTcWs, maxN, sm_count) <= 0)
+        shape.full_threads = 256;
     if (shape.threads == kSubsetTc && full_tc_max_grid(kFullTcWs, maxN, sm_count) <= 0) {
         shape.threads = 256;
         shape.ppt = 4;

@@ -63,7 +63,7 @@ std::string tune_key(const std::vector<HoloSpec> &specs, bool fp16)
 // own launches.
 static const int kSubCandidates[][2] = {{128, 2}, {128, 4}, {128, 8}, {256, 2}, {256, 4},
                                         {256, 8}, {512, 1}, {512, 2}, {512, 4}, {kSubsetTc, 1}};
-static const int kFullCandidates[] = {128, 256, 512, kFullTc, kFullTcWs};
+static const int kFullCandidates[] = {128, 256, 512, kFullTcWs};
 
 static std::vector<HoloSpec> synthetic(const TuneKey &k, double c)
 {

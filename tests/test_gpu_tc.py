@@ -1,7 +1,7 @@
 """The kernels of the full iterations and the final pass, side by side: the
-tensor-core kernels (tcgen05, split-BF16 products accumulated in FP32; one
-with every warp in every stage, and the warp-specialised one, pipelined across
-tiles) and the CUDA-core separable kernel.
+tensor-core kernel (tcgen05, split-BF16 products accumulated in FP32,
+warp-specialised and pipelined across tiles) and the CUDA-core separable
+kernel.
 Each plan is pinned to one of them through its tune cache; each tensor-core
 kernel is compared with the FP64 oracle (teacher-forced full iterations, the
 final pass, free-running solves) and with the CUDA-core kernel, over
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-TC_KERNELS = {"tc": 1, "ws": 2}
+TC_KERNELS = {"ws": 2}
 CUDA_CORE = 256
 
 
