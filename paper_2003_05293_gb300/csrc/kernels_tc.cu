@@ -27,8 +27,8 @@
 // once per hologram; R' (per 128 rows and 16 spots) carries w and theta and is
 // remade before every launch.  A tile streams its blocks into shared memory
 // with bulk copies (cp.async.bulk, completion counted on an mbarrier) through
-// a ring; one control warp issues copies and MMAs and commits them to
-// mbarriers, eight epilogue warps run the CUDA-core stages.  Every wait is
+// a ring; two issuing warps (GEMM 1, GEMM 2) issue the copies and MMAs and
+// commit them to mbarriers, eight epilogue warps run the CUDA-core stages.  Every wait is
 // bounded and a timeout is recorded in the launch's status word instead of
 // hanging.
 #include <cuda_bf16.h>
@@ -325,26 +325,28 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 }
 
 
-// ------------------------------------------------ warp-specialised variant --
-// The same tile, pipelined across tiles by warp roles: one control warp (its
-// lane 0 issues every bulk copy and MMA) and W epilogue warps.  Tensor memory
-// holds two S buffers (columns 256..383 and 384..511; tile k uses buffer
-// k & 1) and Z (columns 0..255).  The control warp issues GEMM 1 of tile k
-// before GEMM 2 of tile k - 1, so the tensor pipe computes the next tile's
-// back-propagation while the epilogue warps turn S into u; the epilogue warps
-// run epilogue 1 and epilogue 2 of each tile in order.  The per-hologram
-// tails (Eqs. 4-6, or the metrics) run in a small kernel right after the
-// launch, so tiles neither fence nor count arrivals.
+// ----------------------------------------------------------- warp roles --
+// Tiles are pipelined by warp roles: a GEMM 1 warp, a GEMM 2 warp (one
+// elected lane of each issues its bulk copies and MMAs) and W epilogue warps.
+// Tensor memory holds two S buffers (columns 256..383 and 384..511; tile k
+// uses buffer k & 1) and Z (columns 0..255).  The GEMM 1 warp runs ahead into
+// the next tile's back-propagation while the epilogue warps turn S into u; the
+// GEMM 2 warp streams the tile's C block in meanwhile and issues GEMM 2 as
+// soon as u is ready; the epilogue warps run epilogue 1 and epilogue 2 of each
+// tile in order.  The per-hologram tails (Eqs. 4-6, or the metrics) run in a
+// small kernel right after the launch, so tiles neither fence nor count
+// arrivals.
 // Hand-overs, all mbarriers:
-//   ready[2]          control -> epilogue: work item k in info slot k & 1
+//   ready[2]          GEMM 1 warp -> epilogue: work item k in info slot k & 1
 //   full[r], empty[r] GEMM 1 operand ring: copies landed / MMAs done
 //   s_full[2]         GEMM 1 of the tile in that S buffer is done
 //   s_empty[2]        the epilogue has read that S buffer and info slot
+//   g2_info           epilogue -> GEMM 2 warp: the tile's C blocks (or done)
 //   u_full            the epilogue has written u
 //   cs_full           GEMM 2's C block has landed
 //   z_full            GEMM 2 of a spot block is done (C block buffer free)
 //   z_empty           the epilogue has read Z
-//   drain             the control's last commit, before tensor memory is freed
+//   drain             both issuing warps' last commits, before tensor memory is freed
 // u is free for the next tile once the epilogue has seen z_full of a tile's
 // last spot block, which it does before it writes the next u.  Every wait is
 // bounded; a timeout ends the loop of the side that saw it and sets the
@@ -365,8 +367,17 @@ enum Bar {
     kCsFull,
     kZFull,
     kZEmpty,
-    kDrain,
+    kG2Info,    // the epilogue has published the next tile's GEMM 2 operands
+    kDrain,     // both issuing warps' last commits (2 arrivals)
     kBarsWs
+};
+
+// The GEMM 2 warp's work item, published by the epilogue warps when they take
+// up a tile with products (a single slot: the next one is written only after
+// that tile's GEMM 2 has been issued and waited for).
+struct G2Info {
+    const unsigned char *cstab;
+    int nsb, cb, done, pad;
 };
 
 // A published work item: the tile, and copies of its launch slot and its
@@ -381,7 +392,7 @@ struct Info {
 template <int W>
 struct Cfg {
     static constexpr int kEpi = 32 * W;               // epilogue threads
-    static constexpr int kThreads = kEpi + 32;        // and the control warp
+    static constexpr int kThreads = kEpi + 64;        // and the GEMM 1 and GEMM 2 warps
     static constexpr int kGroups = W / 4;             // epilogue warps per TMEM lane quadrant
     static constexpr int kColsPer = kCols / kGroups;  // epilogue 1: columns per thread
     static constexpr int kRowsPer = kRows / kGroups;  // epilogue 2: rows per thread
@@ -467,7 +478,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity)
     return __all_sync(0xffffffffu, wait(mbar, parity & 1u)) != 0;
 }
 
-// The control warp's pipeline state, the same in every lane and all scalars.
+// An issuing warp's pipeline state, the same in every lane and all scalars.
 // GEMM 1 chunks go round the ring in order, so chunk q (counted over the
 // block's tiles) is stage q % kRing's (q / kRing)-th use and both ring waits
 // take their parity from q; the other barriers count their phases.  The whole
@@ -536,22 +547,21 @@ __device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, 
     return true;
 }
 
-// GEMM 2 of column block cb of H: Z = conj(C)^T u, one block of 128 spots at a
-// time, into columns 0..255.
-__device__ __forceinline__ bool gemm2(Ctl &C, const HoloDev &H, int cb)
+// GEMM 2 of one tile: Z = conj(C)^T u, one block of 128 spots at a time, into
+// columns 0..255; each block's C streams in once the previous GEMM 2 is done
+// with the buffer (block 0 while u is still being written).
+__device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
 {
     const uint32_t id = idesc(kSpotBlock, kRows, 0), idn = idesc(kSpotBlock, kRows, 1);
     const uint32_t z_re = C.tmem, z_im = C.tmem + kRows;
     const uint64_t cs0 = desc(C.cs, 128, (kCols / 8) * 128);
     const uint64_t u0 = desc(C.u, 128, (kCols / 8) * 128);
-    const int nsb = nspotblocks(H.N);
-    for (int sb = 0; sb < nsb; ++sb) {
-        // the previous GEMM 2 is done with the C block buffer
+    for (int sb = 0; sb < g.nsb; ++sb) {
         if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZFull), C.nz - 1u)) return false;
         if (elect_one()) {
             const uint32_t full = mbar_at(C.mb, kCsFull);
             expect_tx(full, 4 * kCs);
-            const unsigned char *src = H.cstab + ((size_t)cb * nsb + sb) * (4 * kCs);
+            const unsigned char *src = g.cstab + ((size_t)g.cb * g.nsb + sb) * (4 * kCs);
             for (int q = 0; q < 4; ++q) bulk_load(C.cs + q * kCs, src + q * kCs, kCs, full);
         }
         __syncwarp();
@@ -579,11 +589,22 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const HoloDev &H, int cb)
     return true;
 }
 
-// The control warp: takes work items, publishes them, and issues GEMM 1 of each
-// tile and then GEMM 2 of the one before.
-__device__ __noinline__ void control(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
-                                     int nslots, int total_tiles, unsigned *queue, const SmemWs &m,
-                                     Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
+// Every MMA of this warp done before tensor memory is freed, and its copies
+// landed before shared memory is; true when all ended in time.
+__device__ __forceinline__ bool drain(const Ctl &C)
+{
+    if (elect_one()) commit(mbar_at(C.mb, kDrain));
+    __syncwarp();
+    bool drained = warp_wait(mbar_at(C.mb, kDrain), 0u);
+    for (uint32_t s = 0; s < (uint32_t)kRing; ++s) {
+        const uint32_t loads = (C.ql + kRing - 1u - s) / kRing;   // chunks q < ql with q % kRing == s
+        if (loads) drained &= warp_wait(mbar_at(C.mb, kFull0 + s), loads - 1u);
+    }
+    if (C.ncs) drained &= warp_wait(mbar_at(C.mb, kCsFull), C.ncs - 1u);
+    return drained;
+}
+
+__device__ __forceinline__ Ctl ctl_init(const SmemWs &m, uint32_t mb, uint32_t tmem)
 {
     Ctl C;
     C.mb = mb;
@@ -592,9 +613,35 @@ __device__ __noinline__ void control(const HoloDev *__restrict__ holos, const La
     C.cs = saddr(m.cs);
     C.u = saddr(m.u);
     C.ql = C.qm = C.nz = C.ncs = C.nu = 0u;
+    return C;
+}
+
+// The GEMM 2 warp: per tile with products, its operands as the epilogue
+// publishes them, then GEMM 2 once u is ready.
+__device__ __noinline__ void control_gemm2(const SmemWs &m, const G2Info *g2, uint32_t mb, uint32_t tmem,
+                                           unsigned *status)
+{
+    Ctl C = ctl_init(m, mb, tmem);
+    bool ok = true;
+    for (uint32_t n = 0;; ++n) {
+        ok = warp_wait(mbar_at(mb, kG2Info), n);
+        if (!ok) break;
+        const G2Info g = *g2;
+        if (g.done) break;
+        ok = gemm2(C, g);
+        if (!ok) break;
+    }
+    const bool drained = drain(C);
+    if ((!ok || !drained) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
+}
+
+// The GEMM 1 warp: takes work items, publishes them, and issues GEMM 1 of each.
+__device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
+                                           int nslots, int total_tiles, unsigned *queue, const SmemWs &m,
+                                           Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
+{
+    Ctl C = ctl_init(m, mb, tmem);
     const bool lane0 = (threadIdx.x & 31) == 0;
-    const HoloDev *pend = nullptr;       // the tile whose GEMM 2 comes next
-    int pend_cb = 0;
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
@@ -638,21 +685,9 @@ __device__ __noinline__ void control(const HoloDev *__restrict__ holos, const La
             fence_after();
             ok = gemm1(C, *Hp, rb, cb, j);
         }
-        if (pend && ok) ok = gemm2(C, *pend, pend_cb);
-        pend = empty ? nullptr : Hp;
-        pend_cb = cb;
         if (fin || !ok) break;
     }
-    // every MMA done before tensor memory is freed, every copy landed before
-    // shared memory is
-    if (elect_one()) commit(mbar_at(mb, kDrain));
-    __syncwarp();
-    bool drained = warp_wait(mbar_at(mb, kDrain), 0u);
-    for (uint32_t s = 0; s < (uint32_t)kRing; ++s) {
-        const uint32_t loads = (C.ql + kRing - 1u - s) / kRing;   // chunks q < ql with q % kRing == s
-        if (loads) drained &= warp_wait(mbar_at(mb, kFull0 + s), loads - 1u);
-    }
-    if (C.ncs) drained &= warp_wait(mbar_at(mb, kCsFull), C.ncs - 1u);
+    const bool drained = drain(C);
     if ((!ok || !drained) && lane0) atomicOr(status, 1u);
 }
 
@@ -661,7 +696,7 @@ __device__ __noinline__ void control(const HoloDev *__restrict__ holos, const La
 // per spot block.
 template <int W>
 __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
-                                         const SmemWs &m, const Info *info, uint32_t mb,
+                                         const SmemWs &m, const Info *info, G2Info *g2, uint32_t mb,
                                          uint32_t tmem, unsigned *status)
 {
     using G = Cfg<W>;
@@ -677,7 +712,13 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
         const int j = k & 1;
         ok = group_and<W>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
         if (!ok) break;
-        if (info[j].done) break;
+        if (info[j].done) {
+            if (tid == 0) {
+                g2->done = 1;
+                arrive(mbar_at(mb, kG2Info));
+            }
+            break;
+        }
         const int item = info[j].item, empty = info[j].empty;
         const LaunchSlot sl = info[j].sl;
         const HoloDev H = info[j].H;   // by value: global stores below cannot alias it
@@ -706,6 +747,15 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             continue;
         }
 
+        // the GEMM 2 warp's operands for this tile (it streams C in meanwhile)
+        if (tid == 0) {
+            g2->cstab = H.cstab;
+            g2->nsb = nspotblocks(N);
+            g2->cb = t % col_tiles;
+            g2->done = 0;
+            arrive(mbar_at(mb, kG2Info));
+        }
+
         // ---- epilogue 1: S -> u (GEMM 2's B operand), Phi and gray out.  S is
         // released with u: the control warp reuses this S buffer only after
         // u_full in any case.  A compressed pass reads the subset mask bits of
@@ -724,6 +774,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             const uint32_t s_re = tmem + kS0 + 2 * kCols * j, s_im = s_re + kCols;
             const int row = 32 * q + lane, gy = y0 + row, yq = gy - half;
             const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
+            const bool row_in = gy < P, square = H.aperture == 0, gauss = H.kA != 0.f;
 #pragma unroll 1
             for (int xc = 0; xc < G::kColsPer; xc += 16) {
                 const int xs = G::kColsPer * h + xc;
@@ -738,10 +789,12 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                     float2 u[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
+                        // branch-free: the lanes are rows, so a per-pixel branch
+                        // (subset membership, the pupil edge) would diverge
                         const int jj = 8 * g + e;
                         const int gx = x0 + xs + jj, xq = gx - half;
                         const int rho2 = xq * xq + yq2;
-                        const bool valid = gy < P && gx < P && (H.aperture == 0 || rho2 <= R2) && ((bits >> jj) & 1u);
+                        const bool valid = row_in & (gx < P) & (square | (rho2 <= R2)) & (((bits >> jj) & 1u) != 0u);
                         const float a = sr[jj], b = si[jj];
                         const float n2 = a * a + b * b;
                         if (pass == kPassFinal) {
@@ -749,11 +802,11 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                             ph = ph < 0.f ? ph + kTwoPiF : ph;
                             o[jj] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
                         }
-                        if (!valid) u[e] = make_float2(0.f, 0.f);
-                        else if (n2 > 0.f) {
-                            const float rs = rsqrtf(n2) * pupil_amp(H, (float)rho2);
-                            u[e] = make_float2(a * rs, b * rs);
-                        } else u[e] = make_float2(pupil_amp(H, (float)rho2), 0.f);
+                        const float amp = gauss ? exp2f(-H.kA * (float)rho2) : 1.f;   // Eq. 3's A
+                        const bool lit = n2 > 0.f;
+                        const float rs = rsqrtf(n2) * amp;
+                        const float ur = lit ? a * rs : amp, ui = lit ? b * rs : 0.f;   // S = 0: phase 0
+                        u[e] = make_float2(valid ? ur : 0.f, valid ? ui : 0.f);
                     }
                     put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
                 }
@@ -857,12 +910,15 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_mbar[kBarsWs];
     __shared__ Info s_info[2];
+    __shared__ G2Info s_g2;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         for (int b = 0; b < kBarsWs; ++b) {
             // the epilogue's releases arrive once per warp
-            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1 || b == kUFull || b == kZEmpty) ? W : 1;
+            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1 || b == kUFull || b == kZEmpty) ? W
+                                 : b == kDrain                                                  ? 2
+                                                                                                : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::saddr(&s_mbar[b])), "r"(cnt));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -879,9 +935,11 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     const SmemWs m = carve_ws(smem, W / 4);
     unsigned *status = queue + 2;
     if (warp == W) {
-        control(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
+        control_gemm1(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
+    } else if (warp == W + 1) {
+        control_gemm2(m, &s_g2, mb, s_tmem, status);
     } else {
-        epilogue<W>(holos, slots, m, s_info, mb, s_tmem, status);
+        epilogue<W>(holos, slots, m, s_info, &s_g2, mb, s_tmem, status);
     }
     tc::fence_before();
     __syncthreads();
