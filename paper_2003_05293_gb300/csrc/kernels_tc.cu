@@ -636,35 +636,51 @@ __device__ __noinline__ void control_gemm2(const SmemWs &m, const G2Info *g2, ui
 }
 
 // The GEMM 1 warp: takes work items, publishes them, and issues GEMM 1 of each.
+// The pop of the next item and the global loads of the item's slot and
+// descriptor are issued ahead of the waits they would otherwise follow.
 __device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
                                            int nslots, int total_tiles, unsigned *queue, const SmemWs &m,
                                            Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
 {
+    constexpr int kHWords = (int)(sizeof(HoloDev) / 4), kHPer = (kHWords + 31) / 32;
+    static_assert(sizeof(HoloDev) % 4 == 0, "word copies");
     Ctl C = ctl_init(m, mb, tmem);
-    const bool lane0 = (threadIdx.x & 31) == 0;
+    const int lane = threadIdx.x & 31;
+    const bool lane0 = lane == 0;
     bool ok = true;
+    int slot = 0;   // a block's items only rise, so their slots are found by scanning forward
+    int item = total_tiles;
+    if (lane0) item = (int)atomicAdd(queue, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
+        bool fin = item >= total_tiles;
+        // the next item's pop is in flight while this one is published and multiplied
+        int next = total_tiles;
+        if (lane0 && !fin) next = (int)atomicAdd(queue, 1u);
+        const HoloDev *Hp = nullptr;
+        LaunchSlot sl{};
+        uint32_t hw[kHPer];
+        if (!fin) {
+            while (slot + 1 < nslots && slots[slot + 1].tile_begin <= item) ++slot;
+            sl = slots[slot];
+            Hp = &holos[sl.holo];
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(Hp);
+#pragma unroll
+            for (int i = 0; i < kHPer; ++i) {
+                const int w = lane + 32 * i;
+                hw[i] = w < kHWords ? __ldg(src + w) : 0u;
+            }
+        }
         // S buffer j and info slot j are free once the epilogue has read tile k - 2's
         if (k >= 2 && ok) ok = warp_wait(mbar_at(mb, kSEmpty0 + j), (k >> 1) - 1u);
-        int item = total_tiles;
-        if (ok && lane0) item = (int)atomicAdd(queue, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        const bool fin = item >= total_tiles;
-        const HoloDev *Hp = nullptr;
+        fin = fin || !ok;
         bool empty = true;
         int rb = 0, cb = 0;
         if (fin) {
             if (lane0) info[j].done = 1;
         } else {
-            int lo = 0, hi = nslots - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (slots[mid].tile_begin <= item) lo = mid;
-                else hi = mid - 1;
-            }
-            Hp = &holos[slots[lo].holo];
-            const int t = item - slots[lo].tile_begin;
+            const int t = item - sl.tile_begin;
             const int col_tiles = (Hp->P + kCols - 1) / kCols;
             rb = t / col_tiles;
             cb = t % col_tiles;
@@ -673,11 +689,14 @@ __device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, co
                 info[j].item = item;
                 info[j].empty = empty ? 1 : 0;
                 info[j].done = 0;
-                info[j].sl = slots[lo];
+                info[j].sl = sl;
             }
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(Hp);
             uint32_t *dst = reinterpret_cast<uint32_t *>(&info[j].H);
-            for (int w = threadIdx.x & 31; w < (int)(sizeof(HoloDev) / 4); w += 32) dst[w] = __ldg(src + w);
+#pragma unroll
+            for (int i = 0; i < kHPer; ++i) {
+                const int w = lane + 32 * i;
+                if (w < kHWords) dst[w] = hw[i];
+            }
         }
         __syncwarp();
         if (lane0) arrive(mbar_at(mb, kReady0 + j));
@@ -686,6 +705,7 @@ __device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, co
             ok = gemm1(C, *Hp, rb, cb, j);
         }
         if (fin || !ok) break;
+        item = __shfl_sync(0xffffffffu, next, 0);
     }
     const bool drained = drain(C);
     if ((!ok || !drained) && lane0) atomicOr(status, 1u);
@@ -844,9 +864,10 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             ok = group_and<W>(wait_newest(mbar_at(mb, kZFull), n_z));
             if (!ok) break;
             fence_after();
+            // every lane computes (a lane past N uses spot N - 1's factors and
+            // stores nothing): no divergent branch in the row loop
             const int nl = 32 * q + lane, n = sb * kSpotBlock + nl;
-            int4 cf = make_int4(0, 0, 0, 0);
-            if (n < N) cf = H.coef[n];
+            const int4 cf = H.coef[min(n, N - 1)];
             float vr = 0.f, vi = 0.f;
 #pragma unroll 1
             for (int y16 = 0; y16 < G::kRowsPer; y16 += 16) {
@@ -855,23 +876,19 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                 ld16(z_re + lanes + ys, zr);
                 ld16(z_im + lanes + ys, zi);
                 float4 r4[8];
-                if (n < N) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float2 a = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e - half, kFixRound, 1.f);
-                        const float2 b = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e + 1 - half, kFixRound, 1.f);
-                        r4[e] = make_float4(a.x, a.y, b.x, b.y);
-                    }
+                for (int e = 0; e < 8; ++e) {
+                    const float2 a = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e - half, kFixRound, 1.f);
+                    const float2 b = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e + 1 - half, kFixRound, 1.f);
+                    r4[e] = make_float4(a.x, a.y, b.x, b.y);
                 }
                 ld_wait();
-                if (n < N) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        vr = fmaf(r4[e].x, zr[2 * e], fmaf(r4[e].y, zi[2 * e], vr));
-                        vi = fmaf(r4[e].x, zi[2 * e], fmaf(-r4[e].y, zr[2 * e], vi));
-                        vr = fmaf(r4[e].z, zr[2 * e + 1], fmaf(r4[e].w, zi[2 * e + 1], vr));
-                        vi = fmaf(r4[e].z, zi[2 * e + 1], fmaf(-r4[e].w, zr[2 * e + 1], vi));
-                    }
+                for (int e = 0; e < 8; ++e) {
+                    vr = fmaf(r4[e].x, zr[2 * e], fmaf(r4[e].y, zi[2 * e], vr));
+                    vi = fmaf(r4[e].x, zi[2 * e], fmaf(-r4[e].y, zr[2 * e], vi));
+                    vr = fmaf(r4[e].z, zr[2 * e + 1], fmaf(r4[e].w, zi[2 * e + 1], vr));
+                    vi = fmaf(r4[e].z, zi[2 * e + 1], fmaf(-r4[e].w, zr[2 * e + 1], vi));
                 }
             }
             fence_before();
