@@ -586,12 +586,16 @@ def main():
         d_u = max(abs(a["u"] - b["u"]) for a, b in zip(r16, res))
         d_ph = max(float(torch.sqrt(torch.mean((torch.remainder(o16 - o + math.pi, 2 * math.pi) - math.pi) ** 2)))
                    for o16, o in zip(outs16, outs))
+        t16 = b16.tile_shape()
+        what16 = ("compressed iterations on the tensor cores with FP16 forward-projection products (FP32 "
+                  "accumulation); full iterations and the final pass FP32-class" if t16["threads"] == SUBSET_TC else
+                  "compressed iterations with half-precision sincos (packed FP16 on the FMA pipe); full "
+                  "iterations and the final pass FP32")
         line["fp16_sincos"] = {"value": job_throughput(B, world, args.steps, ms16), "unit": "holograms/s",
                                "ms_per_step": ms16 / args.steps,
                                "compressed_ms_per_launch": sum(kt16[1:1 + n_sub]) / max(1, n_sub),
                                "vs_fp32": {"max_abs_de": d_e, "max_abs_du": d_u, "max_phase_rms_rad": d_ph},
-                               "what": "compressed iterations with half-precision sincos (packed FP16 on the FMA "
-                                       "pipe); full iterations and final pass FP32"}
+                               "tile": t16, "what": what16}
         b16.close()
         p16.close()
 

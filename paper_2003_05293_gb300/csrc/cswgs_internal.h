@@ -63,7 +63,8 @@ struct HoloDev {
     // factor tables of the tensor-core full passes (nullptr: not used)
     unsigned char *rwtab;   // R' = w a e^{i theta} R blocks, remade before every full pass
     unsigned char *ctab;    // C blocks (GEMM 1 operand), made once
-    unsigned char *cstab;   // C blocks for GEMM 2, made once
+    unsigned char *cstab;   // C blocks for GEMM 2 (split BF16), made once
+    unsigned char *cstab16; // the same in FP16 for the half-precision option (nullptr: not made)
     // subset mask of compressed passes on the tensor cores (nullptr: not used):
     // P rows of mask_words words, bit c % 32 of word c / 32 for pixel column c
     uint32_t *mask;
@@ -130,8 +131,8 @@ int full_tc_max_grid(int variant, int maxN, int sm_count);
 cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
                            int maxN, unsigned *queue, int grid, cudaStream_t s);
 cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
-                             unsigned *queue, int grid, cudaStream_t s);
-void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs);
+                             unsigned *queue, int grid, int f16, cudaStream_t s);
+void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs);   // cs: split BF16 (FP16: half)
 cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count, cudaStream_t s);
 cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
                                 cudaStream_t s);

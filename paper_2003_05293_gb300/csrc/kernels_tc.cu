@@ -10,15 +10,21 @@
 //                               V_n  = sum_y conj(R_n(y)) Z(n, y)         [per spot, CUDA cores]
 // A compressed iteration is the same computation with u zero outside the
 // subset S_j, so the sums run over S_j as Eqs. 1 and 3 ask.
-// Every FP32 operand is split into two BF16 halves, v = hi + lo, and each
-// real product is kept as hi hi + hi lo + lo hi: 2^-16 relative per product,
-// FP32-class phases; the accumulators (FP32) live in tensor memory.
-// GEMM 1 runs its complex product as two real ones stacked along N (M = 128
-// rows, N = 128, K = 16 spots):
+// The accumulators (FP32) live in tensor memory.
+// GEMM 1 sets each pixel's phase: its FP32 operands are split into two BF16
+// halves, v = hi + lo, and each real product is kept as hi hi + hi lo + lo hi
+// (2^-16 relative per product, FP32-class phases).  It runs its complex
+// product as two real ones stacked along N (M = 128 rows, N = 128, K = 16
+// spots):
 //   [S_re | S_im] = R'_re [C_re | C_im] + R'_im [-C_im | C_re],
 // with the two B operands as two 128-row windows of one 192-row tile
-// [-C_im | C_re | C_im]; GEMM 2 is M = 128 spots x N = 128 rows x K = 16
-// columns per instruction, real and imaginary parts apart.
+// [-C_im | C_re | C_im]: 6 instructions per spot chunk.
+// GEMM 2 (the forward projection) is M = 128 spots x N = 128 rows x K = 16
+// columns per instruction, real and imaginary parts apart, with split BF16
+// operands too (12 instructions per K-step).  The half-precision option
+// (compressed launches only) takes single FP16 operands instead (|u|, |C| <=
+// 1; 4 instructions per K-step): the sums run over many pixels whose
+// rounding errors (2^-12 relative) do not add up coherently.
 //
 // The operands are factor tables in global memory, laid out block by block
 // exactly as the MMAs read them from shared memory (no-swizzle K-major core
@@ -32,6 +38,7 @@
 // bounded and a timeout is recorded in the launch's status word instead of
 // hanging.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -86,11 +93,12 @@ __device__ __forceinline__ uint64_t desc(uint32_t start, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc(int M, int N, int neg_a)
+// Instruction descriptor, kind::f16: D FP32, A and B both BF16 (bf16 = 1) or
+// both FP16 (bf16 = 0), both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc(int M, int N, int neg_a, int bf16 = 1)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg_a << 13) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)neg_a << 13) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
@@ -200,6 +208,26 @@ __device__ __forceinline__ void complex_mma(uint32_t d_re, uint32_t d_im, const 
     mma(d_im, a[3], b[0], id_ir, 1u);
 }
 
+// Eight complex values -> FP16 rows of the re and im component tiles
+// (`stride` bytes apart), one 16-byte store each (round to nearest).
+__device__ __forceinline__ uint32_t h2_bits(__half2 h)
+{
+    return (uint32_t)__half_as_ushort(__low2half(h)) | ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
+}
+
+__device__ __forceinline__ void put8h(unsigned char *base, uint32_t stride, uint32_t off, const float2 *v)
+{
+    uint32_t wr[4], wi[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        wr[q] = h2_bits(__floats2half2_rn(v[2 * q].x, v[2 * q + 1].x));
+        wi[q] = h2_bits(__floats2half2_rn(v[2 * q].y, v[2 * q + 1].y));
+    }
+    *reinterpret_cast<uint4 *>(base + off) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+    *reinterpret_cast<uint4 *>(base + stride + off) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+}
+
+
 // ------------------------------------------------------------- factor tables --
 // Items of eight phasors; consecutive threads take consecutive rows of one
 // core matrix, so a warp's 16-byte stores fill whole 128-byte lines.
@@ -236,7 +264,8 @@ __device__ __forceinline__ void put8_stacked(unsigned char *base, uint32_t re_of
 
 // C (GEMM 1's B: per block of 64 columns and 16 spots, each half a 192-row
 // tile [-C_im | C_re | C_im] with row = column within each third) and C for
-// GEMM 2 (128 spots x 64 columns per block) of hologram blockIdx.y, from its
+// GEMM 2 (128 spots x 64 columns per block; split BF16, and for the
+// half-precision option also FP16 re and im) of hologram blockIdx.y, from its
 // spot coefficients.
 __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__restrict__ holos, int count)
 {
@@ -278,6 +307,7 @@ __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__rest
                 for (int e = 0; e < 8; ++e) v[e] = make_float2(0.f, 0.f);
             }
             put8(H.cstab + (size_t)blk * (4 * kCs), kCs, core_off(nl, 8 * g, kCols), v);
+            if (H.cstab16) put8h(H.cstab16 + (size_t)blk * (2 * kCs), kCs, core_off(nl, 8 * g, kCols), v);
         }
     }
 }
@@ -376,8 +406,8 @@ enum Bar {
 // up a tile with products (a single slot: the next one is written only after
 // that tile's GEMM 2 has been issued and waited for).
 struct G2Info {
-    const unsigned char *cstab;
-    int nsb, cb, done, pad;
+    const unsigned char *cstab;   // GEMM 2's C blocks in the launch's format
+    int nsb, cb, done, f16;
 };
 
 // A published work item: the tile, and copies of its launch slot and its
@@ -549,10 +579,14 @@ __device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, 
 
 // GEMM 2 of one tile: Z = conj(C)^T u, one block of 128 spots at a time, into
 // columns 0..255; each block's C streams in once the previous GEMM 2 is done
-// with the buffer (block 0 while u is still being written).
+// with the buffer (block 0 while u is still being written).  Split BF16
+// operands (4 components each), or FP16 re and im for the half-precision
+// option.
 __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
 {
-    const uint32_t id = idesc(kSpotBlock, kRows, 0), idn = idesc(kSpotBlock, kRows, 1);
+    const int f16 = g.f16;
+    const uint32_t comps = f16 ? 2u : 4u;
+    const uint32_t id = idesc(kSpotBlock, kRows, 0, f16 ? 0 : 1), idn = idesc(kSpotBlock, kRows, 1, f16 ? 0 : 1);
     const uint32_t z_re = C.tmem, z_im = C.tmem + kRows;
     const uint64_t cs0 = desc(C.cs, 128, (kCols / 8) * 128);
     const uint64_t u0 = desc(C.u, 128, (kCols / 8) * 128);
@@ -560,9 +594,9 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
         if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZFull), C.nz - 1u)) return false;
         if (elect_one()) {
             const uint32_t full = mbar_at(C.mb, kCsFull);
-            expect_tx(full, 4 * kCs);
-            const unsigned char *src = g.cstab + ((size_t)g.cb * g.nsb + sb) * (4 * kCs);
-            for (int q = 0; q < 4; ++q) bulk_load(C.cs + q * kCs, src + q * kCs, kCs, full);
+            expect_tx(full, comps * kCs);
+            const unsigned char *src = g.cstab + ((size_t)g.cb * g.nsb + sb) * (comps * kCs);
+            for (uint32_t q = 0; q < comps; ++q) bulk_load(C.cs + q * kCs, src + q * kCs, kCs, full);
         }
         __syncwarp();
         C.ncs++;
@@ -575,12 +609,25 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
         if (!warp_wait(mbar_at(C.mb, kCsFull), C.ncs - 1u)) return false;
         fence_after();
         for (int ks = 0; ks < kCols / 16; ++ks) {
-            uint64_t a[4], b[4];
-            for (int q = 0; q < 4; ++q) {
-                a[q] = cs0 + ((uint64_t)(q * kCs + ks * 256) >> 4);
-                b[q] = u0 + ((uint64_t)(q * kU + ks * 256) >> 4);
+            if (f16) {
+                // conj(C) u: Z_re = C_re u_re + C_im u_im, Z_im = C_re u_im - C_im u_re
+                const uint64_t cr = cs0 + ((uint64_t)(ks * 256) >> 4), ci = cs0 + ((uint64_t)(kCs + ks * 256) >> 4);
+                const uint64_t ur = u0 + ((uint64_t)(ks * 256) >> 4), ui = u0 + ((uint64_t)(kU + ks * 256) >> 4);
+                if (elect_one()) {
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    mma(z_re, cr, ur, id, acc);
+                    mma(z_re, ci, ui, id, 1u);
+                    mma(z_im, cr, ui, id, acc);
+                    mma(z_im, ci, ur, idn, 1u);
+                }
+            } else {
+                uint64_t a[4], b[4];
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = cs0 + ((uint64_t)(q * kCs + ks * 256) >> 4);
+                    b[q] = u0 + ((uint64_t)(q * kU + ks * 256) >> 4);
+                }
+                if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, ks > 0 ? 1u : 0u, 1);
             }
-            if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, ks > 0 ? 1u : 0u, 1);
         }
         if (elect_one()) commit(mbar_at(C.mb, kZFull));
         __syncwarp();
@@ -714,7 +761,7 @@ __device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, co
 // The epilogue warps: per tile, u = A S / |S| (with Phi and the gray level in
 // the final pass), then the tile's partial V_n = sum_y conj(R_n(y)) Z(n, y)
 // per spot block.
-template <int W>
+template <int W, bool F16>
 __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
                                          const SmemWs &m, const Info *info, G2Info *g2, uint32_t mb,
                                          uint32_t tmem, unsigned *status)
@@ -769,10 +816,11 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
 
         // the GEMM 2 warp's operands for this tile (it streams C in meanwhile)
         if (tid == 0) {
-            g2->cstab = H.cstab;
+            g2->cstab = F16 ? H.cstab16 : H.cstab;
             g2->nsb = nspotblocks(N);
             g2->cb = t % col_tiles;
             g2->done = 0;
+            g2->f16 = F16 ? 1 : 0;
             arrive(mbar_at(mb, kG2Info));
         }
 
@@ -828,7 +876,8 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                         const float ur = lit ? a * rs : amp, ui = lit ? b * rs : 0.f;   // S = 0: phase 0
                         u[e] = make_float2(valid ? ur : 0.f, valid ? ui : 0.f);
                     }
-                    put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+                    if (F16) put8h(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+                    else put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
                 }
                 if (pass == kPassFinal && gy < P) {
 #pragma unroll
@@ -918,7 +967,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
 
 }  // namespace tc
 
-template <int W>
+template <int W, bool F16>
 __global__ void __launch_bounds__(tc::ws::Cfg<W>::kThreads, 1)
 iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
                       int total_tiles, unsigned *queue)
@@ -956,7 +1005,7 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     } else if (warp == W + 1) {
         control_gemm2(m, &s_g2, mb, s_tmem, status);
     } else {
-        epilogue<W>(holos, slots, m, s_info, &s_g2, mb, s_tmem, status);
+        epilogue<W, F16>(holos, slots, m, s_info, &s_g2, mb, s_tmem, status);
     }
     tc::fence_before();
     __syncthreads();
@@ -997,31 +1046,41 @@ __global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restri
     else tail_update<256>(H, sl, s_v, s_red);
 }
 
-template <int W>
-static int tcws_max_grid(int maxN, int sm_count)
+template <int W, bool F16>
+static int tcws_max_grid_of(int maxN, int sm_count)
 {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, iter_full_tcws_kernel<W>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, iter_full_tcws_kernel<W, F16>) != cudaSuccess) return 0;
     const size_t limit = 227 * 1024 - fa.sharedSizeBytes;
     const size_t smem = tc::ws::smem_bytes_ws(W / 4);
     if (smem > limit || (size_t)maxN * sizeof(float2) > 48 * 1024) return 0;
-    if (cudaFuncSetAttribute(iter_full_tcws_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(iter_full_tcws_kernel<W, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)limit) != cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iter_full_tcws_kernel<W>, tc::ws::Cfg<W>::kThreads,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iter_full_tcws_kernel<W, F16>,
+                                                      tc::ws::Cfg<W>::kThreads, smem) != cudaSuccess)
         return 0;
     return std::min(per_sm, 1) * sm_count;   // a block holds all 512 tensor-memory columns
 }
 
 template <int W>
+static int tcws_max_grid(int maxN, int sm_count)
+{
+    return std::min(tcws_max_grid_of<W, false>(maxN, sm_count), tcws_max_grid_of<W, true>(maxN, sm_count));
+}
+
+template <int W>
 static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
-                               unsigned *queue, int grid, bool subset, cudaStream_t s)
+                               unsigned *queue, int grid, bool subset, int f16, cudaStream_t s)
 {
     (void)cudaGetLastError();
-    iter_full_tcws_kernel<W><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(W / 4), s>>>(
-        holos, slots, nslots, total_tiles, queue);
+    if (f16)
+        iter_full_tcws_kernel<W, true><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(W / 4), s>>>(
+            holos, slots, nslots, total_tiles, queue);
+    else
+        iter_full_tcws_kernel<W, false><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(W / 4), s>>>(
+            holos, slots, nslots, total_tiles, queue);
     // one tail block per slot, plus (compressed launches) blocks that clear the masks
     const dim3 tails((unsigned)nslots, 1u + (subset ? 8u : 0u));
     tcws_tails_kernel<<<tails, 256, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
@@ -1063,16 +1122,16 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
 }
 
 cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
-                             unsigned *queue, int grid, cudaStream_t s)
+                             unsigned *queue, int grid, int f16, cudaStream_t s)
 {
-    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, true, s);
+    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, true, f16, s);
 }
 
 cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
                            int maxN, unsigned *queue, int grid, cudaStream_t s)
 {
     if (variant != kFullTcWs) return cudaErrorInvalidValue;
-    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, false, s);
+    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, false, 0, s);
 }
 
 }  // namespace cswgs

@@ -202,7 +202,6 @@ bool shape_supported(TileShape shape)
     // the CUDA-core kernels the shape names, with stand-ins for the tensor-core ones
     TileShape cuda_core = shape;
     if (shape.threads == kSubsetTc) {
-        if (shape.fp16) return false;   // the half-precision sincos belongs to the CUDA-core kernel
         cuda_core.threads = 256;
         cuda_core.ppt = 4;
     }
@@ -229,7 +228,7 @@ cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const 
     if (kind == kLaunchFull && is_full_tc(shape.full_threads))
         return launch_full_tc(shape.full_threads, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
     if (kind == kLaunchSubset && shape.threads == kSubsetTc)
-        return launch_subset_tc(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
+        return launch_subset_tc(holos, slots, nslots, total_tiles, maxN, queue, grid, shape.fp16, s);
     return launch_iter_fp32(shape, kind, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
 }
 
@@ -318,6 +317,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             size_t rw, c, cs;
             full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
             work += align256(rw) + align256(c) + align256(cs);
+            if (shape.fp16 && shape.threads == kSubsetTc) work += align256(cs / 2);   // FP16 C for GEMM 2
         }
         b->maxN = std::max(b->maxN, s.N);
     }
@@ -399,6 +399,10 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             w += align256(c);
             H.cstab = reinterpret_cast<unsigned char *>(base + w);
             w += align256(cs);
+            if (shape.fp16 && shape.threads == kSubsetTc) {
+                H.cstab16 = reinterpret_cast<unsigned char *>(base + w);
+                w += align256(cs / 2);
+            }
         }
     }
 

@@ -150,6 +150,7 @@ size_t Server::footprint(const HoloSpec &s) const
         size_t rw, c, cs;
         full_tc_table_bytes(s.P, s.N, &rw, &c, &cs);
         b += al256(rw) + al256(c) + al256(cs);
+        if (shape_.fp16 && shape_.threads == kSubsetTc) b += al256(cs / 2);
     }
     if (shape_.threads == kSubsetTc) b += al256(sizeof(uint32_t) * (size_t)s.P * mask_words_of(s.P));
     return b;
@@ -208,6 +209,10 @@ void Server::place(Req &r)
         o += al256(c);
         H.cstab = reinterpret_cast<unsigned char *>(b + o);
         o += al256(cs);
+        if (shape_.fp16 && shape_.threads == kSubsetTc) {
+            H.cstab16 = reinterpret_cast<unsigned char *>(b + o);
+            o += al256(cs / 2);
+        }
     }
     if (shape_.threads == kSubsetTc) {
         // the subset mask starts clear (each compressed launch's tails clear it again)

@@ -50,6 +50,7 @@ __device__ void tail_update(const HoloDev &H, const LaunchSlot &sl, float2 *s_v,
     double local = 0.0;
     for (int n = threadIdx.x; n < N; n += THREADS) {
         float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll 8   // loads issued ahead of the compensated sum's chain
         for (int t = 0; t < sl.tiles; ++t) {
             float2 p = __ldcg(&H.part[(size_t)t * N + n]);
             float yr = p.x - cr, tr = sr + yr;
@@ -85,6 +86,7 @@ __device__ void tail_metrics(const HoloDev &H, const LaunchSlot &sl, double *s_r
     double e = 0.0, imax = -1.0, imin = 1e300;
     for (int n = threadIdx.x; n < N; n += THREADS) {
         double vr = 0.0, vi = 0.0;
+#pragma unroll 8
         for (int t = 0; t < sl.tiles; ++t) {
             double2 p = __ldcg(&H.part64[(size_t)t * N + n]);
             vr += p.x;

@@ -158,3 +158,48 @@ def test_serving(plans):
         s = cc.solve(pb.xyz, pb.P, pb.c, pb.iterations, pb.seed, out=o2)
         assert rms_wrapped(out.cpu().numpy(), o2.cpu().numpy()) < TOL_PHASE_RMS
         assert abs(r["e"] - s["e"]) < TOL_EU and abs(r["u"] - s["u"]) < TOL_EU
+
+
+# ---- the half-precision option on the tensor cores: GEMM 2 of compressed
+# launches with single FP16 operands (full passes and the final pass keep the
+# split BF16 products); held to the parity bar, not to the FP16-sincos one
+
+@pytest.fixture(scope="module")
+def half_plan(tmp_path_factory):
+    from paper_2003_05293_gb300 import Plan
+    path = tmp_path_factory.mktemp("half") / "h.json"
+    entries = {"P%d_N%d_B%d_H" % (128 * p, 2 ** n, 2 ** b): [SUBSET_TC, 1, FULL_WS]
+               for p in range(1, 11) for n in range(4, 11) for b in range(0, 7)}
+    path.write_text(json.dumps({"format": "cswgs-tune-2", "entries": entries}))
+    plan = Plan(precision="fp32_fp16sincos", tune_cache=str(path))
+    yield plan
+    plan.close()
+
+
+def test_half_path_is_reported(half_plan):
+    pbs = [workloads.problem(256, 40, 5.0, 0.125, 4, seed=s) for s in range(3)]
+    b = half_plan.batch(pbs)
+    assert b.tile_shape()["threads"] == SUBSET_TC
+    b.close()
+
+
+@pytest.mark.parametrize("P,N,c,j", [(512, 100, 0.125, 1), (512, 100, 0.125, 17), (96, 129, 1.0 / 64, 1),
+                                     (96, 129, 1.0 / 64, 2)])
+def test_half_teacher_forced_compressed_iteration(half_plan, P, N, c, j):
+    pb = workloads.problem(P, N, 10.0, c, 30, seed=12 if P == 512 else 7)
+    st = oracle_states(oracle, pb, j, full_iterations=0)
+    w0, th0 = st[j - 1]
+    w1, th1 = st[j]
+    r = half_plan.solve(pb.xyz, pb.P, pb.c, 1, pb.seed, init_w=w0, init_theta=th0, first_iteration=j,
+                        full_iterations=0, final_pass=False, state=True)
+    assert rms_wrapped(r["theta"], th1) < TOL_PHASE_RMS
+    assert math.sqrt(np.mean((r["w"] / w1 - 1) ** 2)) < TOL_PHASE_RMS
+
+
+@pytest.mark.parametrize("P,N,c,I", [(512, 100, 0.125, 30), (1152, 100, 0.125, 12), (200, 300, 0.25, 8)])
+def test_half_free_running_against_oracle(half_plan, P, N, c, I):
+    pb = workloads.problem(P, N, 10.0, c, I, seed=7)
+    ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    r, ph = _solve(half_plan, pb)
+    assert rms_wrapped(ph, ref["phase"]) < TOL_PHASE_RMS
+    assert abs(r["e"] - ref["e"]) < TOL_EU and abs(r["u"] - ref["u"]) < TOL_EU
