@@ -37,6 +37,27 @@ def _pupil(aperture="square", waist=0.0, subset_mode="fresh"):
     return p
 
 
+_SQUARE = _pupil()
+
+
+def _addr(a):
+    """Address of a contiguous array, or None."""
+    return None if a is None else a.ctypes.data
+
+
+def _out_addr(out):
+    """(address, on_host) of an output: a torch CUDA tensor, a numpy float32 array or None."""
+    if out is None:
+        return None, 0
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float32 or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("host output must be a contiguous float32 array")
+        return out.ctypes.data, 1
+    if not out.is_cuda or out.dtype.__str__() != "torch.float32" or not out.is_contiguous():
+        raise ValueError("device output must be a contiguous float32 CUDA tensor")
+    return out.data_ptr(), 0
+
+
 def _u8ptr(t):
     return ctypes.cast(ctypes.c_void_p(t.data_ptr()), capi.c_uint8_p)
 
@@ -217,24 +238,26 @@ class Plan:
             amp = _f64(pb.amp)
             keep += [xyz, amp]
             r = reqs[i]
-            r.spots_xyz = _dptr(xyz)
-            r.amplitudes = _dptr(amp)
+            r.spots_xyz = _addr(xyz)
+            r.amplitudes = _addr(amp)
             r.N = xyz.shape[0]
             r.P = pb.P
             r.subset_fraction = pb.c
             r.iterations = pb.iterations
             r.seed = int(pb.seed) & (2**64 - 1)
-            extra = getattr(pb, "extra", {}) or {}
-            r.full_iterations = int(extra.get("full_iterations", 2))
-            r.pupil = _pupil(extra.get("aperture", "square"), extra.get("waist", 0.0),
-                             extra.get("subset_mode", "fresh"))
-            slm = extra.get("slm")
-            if slm is not None:
-                r.slm = ctypes.pointer(slm.c)
-                keep.append(slm)
-            ptr, host = _out_ptr(outs[i] if outs is not None else None)
-            r.phase_out = ptr
-            r.out_on_host = host
+            extra = getattr(pb, "extra", None)
+            if extra:
+                r.full_iterations = int(extra.get("full_iterations", 2))
+                r.pupil = _pupil(extra.get("aperture", "square"), extra.get("waist", 0.0),
+                                 extra.get("subset_mode", "fresh"))
+                slm = extra.get("slm")
+                if slm is not None:
+                    r.slm = ctypes.pointer(slm.c)
+                    keep.append(slm)
+            else:
+                r.full_iterations = 2
+                r.pupil = _SQUARE
+            r.phase_out, r.out_on_host = _out_addr(outs[i] if outs is not None else None)
         return reqs, keep
 
     def batch(self, problems, outs=None) -> "Batch":

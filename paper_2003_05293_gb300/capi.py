@@ -55,10 +55,13 @@ class cswgs_solve_opts(ctypes.Structure):
 
 
 class cswgs_request(ctypes.Structure):
-    _fields_ = [("spots_xyz", c_double_p), ("amplitudes", c_double_p), ("N", ctypes.c_int),
+    # the data pointers are declared void* here (same size and place as the
+    # header's const double* / float*): a batch of requests is filled with
+    # plain addresses, without a ctypes cast per field
+    _fields_ = [("spots_xyz", ctypes.c_void_p), ("amplitudes", ctypes.c_void_p), ("N", ctypes.c_int),
                 ("P", ctypes.c_int), ("subset_fraction", ctypes.c_double),
                 ("iterations", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("full_iterations", ctypes.c_int), ("phase_out", c_float_p),
+                ("full_iterations", ctypes.c_int), ("phase_out", ctypes.c_void_p),
                 ("out_on_host", ctypes.c_int), ("pupil", cswgs_pupil),
                 ("slm", ctypes.POINTER(cswgs_slm_frame))]
 
