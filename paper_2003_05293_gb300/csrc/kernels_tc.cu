@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 //   s_full[2]         GEMM 1 of the tile in that S buffer is done
 //   s_empty[2]        the epilogue has read that S buffer and info slot
 //   g2_info           epilogue -> GEMM 2 warp: the tile's C blocks (or done)
-//   u_full            the epilogue has written u
+//   u_half[2]         the epilogue has written half of u (GEMM 2 starts on it)
 //   cs_full           GEMM 2's C block has landed
 //   z_full            GEMM 2 of a spot block is done (C block buffer free)
 //   z_empty           the epilogue has read Z
@@ -393,7 +393,8 @@ enum Bar {
     kEmpty0 = kFull0 + kRing,
     kSFull0 = kEmpty0 + kRing,
     kSEmpty0 = kSFull0 + 2,
-    kUFull = kSEmpty0 + 2,
+    kUHalf0 = kSEmpty0 + 2,   // u's first 16-column chunk of every thread: columns 0-15 and 32-47
+    kUHalf1,                  // the second: columns 16-31 and 48-63
     kCsFull,
     kZFull,
     kZEmpty,
@@ -428,6 +429,7 @@ struct Cfg {
     static constexpr int kRowsPer = kRows / kGroups;  // epilogue 2: rows per thread
     static_assert(W % 4 == 0 && kColsPer % 16 == 0 && kRowsPer % 16 == 0, "epilogue split");
     static_assert(kColsPer <= 32, "a thread's columns lie in one mask word");
+    static_assert(kColsPer == 32, "u is handed over in two 16-column chunks per thread");
 };
 
 // Dynamic shared memory: the partial sums of epilogue 2, the GEMM 1 ring,
@@ -600,21 +602,25 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
         }
         __syncwarp();
         C.ncs++;
-        if (sb == 0) {
-            if (!warp_wait(mbar_at(C.mb, kUFull), C.nu)) return false;
-            C.nu++;
-        }
+        if (sb == 0 && !warp_wait(mbar_at(C.mb, kUHalf0), C.nu)) return false;
         // the epilogue has read the previous Z
         if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZEmpty), C.nz - 1u)) return false;
         if (!warp_wait(mbar_at(C.mb, kCsFull), C.ncs - 1u)) return false;
         fence_after();
-        for (int ks = 0; ks < kCols / 16; ++ks) {
+        // on a tile's first spot block, the K-steps of u's first half (0, 2)
+        // go before those of the second (1, 3), which wait for it
+        for (int i = 0; i < kCols / 16; ++i) {
+            const int ks = sb == 0 ? (i < 2 ? 2 * i : 2 * i - 3) : i;
+            if (sb == 0 && i == 2) {
+                if (!warp_wait(mbar_at(C.mb, kUHalf1), C.nu)) return false;
+                fence_after();
+            }
             if (f16) {
                 // conj(C) u: Z_re = C_re u_re + C_im u_im, Z_im = C_re u_im - C_im u_re
                 const uint64_t cr = cs0 + ((uint64_t)(ks * 256) >> 4), ci = cs0 + ((uint64_t)(kCs + ks * 256) >> 4);
                 const uint64_t ur = u0 + ((uint64_t)(ks * 256) >> 4), ui = u0 + ((uint64_t)(kU + ks * 256) >> 4);
                 if (elect_one()) {
-                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    const uint32_t acc = i > 0 ? 1u : 0u;
                     mma(z_re, cr, ur, id, acc);
                     mma(z_re, ci, ui, id, 1u);
                     mma(z_im, cr, ui, id, acc);
@@ -626,9 +632,10 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
                     a[q] = cs0 + ((uint64_t)(q * kCs + ks * 256) >> 4);
                     b[q] = u0 + ((uint64_t)(q * kU + ks * 256) >> 4);
                 }
-                if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, ks > 0 ? 1u : 0u, 1);
+                if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, i > 0 ? 1u : 0u, 1);
             }
         }
+        if (sb == 0) C.nu++;
         if (elect_one()) commit(mbar_at(C.mb, kZFull));
         __syncwarp();
         C.nz++;
@@ -897,15 +904,15 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                         if (H.slm) write_gray4(H, gy, col, o + 4 * g);
                     }
                 }
+                // this chunk of u is in place: GEMM 2 takes its K-steps
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) arrive(mbar_at(mb, xc == 0 ? kUHalf0 : kUHalf1));
             }
         }
         fence_before();
-        fence_async_smem();
         __syncwarp();
-        if (lane == 0) {
-            arrive(mbar_at(mb, kSEmpty0 + j));
-            arrive(mbar_at(mb, kUFull));
-        }
+        if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
 
         // ---- epilogue 2 per spot block: V_n = sum_y conj(R_n(y)) Z(n, y)
         for (int sb = 0; sb * kSpotBlock < N; ++sb) {
@@ -982,7 +989,7 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     if (tid == 0) {
         for (int b = 0; b < kBarsWs; ++b) {
             // the epilogue's releases arrive once per warp
-            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1 || b == kUFull || b == kZEmpty) ? W
+            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1 || b == kUHalf0 || b == kUHalf1 || b == kZEmpty) ? W
                                  : b == kDrain                                                  ? 2
                                                                                                 : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::saddr(&s_mbar[b])), "r"(cnt));
