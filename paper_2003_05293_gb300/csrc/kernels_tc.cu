@@ -33,8 +33,9 @@
 // once per hologram; R' (per 128 rows and 16 spots) carries w and theta and is
 // remade before every launch.  A tile streams its blocks into shared memory
 // with bulk copies (cp.async.bulk, completion counted on an mbarrier) through
-// a ring; two issuing warps (GEMM 1, GEMM 2) issue the copies and MMAs and
-// commit them to mbarriers, eight epilogue warps run the CUDA-core stages.  Every wait is
+// a ring; a producer warp issues GEMM 1's copies, two issuing warps (GEMM 1,
+// GEMM 2) issue the MMAs and commit them to mbarriers, eight epilogue warps
+// run the CUDA-core stages.  Every wait is
 // bounded and a timeout is recorded in the launch's status word instead of
 // hanging.
 #include <cuda_bf16.h>
@@ -356,10 +357,14 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 
 
 // ----------------------------------------------------------- warp roles --
-// Tiles are pipelined by warp roles: a GEMM 1 warp, a GEMM 2 warp (one
-// elected lane of each issues its bulk copies and MMAs) and W epilogue warps.
+// Tiles are pipelined by warp roles: a producer warp (takes the work items and
+// loads GEMM 1's operand stages), a GEMM 1 warp, a GEMM 2 warp (one elected
+// lane of each issues its bulk copies and MMAs) and W epilogue warps.  The
+// producer runs ahead of the GEMM 1 warp by the ring's depth: a tcgen05.mma
+// issue waits for the tensor pipe, so copies issued from the MMA warp would
+// start one stage late.
 // Tensor memory holds two S buffers (columns 256..383 and 384..511; tile k
-// uses buffer k & 1) and Z (columns 0..255).  The GEMM 1 warp runs ahead into
+// uses buffer k & 1) and Z (columns 0..255).  GEMM 1 runs ahead into
 // the next tile's back-propagation while the epilogue warps turn S into u; the
 // GEMM 2 warp streams the tile's C block in meanwhile and issues GEMM 2 as
 // soon as u is ready; the epilogue warps run epilogue 1 and epilogue 2 of each
@@ -367,10 +372,11 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 // small kernel right after the launch, so tiles neither fence nor count
 // arrivals.
 // Hand-overs, all mbarriers:
-//   ready[2]          GEMM 1 warp -> epilogue: work item k in info slot k & 1
+//   ready[2]          producer -> GEMM 1 warp, epilogue: work item k in info slot k & 1
 //   full[r], empty[r] GEMM 1 operand ring: copies landed / MMAs done
 //   s_full[2]         GEMM 1 of the tile in that S buffer is done
-//   s_empty[2]        the epilogue has read that S buffer and info slot
+//   s_empty[2]        the epilogue has read that S buffer and info slot, and the
+//                     GEMM 1 warp that info slot
 //   g2_info           epilogue -> GEMM 2 warp: the tile's C blocks (or done)
 //   u_half[2]         the epilogue has written half of u (GEMM 2 starts on it)
 //   cs_full           GEMM 2's C block has landed
@@ -412,7 +418,7 @@ struct G2Info {
 };
 
 // A published work item: the tile, and copies of its launch slot and its
-// hologram's descriptor (staged by the control warp so that the epilogue
+// hologram's descriptor (staged by the producer warp so that the epilogue
 // warps read them from shared memory).
 struct Info {
     int item, empty, done, pad;
@@ -423,13 +429,15 @@ struct Info {
 template <int W>
 struct Cfg {
     static constexpr int kEpi = 32 * W;               // epilogue threads
-    static constexpr int kThreads = kEpi + 64;        // and the GEMM 1 and GEMM 2 warps
+    static constexpr int kThreads = kEpi + 96;        // and the producer, GEMM 1 and GEMM 2 warps
     static constexpr int kGroups = W / 4;             // epilogue warps per TMEM lane quadrant
     static constexpr int kColsPer = kCols / kGroups;  // epilogue 1: columns per thread
     static constexpr int kRowsPer = kRows / kGroups;  // epilogue 2: rows per thread
     static_assert(W % 4 == 0 && kColsPer % 16 == 0 && kRowsPer % 16 == 0, "epilogue split");
     static_assert(kColsPer <= 32, "a thread's columns lie in one mask word");
-    static_assert(kColsPer == 32, "u is handed over in two 16-column chunks per thread");
+    // u goes to GEMM 2 in two halves, K-steps 0, 2 and 1, 3: each 16-column
+    // chunk of u signals the half of its K-step, once per warp
+    static constexpr uint32_t kUHalfArrivals = W * (kColsPer / 16) / 2;
 };
 
 // Dynamic shared memory: the partial sums of epilogue 2, the GEMM 1 ring,
@@ -496,7 +504,7 @@ __device__ __forceinline__ bool tile_outside(const HoloDev &H, int t)
 // Barrier i of the block's array, by shared-memory address.
 __device__ __forceinline__ uint32_t mbar_at(uint32_t base, int i) { return base + 8u * (uint32_t)i; }
 
-// One elected lane of a converged warp (the issuing lane of the control warp).
+// One elected lane of a converged warp (the issuing lane of a producer or MMA warp).
 __device__ __forceinline__ bool elect_one()
 {
     uint32_t p;
@@ -527,16 +535,13 @@ struct Ctl {
     uint32_t nu;      // u hand-overs taken
 };
 
-// GEMM 1 of tile (rb, cb) of H into S buffer j: S = R' C^T over spot chunks,
-// operands streamed through the ring.  Chunk c's MMAs are queued before the
-// wait for chunk c - 1's, whose stage then takes chunk c - 1 + kRing.
-__device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, int j)
+// GEMM 1's operands of one tile, issued by the producer warp: for each chunk of
+// 16 spots, R' of row block rb and the stacked C of column block cb into the
+// next ring stage once the GEMM 1 warp's products have released it.
+__device__ __forceinline__ bool load_gemm1(Ctl &C, const HoloDev &H, int rb, int cb)
 {
-    const uint32_t id = idesc(kRows, 2 * kCols, 0);
-    const uint32_t s_acc = C.tmem + kS0 + 2 * kCols * j;   // [S_re | S_im]
     const int nc = nchunks(H.N);
-    const uint64_t ring0 = desc(C.ring, 128, 256);
-    auto load = [&](int c) -> bool {
+    for (int c = 0; c < nc; ++c) {
         const uint32_t s = C.ql % kRing;
         if (C.ql >= (uint32_t)kRing && !warp_wait(mbar_at(C.mb, kEmpty0 + s), C.ql / kRing - 1u)) return false;
         if (elect_one()) {
@@ -547,14 +552,23 @@ __device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, 
         }
         __syncwarp();
         C.ql++;
-        return true;
-    };
-    bool ok = true;
-    for (int c = 0; c < min(kRing, nc) && ok; ++c) ok = load(c);
-    for (int c = 0; c < nc && ok; ++c) {
+    }
+    return true;
+}
+
+// GEMM 1 of one tile into S buffer j, [S_re | S_im] = R' [C_re | C_im] with
+// the complex product stacked along N: per chunk six M128 N128 K16 MMAs (the
+// split operands' hi hi, hi lo and lo hi terms of R'_re [C_re | C_im] and
+// R'_im [-C_im | C_re]), issued as each ring stage lands.  The stage goes back
+// to the producer when its MMAs complete.
+__device__ __forceinline__ bool gemm1(Ctl &C, int nc, int j)
+{
+    const uint32_t id = idesc(kRows, 2 * kCols, 0);
+    const uint32_t s_acc = C.tmem + kS0 + 2 * kCols * j;   // [S_re | S_im]
+    const uint64_t ring0 = desc(C.ring, 128, 256);
+    for (int c = 0; c < nc; ++c) {
         const uint32_t s = C.qm % kRing;
-        ok = warp_wait(mbar_at(C.mb, kFull0 + s), C.qm / kRing);
-        if (!ok) break;
+        if (!warp_wait(mbar_at(C.mb, kFull0 + s), C.qm / kRing)) return false;
         // A: R' re hi, re lo, im hi, im lo; B: [C_re | C_im] and [-C_im | C_re] windows, hi and lo
         const uint64_t st = ring0 + ((uint64_t)(s * kStage) >> 4);
         const uint64_t arh = st, arl = st + (kA1 >> 4), aih = st + (2 * kA1 >> 4), ail = st + (3 * kA1 >> 4);
@@ -571,9 +585,7 @@ __device__ __forceinline__ bool gemm1(Ctl &C, const HoloDev &H, int rb, int cb, 
         }
         __syncwarp();
         C.qm++;
-        if (c >= 1 && c - 1 + kRing < nc) ok = load(c - 1 + kRing);
     }
-    if (!ok) return false;
     if (elect_one()) commit(mbar_at(C.mb, kSFull0 + j));   // covers this GEMM 1 and every MMA before it
     __syncwarp();
     return true;
@@ -643,13 +655,16 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
     return true;
 }
 
-// Every MMA of this warp done before tensor memory is freed, and its copies
-// landed before shared memory is; true when all ended in time.
-__device__ __forceinline__ bool drain(const Ctl &C)
+// Every MMA of an issuing warp done before tensor memory is freed, and every
+// copy of a warp landed before shared memory is; true when all ended in time.
+__device__ __forceinline__ bool drain(const Ctl &C, bool mmas)
 {
-    if (elect_one()) commit(mbar_at(C.mb, kDrain));
-    __syncwarp();
-    bool drained = warp_wait(mbar_at(C.mb, kDrain), 0u);
+    bool drained = true;
+    if (mmas) {
+        if (elect_one()) commit(mbar_at(C.mb, kDrain));
+        __syncwarp();
+        drained = warp_wait(mbar_at(C.mb, kDrain), 0u);
+    }
     for (uint32_t s = 0; s < (uint32_t)kRing; ++s) {
         const uint32_t loads = (C.ql + kRing - 1u - s) / kRing;   // chunks q < ql with q % kRing == s
         if (loads) drained &= warp_wait(mbar_at(C.mb, kFull0 + s), loads - 1u);
@@ -685,14 +700,40 @@ __device__ __noinline__ void control_gemm2(const SmemWs &m, const G2Info *g2, ui
         ok = gemm2(C, g);
         if (!ok) break;
     }
-    const bool drained = drain(C);
+    const bool drained = drain(C, true);
     if ((!ok || !drained) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
 
-// The GEMM 1 warp: takes work items, publishes them, and issues GEMM 1 of each.
+// The GEMM 1 warp: per published tile with products, GEMM 1 into S buffer j
+// as the producer's stages land; then it gives info slot j back.
+__device__ __noinline__ void control_gemm1(const SmemWs &m, const Info *info, uint32_t mb, uint32_t tmem,
+                                           unsigned *status)
+{
+    Ctl C = ctl_init(m, mb, tmem);
+    bool ok = true;
+    for (uint32_t k = 0;; ++k) {
+        const int j = k & 1;
+        ok = warp_wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u);
+        if (!ok) break;
+        const int done = info[j].done, empty = info[j].empty, N = info[j].H.N;
+        if (done) break;
+        if (!empty) {
+            fence_after();
+            ok = gemm1(C, nchunks(N), j);
+        }
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) arrive(mbar_at(mb, kSEmpty0 + j));
+        if (!ok) break;
+    }
+    const bool drained = drain(C, true);
+    if ((!ok || !drained) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
+}
+
+// The producer warp: takes work items, publishes them, and loads GEMM 1's
+// operand stages of each (running up to the ring's depth ahead of the MMAs).
 // The pop of the next item and the global loads of the item's slot and
 // descriptor are issued ahead of the waits they would otherwise follow.
-__device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
+__device__ __noinline__ void control_load(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
                                            int nslots, int total_tiles, unsigned *queue, const SmemWs &m,
                                            Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
 {
@@ -726,7 +767,8 @@ __device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, co
                 hw[i] = w < kHWords ? __ldg(src + w) : 0u;
             }
         }
-        // S buffer j and info slot j are free once the epilogue has read tile k - 2's
+        // S buffer j and info slot j are free once the epilogue and the GEMM 1
+        // warp are done with tile k - 2
         if (k >= 2 && ok) ok = warp_wait(mbar_at(mb, kSEmpty0 + j), (k >> 1) - 1u);
         fin = fin || !ok;
         bool empty = true;
@@ -754,14 +796,11 @@ __device__ __noinline__ void control_gemm1(const HoloDev *__restrict__ holos, co
         }
         __syncwarp();
         if (lane0) arrive(mbar_at(mb, kReady0 + j));
-        if (!empty && ok) {
-            fence_after();
-            ok = gemm1(C, *Hp, rb, cb, j);
-        }
+        if (!empty && ok) ok = load_gemm1(C, *Hp, rb, cb);
         if (fin || !ok) break;
         item = __shfl_sync(0xffffffffu, next, 0);
     }
-    const bool drained = drain(C);
+    const bool drained = drain(C, false);
     if ((!ok || !drained) && lane0) atomicOr(status, 1u);
 }
 
@@ -832,8 +871,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
         }
 
         // ---- epilogue 1: S -> u (GEMM 2's B operand), Phi and gray out.  S is
-        // released with u: the control warp reuses this S buffer only after
-        // u_full in any case.  A compressed pass reads the subset mask bits of
+        // released once u is written.  A compressed pass reads the subset mask bits of
         // the thread's columns first (a multiple of 16 columns from a multiple
         // of 16: within one word per 32), before the wait for S.
         uint32_t mword = 0xFFFFFFFFu;
@@ -907,7 +945,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                 // this chunk of u is in place: GEMM 2 takes its K-steps
                 fence_async_smem();
                 __syncwarp();
-                if (lane == 0) arrive(mbar_at(mb, xc == 0 ? kUHalf0 : kUHalf1));
+                if (lane == 0) arrive(mbar_at(mb, kUHalf0 + ((xs >> 4) & 1)));
             }
         }
         fence_before();
@@ -924,29 +962,49 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             // stores nothing): no divergent branch in the row loop
             const int nl = 32 * q + lane, n = sb * kSpotBlock + nl;
             const int4 cf = H.coef[min(n, N - 1)];
-            float vr = 0.f, vi = 0.f;
+            const int32_t tilt = cf.y, Gh = cf.z;
+            const float gl = __int_as_float(cf.w);
+            // R_n(y) along the rows by recurrence: its phase is quadratic in y,
+            // so R(y + 1) = R(y) D(y) and D(y + 1) = D(y) E with the constant
+            // E = e^{i (2 pi 2 Gh / 2^32 + 2 gl)}; R and D are evaluated directly
+            // every 8 rows (the product's rounding grows with the run length)
+            float es, ec;
+            sincos_fix(kFixRound + 2u * (uint32_t)Gh, fmaf(2.f, gl, -kTwoPiF), es, ec);
+            float vr0 = 0.f, vi0 = 0.f, vr1 = 0.f, vi1 = 0.f;
 #pragma unroll 1
             for (int y16 = 0; y16 < G::kRowsPer; y16 += 16) {
                 const int ys = G::kRowsPer * h + y16;
                 float zr[16], zi[16];
                 ld16(z_re + lanes + ys, zr);
                 ld16(z_im + lanes + ys, zi);
-                float4 r4[8];
+                float2 r[16];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const float2 a = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e - half, kFixRound, 1.f);
-                    const float2 b = spot_factor(cf.y, cf.z, __int_as_float(cf.w), y0 + ys + 2 * e + 1 - half, kFixRound, 1.f);
-                    r4[e] = make_float4(a.x, a.y, b.x, b.y);
+                for (int b = 0; b < 2; ++b) {
+                    const int u0 = y0 + ys + 8 * b - half, du = 2 * u0 + 1;
+                    float2 pr = spot_factor(tilt, Gh, gl, u0, kFixRound, 1.f);
+                    float ds, dc;
+                    sincos_fix(kFixRound + (uint32_t)tilt + (uint32_t)Gh * (uint32_t)du, fmaf(gl, (float)du, -kTwoPiF),
+                               ds, dc);
+                    float2 d = make_float2(dc, ds);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        r[8 * b + k] = pr;
+                        if (k < 7) {
+                            pr = make_float2(fmaf(pr.x, d.x, -pr.y * d.y), fmaf(pr.x, d.y, pr.y * d.x));
+                            d = make_float2(fmaf(d.x, ec, -d.y * es), fmaf(d.x, es, d.y * ec));
+                        }
+                    }
                 }
                 ld_wait();
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    vr = fmaf(r4[e].x, zr[2 * e], fmaf(r4[e].y, zi[2 * e], vr));
-                    vi = fmaf(r4[e].x, zi[2 * e], fmaf(-r4[e].y, zr[2 * e], vi));
-                    vr = fmaf(r4[e].z, zr[2 * e + 1], fmaf(r4[e].w, zi[2 * e + 1], vr));
-                    vi = fmaf(r4[e].z, zi[2 * e + 1], fmaf(-r4[e].w, zr[2 * e + 1], vi));
+                    vr0 = fmaf(r[2 * e].x, zr[2 * e], fmaf(r[2 * e].y, zi[2 * e], vr0));
+                    vi0 = fmaf(r[2 * e].x, zi[2 * e], fmaf(-r[2 * e].y, zr[2 * e], vi0));
+                    vr1 = fmaf(r[2 * e + 1].x, zr[2 * e + 1], fmaf(r[2 * e + 1].y, zi[2 * e + 1], vr1));
+                    vi1 = fmaf(r[2 * e + 1].x, zi[2 * e + 1], fmaf(-r[2 * e + 1].y, zr[2 * e + 1], vi1));
                 }
             }
+            float vr = vr0 + vr1, vi = vi0 + vi1;
             fence_before();
             __syncwarp();
             if (lane == 0) arrive(mbar_at(mb, kZEmpty));
@@ -989,9 +1047,12 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     if (tid == 0) {
         for (int b = 0; b < kBarsWs; ++b) {
             // the epilogue's releases arrive once per warp
-            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1 || b == kUHalf0 || b == kUHalf1 || b == kZEmpty) ? W
-                                 : b == kDrain                                                  ? 2
-                                                                                                : 1;
+            // S buffers and info slots go back from the epilogue and the GEMM 1 warp
+            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1) ? W + 1
+                                 : b == kZEmpty                               ? W
+                                 : (b == kUHalf0 || b == kUHalf1)             ? Cfg<W>::kUHalfArrivals
+                                 : b == kDrain                                             ? 2
+                                                                                           : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::saddr(&s_mbar[b])), "r"(cnt));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1008,8 +1069,10 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     const SmemWs m = carve_ws(smem, W / 4);
     unsigned *status = queue + 2;
     if (warp == W) {
-        control_gemm1(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
+        control_load(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
     } else if (warp == W + 1) {
+        control_gemm1(m, s_info, mb, s_tmem, status);
+    } else if (warp == W + 2) {
         control_gemm2(m, &s_g2, mb, s_tmem, status);
     } else {
         epilogue<W, F16>(holos, slots, m, s_info, &s_g2, mb, s_tmem, status);
@@ -1094,11 +1157,14 @@ static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, in
     return cudaGetLastError();
 }
 
+// epilogue warps of the warp-specialised kernel
+constexpr int kWsWarps = 8;
+
 int full_tc_tiles(int P) { return tc::tiles(P); }
 
 int full_tc_max_grid(int variant, int maxN, int sm_count)
 {
-    return variant == kFullTcWs ? tcws_max_grid<8>(maxN, sm_count) : 0;
+    return variant == kFullTcWs ? tcws_max_grid<kWsWarps>(maxN, sm_count) : 0;
 }
 
 void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs)
@@ -1131,14 +1197,14 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
 cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
                              unsigned *queue, int grid, int f16, cudaStream_t s)
 {
-    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, true, f16, s);
+    return tcws_launch<kWsWarps>(holos, slots, nslots, total_tiles, maxN, queue, grid, true, f16, s);
 }
 
 cudaError_t launch_full_tc(int variant, const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
                            int maxN, unsigned *queue, int grid, cudaStream_t s)
 {
     if (variant != kFullTcWs) return cudaErrorInvalidValue;
-    return tcws_launch<8>(holos, slots, nslots, total_tiles, maxN, queue, grid, false, 0, s);
+    return tcws_launch<kWsWarps>(holos, slots, nslots, total_tiles, maxN, queue, grid, false, 0, s);
 }
 
 }  // namespace cswgs
