@@ -42,6 +42,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "tile.cuh"
 
@@ -887,66 +888,93 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             const uint32_t s_re = tmem + kS0 + 2 * kCols * j, s_im = s_re + kCols;
             const int row = 32 * q + lane, gy = y0 + row, yq = gy - half;
             const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
-            const bool row_in = gy < P, square = H.aperture == 0, gauss = H.kA != 0.f;
-#pragma unroll 1
-            for (int xc = 0; xc < G::kColsPer; xc += 16) {
-                const int xs = G::kColsPer * h + xc;
-                // compressed pass: only the pixels of S_j carry u (the rest add nothing to Eq. 3's sum)
-                const uint32_t bits = (mword >> xc) & 0xFFFFu;
-                float sr[16], si[16], o[16];
-                ld16(s_re + lanes + xs, sr);
-                ld16(s_im + lanes + xs, si);
-                ld_wait();
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    float2 u[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        // branch-free: the lanes are rows, so a per-pixel branch
-                        // (subset membership, the pupil edge) would diverge
-                        const int jj = 8 * g + e;
-                        const int gx = x0 + xs + jj, xq = gx - half;
-                        const int rho2 = xq * xq + yq2;
-                        const bool valid = row_in & (gx < P) & (square | (rho2 <= R2)) & (((bits >> jj) & 1u) != 0u);
-                        const float a = sr[jj], b = si[jj];
-                        const float n2 = a * a + b * b;
-                        if (pass == kPassFinal) {
-                            float ph = atan2f(b, a);
-                            ph = ph < 0.f ? ph + kTwoPiF : ph;
-                            o[jj] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
-                        }
-                        const float amp = gauss ? exp2f(-H.kA * (float)rho2) : 1.f;   // Eq. 3's A
-                        const bool lit = n2 > 0.f;
-                        const float rs = rsqrtf(n2) * amp;
-                        const float ur = lit ? a * rs : amp, ui = lit ? b * rs : 0.f;   // S = 0: phase 0
-                        u[e] = make_float2(valid ? ur : 0.f, valid ? ui : 0.f);
-                    }
-                    if (F16) put8h(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
-                    else put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+            // the row's pixels are columns xl..xr: the grid's, within the round
+            // pupil (|x - half|^2 + yq^2 <= half^2) unless the aperture is square
+            int xl = 0, xr = gy < P ? P - 1 : -1;
+            if (H.aperture != 0) {
+                const int D = R2 - yq2;
+                int w = -1;
+                if (D >= 0) {
+                    w = (int)sqrtf((float)D);   // within 1 of floor(sqrt(D))
+                    if ((w + 1) * (w + 1) <= D) ++w;
+                    if (w * w > D) --w;
                 }
-                if (pass == kPassFinal && gy < P) {
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        const int col = x0 + xs + 4 * g;
-                        if (col >= P) break;
-                        if (H.phase_out) {
-                            float *dst = H.phase_out + (size_t)gy * P + col;
-                            if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-                                *reinterpret_cast<float4 *>(dst) =
-                                    make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
-                            } else {
-                                for (int e = 0; e < 4; ++e)
-                                    if (col + e < P) dst[e] = o[4 * g + e];
-                            }
-                        }
-                        if (H.slm) write_gray4(H, gy, col, o + 4 * g);
-                    }
-                }
-                // this chunk of u is in place: GEMM 2 takes its K-steps
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) arrive(mbar_at(mb, kUHalf0 + ((xs >> 4) & 1)));
+                xl = max(xl, half - w);
+                xr = min(xr, half + w);
             }
+            const float kA = H.kA;
+            // epilogue 1 of the thread's chunks, with the Gaussian beam's
+            // amplitude or the uniform one (a uniform branch outside the loop)
+            auto chunks = [&](auto gauss_tag) {
+                constexpr bool kGauss = decltype(gauss_tag)::value;
+#pragma unroll 1
+                for (int xc = 0; xc < G::kColsPer; xc += 16) {
+                    const int xs = G::kColsPer * h + xc, gx0 = x0 + xs;
+                    // the chunk's pixels that carry u: in the row's span and, in a
+                    // compressed pass, in S_j (the rest add nothing to Eq. 3's sum)
+                    const int lo = max(xl - gx0, 0), hi = min(xr - gx0, 15);
+                    uint32_t bits = 0u;
+                    if (lo <= hi) bits = (0xFFFFu >> (15 - hi + lo)) << lo;
+                    bits &= mword >> xc;
+                    float sr[16], si[16], o[16];
+                    ld16(s_re + lanes + xs, sr);
+                    ld16(s_im + lanes + xs, si);
+                    ld_wait();
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        float2 u[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            // branch-free: the lanes are rows, so a per-pixel branch
+                            // (subset membership, the pupil edge) would diverge
+                            const int jj = 8 * g + e;
+                            const bool valid = ((bits >> jj) & 1u) != 0u;
+                            const float a = sr[jj], b = si[jj];
+                            const float n2 = a * a + b * b;
+                            if (pass == kPassFinal) {
+                                float ph = atan2f(b, a);
+                                ph = ph < 0.f ? ph + kTwoPiF : ph;
+                                o[jj] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
+                            }
+                            float amp = 1.f;   // Eq. 3's A
+                            if constexpr (kGauss) {
+                                const int xq = gx0 + jj - half;
+                                amp = exp2f(-kA * (float)(xq * xq + yq2));
+                            }
+                            const bool lit = n2 > 0.f;
+                            const float rs = rsqrtf(n2) * amp;
+                            const float ur = lit ? a * rs : amp, ui = lit ? b * rs : 0.f;   // S = 0: phase 0
+                            u[e] = make_float2(valid ? ur : 0.f, valid ? ui : 0.f);
+                        }
+                        if (F16) put8h(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+                        else put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+                    }
+                    if (pass == kPassFinal && gy < P) {
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            const int col = gx0 + 4 * g;
+                            if (col >= P) break;
+                            if (H.phase_out) {
+                                float *dst = H.phase_out + (size_t)gy * P + col;
+                                if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                                    *reinterpret_cast<float4 *>(dst) =
+                                        make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
+                                } else {
+                                    for (int e = 0; e < 4; ++e)
+                                        if (col + e < P) dst[e] = o[4 * g + e];
+                                }
+                            }
+                            if (H.slm) write_gray4(H, gy, col, o + 4 * g);
+                        }
+                    }
+                    // this chunk of u is in place: GEMM 2 takes its K-steps
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) arrive(mbar_at(mb, kUHalf0 + ((xs >> 4) & 1)));
+                }
+            };
+            if (kA != 0.f) chunks(std::true_type{});
+            else chunks(std::false_type{});
         }
         fence_before();
         __syncwarp();
