@@ -146,6 +146,17 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void ld8(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
 __device__ __forceinline__ void ld16(uint32_t taddr, float *v)
 {
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 //   s_empty[2]        the epilogue has read that S buffer and info slot, and the
 //                     GEMM 1 warp that info slot
 //   g2_info           epilogue -> GEMM 2 warp: the tile's C blocks (or done)
-//   u_half[2]         the epilogue has written half of u (GEMM 2 starts on it)
+//   u_step[4]         the epilogue has written u's columns of one K-step of GEMM 2
 //   cs_full           GEMM 2's C block has landed
 //   z_full            GEMM 2 of a spot block is done (C block buffer free)
 //   z_empty           the epilogue has read Z
@@ -400,9 +411,8 @@ enum Bar {
     kEmpty0 = kFull0 + kRing,
     kSFull0 = kEmpty0 + kRing,
     kSEmpty0 = kSFull0 + 2,
-    kUHalf0 = kSEmpty0 + 2,   // u's first 16-column chunk of every thread: columns 0-15 and 32-47
-    kUHalf1,                  // the second: columns 16-31 and 48-63
-    kCsFull,
+    kUStep0 = kSEmpty0 + 2,   // u's columns of GEMM 2's K-step 0 .. 3 are written
+    kCsFull = kUStep0 + kCols / 16,
     kZFull,
     kZEmpty,
     kG2Info,    // the epilogue has published the next tile's GEMM 2 operands
@@ -435,10 +445,9 @@ struct Cfg {
     static constexpr int kColsPer = kCols / kGroups;  // epilogue 1: columns per thread
     static constexpr int kRowsPer = kRows / kGroups;  // epilogue 2: rows per thread
     static_assert(W % 4 == 0 && kColsPer % 16 == 0 && kRowsPer % 16 == 0, "epilogue split");
-    static_assert(kColsPer <= 32, "a thread's columns lie in one mask word");
-    // u goes to GEMM 2 in two halves, K-steps 0, 2 and 1, 3: each 16-column
-    // chunk of u signals the half of its K-step, once per warp
-    static constexpr uint32_t kUHalfArrivals = W * (kColsPer / 16) / 2;
+    // epilogue 1 writes u K-step by K-step (each thread 8 of its 16 columns),
+    // so that GEMM 2 follows one K-step behind
+    static_assert(kGroups == 2, "two epilogue warps per TMEM lane quadrant");
 };
 
 // Dynamic shared memory: the partial sums of epilogue 2, the GEMM 1 ring,
@@ -615,17 +624,14 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
         }
         __syncwarp();
         C.ncs++;
-        if (sb == 0 && !warp_wait(mbar_at(C.mb, kUHalf0), C.nu)) return false;
         // the epilogue has read the previous Z
         if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZEmpty), C.nz - 1u)) return false;
         if (!warp_wait(mbar_at(C.mb, kCsFull), C.ncs - 1u)) return false;
         fence_after();
-        // on a tile's first spot block, the K-steps of u's first half (0, 2)
-        // go before those of the second (1, 3), which wait for it
-        for (int i = 0; i < kCols / 16; ++i) {
-            const int ks = sb == 0 ? (i < 2 ? 2 * i : 2 * i - 3) : i;
-            if (sb == 0 && i == 2) {
-                if (!warp_wait(mbar_at(C.mb, kUHalf1), C.nu)) return false;
+        // on a tile's first spot block, each K-step waits for its columns of u
+        for (int ks = 0; ks < kCols / 16; ++ks) {
+            if (sb == 0) {
+                if (!warp_wait(mbar_at(C.mb, kUStep0 + ks), C.nu)) return false;
                 fence_after();
             }
             if (f16) {
@@ -633,7 +639,7 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
                 const uint64_t cr = cs0 + ((uint64_t)(ks * 256) >> 4), ci = cs0 + ((uint64_t)(kCs + ks * 256) >> 4);
                 const uint64_t ur = u0 + ((uint64_t)(ks * 256) >> 4), ui = u0 + ((uint64_t)(kU + ks * 256) >> 4);
                 if (elect_one()) {
-                    const uint32_t acc = i > 0 ? 1u : 0u;
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
                     mma(z_re, cr, ur, id, acc);
                     mma(z_re, ci, ui, id, 1u);
                     mma(z_im, cr, ui, id, acc);
@@ -645,7 +651,7 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
                     a[q] = cs0 + ((uint64_t)(q * kCs + ks * 256) >> 4);
                     b[q] = u0 + ((uint64_t)(q * kU + ks * 256) >> 4);
                 }
-                if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, i > 0 ? 1u : 0u, 1);
+                if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, ks > 0 ? 1u : 0u, 1);
             }
         }
         if (sb == 0) C.nu++;
@@ -872,13 +878,18 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
         }
 
         // ---- epilogue 1: S -> u (GEMM 2's B operand), Phi and gray out.  S is
-        // released once u is written.  A compressed pass reads the subset mask bits of
-        // the thread's columns first (a multiple of 16 columns from a multiple
-        // of 16: within one word per 32), before the wait for S.
-        uint32_t mword = 0xFFFFFFFFu;
+        // released once u is written.  A compressed pass reads the subset mask
+        // bits of the tile's columns first, before the wait for S.
+        uint64_t mword = ~0ull;
         if (pass == kPassSubset) {
-            const int gy = y0 + 32 * q + lane, c0 = x0 + G::kColsPer * h;
-            mword = (gy < P && c0 < P) ? __ldg(H.mask + (size_t)gy * H.mask_words + (c0 >> 5)) >> (c0 & 31) : 0u;
+            // the tile's 64 columns: two words (x0 is a multiple of 64)
+            const int gy = y0 + 32 * q + lane, w0 = x0 >> 5;
+            if (gy < P) {
+                const uint32_t *mrow = H.mask + (size_t)gy * H.mask_words;
+                mword = (uint64_t)__ldg(mrow + w0) | (w0 + 1 < H.mask_words ? (uint64_t)__ldg(mrow + w0 + 1) << 32 : 0ull);
+            } else {
+                mword = 0ull;
+            }
         }
         n_s += 1u << (16 * j);
         ok = group_and<W>(wait_newest(mbar_at(mb, kSFull0 + j), (n_s >> (16 * j)) & 0xFFFFu));
@@ -908,26 +919,27 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             auto chunks = [&](auto gauss_tag) {
                 constexpr bool kGauss = decltype(gauss_tag)::value;
 #pragma unroll 1
-                for (int xc = 0; xc < G::kColsPer; xc += 16) {
-                    const int xs = G::kColsPer * h + xc, gx0 = x0 + xs;
-                    // the chunk's pixels that carry u: in the row's span and, in a
+                for (int ks = 0; ks < kCols / 16; ++ks) {
+                    // the thread's 8 columns of K-step ks
+                    const int xs = 16 * ks + 8 * h, gx0 = x0 + xs;
+                    // the pixels that carry u: in the row's span and, in a
                     // compressed pass, in S_j (the rest add nothing to Eq. 3's sum)
-                    const int lo = max(xl - gx0, 0), hi = min(xr - gx0, 15);
+                    const int lo = max(xl - gx0, 0), hi = min(xr - gx0, 7);
                     uint32_t bits = 0u;
-                    if (lo <= hi) bits = (0xFFFFu >> (15 - hi + lo)) << lo;
-                    bits &= mword >> xc;
-                    float sr[16], si[16], o[16];
-                    ld16(s_re + lanes + xs, sr);
-                    ld16(s_im + lanes + xs, si);
+                    if (lo <= hi) bits = (0xFFu >> (7 - hi + lo)) << lo;
+                    bits &= (uint32_t)(mword >> xs);
+                    float sr[8], si[8], o[8];
+                    ld8(s_re + lanes + xs, sr);
+                    ld8(s_im + lanes + xs, si);
                     ld_wait();
-#pragma unroll
-                    for (int g = 0; g < 2; ++g) {
+                    {
+                        constexpr int g = 0;
                         float2 u[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             // branch-free: the lanes are rows, so a per-pixel branch
                             // (subset membership, the pupil edge) would diverge
-                            const int jj = 8 * g + e;
+                            const int jj = e;
                             const bool valid = ((bits >> jj) & 1u) != 0u;
                             const float a = sr[jj], b = si[jj];
                             const float n2 = a * a + b * b;
@@ -951,7 +963,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                     }
                     if (pass == kPassFinal && gy < P) {
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) {
+                        for (int g = 0; g < 2; ++g) {
                             const int col = gx0 + 4 * g;
                             if (col >= P) break;
                             if (H.phase_out) {
@@ -967,10 +979,10 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                             if (H.slm) write_gray4(H, gy, col, o + 4 * g);
                         }
                     }
-                    // this chunk of u is in place: GEMM 2 takes its K-steps
+                    // this K-step's columns of u are in place
                     fence_async_smem();
                     __syncwarp();
-                    if (lane == 0) arrive(mbar_at(mb, kUHalf0 + ((xs >> 4) & 1)));
+                    if (lane == 0) arrive(mbar_at(mb, kUStep0 + ks));
                 }
             };
             if (kA != 0.f) chunks(std::true_type{});
@@ -1076,9 +1088,8 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
         for (int b = 0; b < kBarsWs; ++b) {
             // the epilogue's releases arrive once per warp
             // S buffers and info slots go back from the epilogue and the GEMM 1 warp
-            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1) ? W + 1
-                                 : b == kZEmpty                               ? W
-                                 : (b == kUHalf0 || b == kUHalf1)             ? Cfg<W>::kUHalfArrivals
+            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1)          ? W + 1
+                                 : (b == kZEmpty || (b >= kUStep0 && b < kCsFull)) ? W
                                  : b == kDrain                                             ? 2
                                                                                            : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::saddr(&s_mbar[b])), "r"(cnt));
