@@ -73,7 +73,8 @@ def measured_traffic(args, tile):
 
 
 # full_threads markers of the tensor-core kernels: kernel name, threads per block
-TC_KERNELS = {2: ("iter_full_tcws_kernel (warp-specialised: 8 epilogue warps + 1 control warp)", 288)}
+TC_KERNELS = {2: ("iter_full_tcws_kernel (warp-specialised: 8 epilogue warps, a producer warp, a GEMM 1 warp "
+                   "and a GEMM 2 warp)", 352)}
 
 
 # threads marker of compressed iterations on the warp-specialised tensor-core
@@ -110,7 +111,7 @@ def subset_roofline(tile, pairs_sub_launch, n_sub, sub_ms, full_ms, sm_count, ma
                           "outside the subset (%d per step, %.1f%% of the step)" % (n_sub, share),
                 "issued_tensor_flops_per_algorithmic": 3.0 * args.P * args.P / max(1, Mp),
                 "ms_per_launch": sub_ms / max(1, n_sub),
-                "tile": {"threads": 288, "blocks": tile["blocks"], "pixels": "128 rows x 64 columns"}}
+                "tile": {"threads": TC_KERNELS[2][1], "blocks": tile["blocks"], "pixels": "128 rows x 64 columns"}}
     sfu_peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9           # G sin-or-cos/s
     ach = 2.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e9 if n_sub else 0.0
     return {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": ach, "peak": sfu_peak,

@@ -69,18 +69,44 @@ __device__ __forceinline__ void feistel_round(uint32_t &L, uint32_t &R, uint32_t
     R = nr;
 }
 
+// Exact division by a divisor d fixed for many dividends: with the reciprocal
+// m = floor((2^32 - 1) / d), umulhi(x, m) is floor(x / d) or one less for
+// every 32-bit x (the product undershoots x / d by less than x / 2^32 < 1), and
+// one comparison of the remainder settles it.
+struct UDiv {
+    uint32_t d, m;
+};
+
+__host__ __device__ __forceinline__ UDiv udiv_of(uint32_t d) { return UDiv{d, 0xFFFFFFFFu / d}; }
+
+__device__ __forceinline__ uint32_t udiv(uint32_t x, const UDiv &v, uint32_t &r)
+{
+    uint32_t q = __umulhi(x, v.m);
+    r = x - q * v.d;
+    if (r >= v.d) {
+        ++q;
+        r -= v.d;
+    }
+    return q;
+}
+
 // Keyed bijection of [0, a b): k = L b + R with L in [0, a), R in [0, b);
 // four rounds whose moduli alternate a, b, a, b (each round swaps the two
 // halves' ranges); result L b + R.
+__device__ __forceinline__ uint32_t permute_rect(uint32_t k, uint32_t a, const UDiv &b, const SubsetKeys &K)
+{
+    uint32_t R;
+    uint32_t L = udiv(k, b, R);
+    feistel_round(L, R, K.k0, a);
+    feistel_round(L, R, K.k1, b.d);
+    feistel_round(L, R, K.k2, a);
+    feistel_round(L, R, K.k3, b.d);
+    return L * b.d + R;
+}
+
 __device__ __forceinline__ uint32_t permute_rect(uint32_t k, uint32_t a, uint32_t b, const SubsetKeys &K)
 {
-    uint32_t L = k / b;
-    uint32_t R = k - L * b;
-    feistel_round(L, R, K.k0, a);
-    feistel_round(L, R, K.k1, b);
-    feistel_round(L, R, K.k2, a);
-    feistel_round(L, R, K.k3, b);
-    return L * b + R;
+    return permute_rect(k, a, udiv_of(b), K);
 }
 
 // pi_{seed,j}(k): keyed bijection of [0, P^2), the square grid's subset order.
@@ -98,11 +124,11 @@ __device__ __forceinline__ uint32_t permute(uint32_t k, uint32_t P, const Subset
 // walk from k < D meets at most a b - D values >= D before it returns below
 // D, so the loop bound never cuts a walk short; the final clamp only keeps a
 // corrupted input in range.
-__device__ __forceinline__ uint32_t permute_domain(uint32_t k, uint32_t D, uint32_t a, uint32_t b,
+__device__ __forceinline__ uint32_t permute_domain(uint32_t k, uint32_t D, uint32_t a, const UDiv &b,
                                                    const SubsetKeys &K)
 {
     uint32_t y = permute_rect(k, a, b, K);
-    const uint32_t extra = a * b - D;
+    const uint32_t extra = a * b.d - D;
     for (uint32_t s = 0; y >= D && s < extra; ++s) y = permute_rect(y, a, b, K);
     return y < D ? y : 0u;
 }

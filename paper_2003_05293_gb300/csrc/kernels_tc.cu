@@ -338,9 +338,11 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
     if (!H.rwtab) return;
     if (sl.pass == kPassSubset && H.mask) {
         const SubsetDraw d = subset_draw(H, sl.j);
+        const UDiv dP = udiv_of((uint32_t)H.P);
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H.Mp; k += gridDim.x * blockDim.x) {
             const uint32_t m = subset_pixel(H, d, (uint32_t)k);
-            const uint32_t r = m / (uint32_t)H.P, c = m - r * (uint32_t)H.P;
+            uint32_t c;
+            const uint32_t r = udiv(m, dP, c);
             atomicOr(H.mask + (size_t)r * H.mask_words + (c >> 5), 1u << (c & 31));
         }
     }

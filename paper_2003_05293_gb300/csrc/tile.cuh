@@ -247,6 +247,7 @@ __device__ __forceinline__ void finish_tile(const HoloDev &H, const LaunchSlot &
 struct SubsetDraw {
     SubsetKeys K;
     uint32_t off;
+    UDiv fb;   // the permutation rectangle's b, as a divisor
 };
 
 __device__ __forceinline__ SubsetDraw subset_draw(const HoloDev &H, int j)
@@ -254,6 +255,7 @@ __device__ __forceinline__ SubsetDraw subset_draw(const HoloDev &H, int j)
     SubsetDraw d;
     d.K = subset_keys(H.seed, H.windows ? 0 : j);
     d.off = 0u;
+    d.fb = udiv_of(H.fb);
     if (H.windows) {
         const int64_t D = H.D;
         int64_t t = (((int64_t)(j - 1) % D) * ((int64_t)H.Mp % D)) % D;
@@ -283,7 +285,7 @@ __device__ __forceinline__ uint32_t subset_pixel(const HoloDev &H, const SubsetD
 {
     uint32_t kk = k + d.off;
     kk = kk >= (uint32_t)H.D ? kk - (uint32_t)H.D : kk;
-    return pupil_pixel(H, permute_domain(kk, (uint32_t)H.D, H.fa, H.fb, d.K));
+    return pupil_pixel(H, permute_domain(kk, (uint32_t)H.D, H.fa, d.fb, d.K));
 }
 
 // Pupil amplitude A = exp(-rho^2 / waist^2) = exp2(-kA rho^2) (Eq. 3's A;
