@@ -373,32 +373,34 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 // ----------------------------------------------------------- warp roles --
 // Tiles are pipelined by warp roles: a producer warp (takes the work items and
 // loads GEMM 1's operand stages), a GEMM 1 warp, a GEMM 2 warp (one elected
-// lane of each issues its bulk copies and MMAs) and W epilogue warps.  The
-// producer runs ahead of the GEMM 1 warp by the ring's depth: a tcgen05.mma
-// issue waits for the tensor pipe, so copies issued from the MMA warp would
-// start one stage late.
+// lane of each issues its bulk copies and MMAs), 4 u warps (epilogue 1) and 4
+// V warps (epilogue 2).  The producer runs ahead of the GEMM 1 warp by the
+// ring's depth: a tcgen05.mma issue waits for the tensor pipe, so copies
+// issued from the MMA warp would start one stage late.
 // Tensor memory holds two S buffers (columns 256..383 and 384..511; tile k
-// uses buffer k & 1) and Z (columns 0..255).  GEMM 1 runs ahead into
-// the next tile's back-propagation while the epilogue warps turn S into u; the
-// GEMM 2 warp streams the tile's C block in meanwhile and issues GEMM 2 as
-// soon as u is ready; the epilogue warps run epilogue 1 and epilogue 2 of each
-// tile in order.  The per-hologram tails (Eqs. 4-6, or the metrics) run in a
-// small kernel right after the launch, so tiles neither fence nor count
-// arrivals.
+// uses buffer k & 1) and Z (columns 0..255).  GEMM 1 runs ahead into the next
+// tile's back-propagation while the u warps turn S into u; the GEMM 2 warp
+// streams the tile's C block in meanwhile and follows the u warps K-step by
+// K-step; the V warps reduce Z of tile k while the u warps already work on
+// tile k + 1 (the next GEMM 2 waits for both).  The per-hologram tails (Eqs.
+// 4-6, or the metrics) run in a small kernel right after the launch, so tiles
+// neither fence nor count arrivals.
 // Hand-overs, all mbarriers:
-//   ready[2]          producer -> GEMM 1 warp, epilogue: work item k in info slot k & 1
+//   ready[2]          producer -> GEMM 1, u and V warps: work item k in info slot k & 1
 //   full[r], empty[r] GEMM 1 operand ring: copies landed / MMAs done
 //   s_full[2]         GEMM 1 of the tile in that S buffer is done
-//   s_empty[2]        the epilogue has read that S buffer and info slot, and the
-//                     GEMM 1 warp that info slot
-//   g2_info           epilogue -> GEMM 2 warp: the tile's C blocks (or done)
-//   u_step[4]         the epilogue has written u's columns of one K-step of GEMM 2
+//   s_empty[2]        the u warps have read that S buffer and info slot, the V and
+//                     GEMM 1 warps that info slot
+//   g2_info           u warps -> GEMM 2 warp: the tile's C blocks (or done)
+//   u_step[4]         the u warps have written u's columns of one K-step of GEMM 2
 //   cs_full           GEMM 2's C block has landed
 //   z_full            GEMM 2 of a spot block is done (C block buffer free)
-//   z_empty           the epilogue has read Z
+//   z_empty           the V warps have read Z
+//   g2_done           GEMM 2 of a tile is done: u and the operand slot are free
+//                     (one phase per tile, so that the u warps, which skip the
+//                     spot blocks, never wait two phases ahead)
 //   drain             both issuing warps' last commits, before tensor memory is freed
-// u is free for the next tile once the epilogue has seen z_full of a tile's
-// last spot block, which it does before it writes the next u.  Every wait is
+// Every wait is
 // bounded; a timeout ends the loop of the side that saw it and sets the
 // status word, and the other side's waits then run out in turn.
 namespace ws {
@@ -417,61 +419,58 @@ enum Bar {
     kCsFull = kUStep0 + kCols / 16,
     kZFull,
     kZEmpty,
-    kG2Info,    // the epilogue has published the next tile's GEMM 2 operands
+    kG2Info,    // the u warps have published the next tile's GEMM 2 operands
+    kG2Done,    // GEMM 2 of a tile (its last spot block) is done
     kDrain,     // both issuing warps' last commits (2 arrivals)
     kBarsWs
 };
 
-// The GEMM 2 warp's work item, published by the epilogue warps when they take
-// up a tile with products (a single slot: the next one is written only after
-// that tile's GEMM 2 has been issued and waited for).
+// The GEMM 2 warp's work item, published by the u warps when they take up a
+// tile with products (a single slot: the next one is written only after that
+// tile's GEMM 2 is done).
 struct G2Info {
     const unsigned char *cstab;   // GEMM 2's C blocks in the launch's format
     int nsb, cb, done, f16;
 };
 
 // A published work item: the tile, and copies of its launch slot and its
-// hologram's descriptor (staged by the producer warp so that the epilogue
-// warps read them from shared memory).
+// hologram's descriptor (staged by the producer warp so that the other warps
+// read them from shared memory).
 struct Info {
     int item, empty, done, pad;
     LaunchSlot sl;
     HoloDev H;
 };
 
+// The epilogue warps: 4 u warps (epilogue 1, warps 0 .. 3) and 4 V warps
+// (epilogue 2, warps 4 .. 7), each group one warp per TMEM lane quadrant, each
+// with its own named barrier.
+constexpr int kUWarps = 4, kVWarps = 4;
+constexpr int kBarU = 1, kBarV = 2;
+
 template <int W>
 struct Cfg {
+    static_assert(W == kUWarps + kVWarps, "epilogue warps: the u and the V group");
     static constexpr int kEpi = 32 * W;               // epilogue threads
     static constexpr int kThreads = kEpi + 96;        // and the producer, GEMM 1 and GEMM 2 warps
-    static constexpr int kGroups = W / 4;             // epilogue warps per TMEM lane quadrant
-    static constexpr int kColsPer = kCols / kGroups;  // epilogue 1: columns per thread
-    static constexpr int kRowsPer = kRows / kGroups;  // epilogue 2: rows per thread
-    static_assert(W % 4 == 0 && kColsPer % 16 == 0 && kRowsPer % 16 == 0, "epilogue split");
-    // epilogue 1 writes u K-step by K-step (each thread 8 of its 16 columns),
-    // so that GEMM 2 follows one K-step behind
-    static_assert(kGroups == 2, "two epilogue warps per TMEM lane quadrant");
 };
 
-// Dynamic shared memory: the partial sums of epilogue 2, the GEMM 1 ring,
-// GEMM 2's C block and u (and 128 bytes to align the base; the no-swizzle
-// layouts and the bulk copies need 16).
-__host__ __device__ constexpr size_t smem_bytes_ws(int groups)
+// Dynamic shared memory: the GEMM 1 ring, GEMM 2's C block and u (and 128
+// bytes to align the base; the no-swizzle layouts and the bulk copies need 16).
+__host__ __device__ constexpr size_t smem_bytes_ws()
 {
-    return 128 + (size_t)(groups - 1) * kSpotBlock * sizeof(float2) + (size_t)kRing * kStage + 4 * (size_t)kCs +
-           4 * (size_t)kU;
+    return 128 + (size_t)kRing * kStage + 4 * (size_t)kCs + 4 * (size_t)kU;
 }
 
 struct SmemWs {
-    float2 *vh;
     unsigned char *ring, *cs, *u;
 };
 
-__device__ __forceinline__ SmemWs carve_ws(unsigned char *raw, int groups)
+__device__ __forceinline__ SmemWs carve_ws(unsigned char *raw)
 {
     unsigned char *b = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~(uintptr_t)127);
     SmemWs m;
-    m.vh = reinterpret_cast<float2 *>(b);
-    m.ring = b + (size_t)(groups - 1) * kSpotBlock * sizeof(float2);
+    m.ring = b;
     m.cs = m.ring + kRing * kStage;
     m.u = m.cs + 4 * kCs;
     return m;
@@ -484,19 +483,14 @@ __device__ __forceinline__ void arrive(uint32_t mbar)
 
 __device__ __forceinline__ bool wait_newest(uint32_t mbar, uint32_t given) { return wait(mbar, (given - 1u) & 1u); }
 
-// Named barrier 1 joins the epilogue warps only.
-template <int W>
-__device__ __forceinline__ void group_sync()
-{
-    asm volatile("bar.sync 1, %0;" :: "n"(Cfg<W>::kEpi) : "memory");
-}
-
-template <int W>
+// A group's vote over named barrier Id (Threads threads): true when every
+// thread's p is.
+template <int Id, int Threads>
 __device__ __forceinline__ bool group_and(bool p)
 {
     uint32_t r;
-    asm volatile("{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, 1, %2, pin;\n"
-                 " selp.u32 %0, 1, 0, pout;\n}\n" : "=r"(r) : "r"((uint32_t)p), "n"(Cfg<W>::kEpi) : "memory");
+    asm volatile("{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, %2, %3, pin;\n"
+                 " selp.u32 %0, 1, 0, pout;\n}\n" : "=r"(r) : "r"((uint32_t)p), "n"(Id), "n"(Threads) : "memory");
     return r != 0;
 }
 
@@ -657,7 +651,10 @@ __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
             }
         }
         if (sb == 0) C.nu++;
-        if (elect_one()) commit(mbar_at(C.mb, kZFull));
+        if (elect_one()) {
+            commit(mbar_at(C.mb, kZFull));
+            if (sb == g.nsb - 1) commit(mbar_at(C.mb, kG2Done));
+        }
         __syncwarp();
         C.nz++;
     }
@@ -813,29 +810,30 @@ __device__ __noinline__ void control_load(const HoloDev *__restrict__ holos, con
     if ((!ok || !drained) && lane0) atomicOr(status, 1u);
 }
 
-// The epilogue warps: per tile, u = A S / |S| (with Phi and the gray level in
-// the final pass), then the tile's partial V_n = sum_y conj(R_n(y)) Z(n, y)
-// per spot block.
-template <int W, bool F16>
-__device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
-                                         const SmemWs &m, const Info *info, G2Info *g2, uint32_t mb,
-                                         uint32_t tmem, unsigned *status)
+// The u warps (epilogue 1): per tile, u = A S / |S| (with Phi and the gray
+// level in the final pass) into GEMM 2's B operand, K-step by K-step.  u is
+// free for the tile once GEMM 2 of the previous tile with products is done.
+// A tile outside the pupil gets its zero partials (and, in the final pass,
+// phase 0 and gray lut[0]) here.
+template <bool F16>
+__device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2Info *g2, uint32_t mb, uint32_t tmem,
+                                           unsigned *status)
 {
-    using G = Cfg<W>;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, h = warp >> 2;
+    constexpr int kT = 32 * kUWarps;
+    const int tid = threadIdx.x, lane = tid & 31, q = tid >> 5;   // warps 0 .. 3: TMEM lane quadrant q
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
-    const uint32_t z_re = tmem, z_im = tmem + kRows;
-    // phases seen: ready[j] once per tile of slot j (tile k is its (k >> 1)-th),
-    // s_full[j] once per tile with products (low half: j = 0, high half: j = 1)
-    uint32_t n_s = 0u, n_z = 0u;
+    // phases seen: s_full[j] once per tile with products (low half: j = 0,
+    // high half: j = 1); g2_done once per tile with products
+    uint32_t n_s = 0u, n_p = 0u;
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
-        ok = group_and<W>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
+        ok = group_and<kBarU, kT>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
         if (!ok) break;
         if (info[j].done) {
-            if (tid == 0) {
+            // the GEMM 2 warp is done with the operand slot once its last GEMM 2 is
+            if (n_p > 0u) ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kG2Done), n_p));
+            if (ok && tid == 0) {
                 g2->done = 1;
                 arrive(mbar_at(mb, kG2Info));
             }
@@ -853,14 +851,14 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             // phase 0 (gray lut[0]) over its grid pixels
             __syncwarp();
             if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
-            for (int n = tid; n < N; n += G::kEpi) {
+            for (int n = tid; n < N; n += kT) {
                 if (pass == kPassFinal) H.part64[(size_t)t * N + n] = make_double2(0.0, 0.0);
                 else H.part[(size_t)t * N + n] = make_float2(0.f, 0.f);
             }
             if (pass == kPassFinal) {
                 const int rows = min(kRows, P - y0), cols = min(kCols, P - x0);
                 const uint8_t g0 = H.slm ? __ldg(H.lut) : 0;
-                for (int f = tid; f < rows * cols; f += G::kEpi) {
+                for (int f = tid; f < rows * cols; f += kT) {
                     const int r = y0 + f / cols, c = x0 + f % cols;
                     if (H.phase_out) H.phase_out[(size_t)r * P + c] = 0.f;
                     if (H.slm) H.slm[(size_t)r * H.slm_pitch + c] = g0;
@@ -869,7 +867,25 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             continue;
         }
 
-        // the GEMM 2 warp's operands for this tile (it streams C in meanwhile)
+        // A compressed pass reads the subset mask bits of the tile's columns
+        // first (two words: x0 is a multiple of 64), before the waits.
+        const int row = 32 * q + lane, gy = y0 + row;
+        uint64_t mword = ~0ull;
+        if (pass == kPassSubset) {
+            const int w0 = x0 >> 5;
+            if (gy < P) {
+                const uint32_t *mrow = H.mask + (size_t)gy * H.mask_words;
+                mword = (uint64_t)__ldg(mrow + w0) | (w0 + 1 < H.mask_words ? (uint64_t)__ldg(mrow + w0 + 1) << 32 : 0ull);
+            } else {
+                mword = 0ull;
+            }
+        }
+        // u and the single GEMM 2 operand slot are free once GEMM 2 of the
+        // previous tile with products is done
+        if (n_p > 0u) {
+            ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kG2Done), n_p));
+            if (!ok) break;
+        }
         if (tid == 0) {
             g2->cstab = F16 ? H.cstab16 : H.cstab;
             g2->nsb = nspotblocks(N);
@@ -878,28 +894,14 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             g2->f16 = F16 ? 1 : 0;
             arrive(mbar_at(mb, kG2Info));
         }
-
-        // ---- epilogue 1: S -> u (GEMM 2's B operand), Phi and gray out.  S is
-        // released once u is written.  A compressed pass reads the subset mask
-        // bits of the tile's columns first, before the wait for S.
-        uint64_t mword = ~0ull;
-        if (pass == kPassSubset) {
-            // the tile's 64 columns: two words (x0 is a multiple of 64)
-            const int gy = y0 + 32 * q + lane, w0 = x0 >> 5;
-            if (gy < P) {
-                const uint32_t *mrow = H.mask + (size_t)gy * H.mask_words;
-                mword = (uint64_t)__ldg(mrow + w0) | (w0 + 1 < H.mask_words ? (uint64_t)__ldg(mrow + w0 + 1) << 32 : 0ull);
-            } else {
-                mword = 0ull;
-            }
-        }
+        n_p++;
         n_s += 1u << (16 * j);
-        ok = group_and<W>(wait_newest(mbar_at(mb, kSFull0 + j), (n_s >> (16 * j)) & 0xFFFFu));
+        ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kSFull0 + j), (n_s >> (16 * j)) & 0xFFFFu));
         if (!ok) break;
         fence_after();
         {
             const uint32_t s_re = tmem + kS0 + 2 * kCols * j, s_im = s_re + kCols;
-            const int row = 32 * q + lane, gy = y0 + row, yq = gy - half;
+            const int yq = gy - half;
             const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
             // the row's pixels are columns xl..xr: the grid's, within the round
             // pupil (|x - half|^2 + yq^2 <= half^2) unless the aperture is square
@@ -916,32 +918,31 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                 xr = min(xr, half + w);
             }
             const float kA = H.kA;
-            // epilogue 1 of the thread's chunks, with the Gaussian beam's
+            // the row's 16 columns of each K-step, with the Gaussian beam's
             // amplitude or the uniform one (a uniform branch outside the loop)
-            auto chunks = [&](auto gauss_tag) {
+            auto ksteps = [&](auto gauss_tag) {
                 constexpr bool kGauss = decltype(gauss_tag)::value;
 #pragma unroll 1
                 for (int ks = 0; ks < kCols / 16; ++ks) {
-                    // the thread's 8 columns of K-step ks
-                    const int xs = 16 * ks + 8 * h, gx0 = x0 + xs;
+                    const int xs = 16 * ks, gx0 = x0 + xs;
                     // the pixels that carry u: in the row's span and, in a
                     // compressed pass, in S_j (the rest add nothing to Eq. 3's sum)
-                    const int lo = max(xl - gx0, 0), hi = min(xr - gx0, 7);
+                    const int lo = max(xl - gx0, 0), hi = min(xr - gx0, 15);
                     uint32_t bits = 0u;
-                    if (lo <= hi) bits = (0xFFu >> (7 - hi + lo)) << lo;
+                    if (lo <= hi) bits = (0xFFFFu >> (15 - hi + lo)) << lo;
                     bits &= (uint32_t)(mword >> xs);
-                    float sr[8], si[8], o[8];
-                    ld8(s_re + lanes + xs, sr);
-                    ld8(s_im + lanes + xs, si);
+                    float sr[16], si[16], o[16];
+                    ld16(s_re + lanes + xs, sr);
+                    ld16(s_im + lanes + xs, si);
                     ld_wait();
-                    {
-                        constexpr int g = 0;
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
                         float2 u[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             // branch-free: the lanes are rows, so a per-pixel branch
                             // (subset membership, the pupil edge) would diverge
-                            const int jj = e;
+                            const int jj = 8 * g + e;
                             const bool valid = ((bits >> jj) & 1u) != 0u;
                             const float a = sr[jj], b = si[jj];
                             const float n2 = a * a + b * b;
@@ -965,7 +966,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                     }
                     if (pass == kPassFinal && gy < P) {
 #pragma unroll
-                        for (int g = 0; g < 2; ++g) {
+                        for (int g = 0; g < 4; ++g) {
                             const int col = gx0 + 4 * g;
                             if (col >= P) break;
                             if (H.phase_out) {
@@ -987,23 +988,53 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                     if (lane == 0) arrive(mbar_at(mb, kUStep0 + ks));
                 }
             };
-            if (kA != 0.f) chunks(std::true_type{});
-            else chunks(std::false_type{});
+            if (kA != 0.f) ksteps(std::true_type{});
+            else ksteps(std::false_type{});
         }
         fence_before();
         __syncwarp();
         if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
+    }
+    if (!ok && tid == 0) atomicOr(status, 1u);
+}
 
-        // ---- epilogue 2 per spot block: V_n = sum_y conj(R_n(y)) Z(n, y)
+// The V warps (epilogue 2): per tile with products and spot block, the tile's
+// partial V_n = sum_y conj(R_n(y)) Z(n, y), one spot per thread over all 128
+// rows, while the u warps go on with the next tile.
+__device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
+{
+    constexpr int kT = 32 * kVWarps;
+    const int tid = threadIdx.x - 32 * kUWarps, lane = tid & 31, q = tid >> 5;   // TMEM lane quadrant q
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    const uint32_t z_re = tmem, z_im = tmem + kRows;
+    uint32_t n_z = 0u;   // z_full phases seen
+    bool ok = true;
+    for (uint32_t k = 0;; ++k) {
+        const int j = k & 1;
+        ok = group_and<kBarV, kT>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
+        if (!ok) break;
+        if (info[j].done) break;
+        const int item = info[j].item, empty = info[j].empty;
+        const int tile_begin = info[j].sl.tile_begin, pass = info[j].sl.pass;
+        const int P = info[j].H.P, N = info[j].H.N;
+        const int4 *coef = info[j].H.coef;
+        float2 *part = info[j].H.part;
+        double2 *part64 = info[j].H.part64;
+        // the info slot is read: it goes back with this group's arrival
+        __syncwarp();
+        if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
+        if (empty) continue;
+        const int t = item - tile_begin, half = P >> 1;
+        const int y0 = (t / ((P + kCols - 1) / kCols)) * kRows;
         for (int sb = 0; sb * kSpotBlock < N; ++sb) {
             n_z++;
-            ok = group_and<W>(wait_newest(mbar_at(mb, kZFull), n_z));
+            ok = group_and<kBarV, kT>(wait_newest(mbar_at(mb, kZFull), n_z));
             if (!ok) break;
             fence_after();
             // every lane computes (a lane past N uses spot N - 1's factors and
             // stores nothing): no divergent branch in the row loop
-            const int nl = 32 * q + lane, n = sb * kSpotBlock + nl;
-            const int4 cf = H.coef[min(n, N - 1)];
+            const int n = sb * kSpotBlock + 32 * q + lane;
+            const int4 cf = coef[min(n, N - 1)];
             const int32_t tilt = cf.y, Gh = cf.z;
             const float gl = __int_as_float(cf.w);
             // R_n(y) along the rows by recurrence: its phase is quadratic in y,
@@ -1014,8 +1045,7 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
             sincos_fix(kFixRound + 2u * (uint32_t)Gh, fmaf(2.f, gl, -kTwoPiF), es, ec);
             float vr0 = 0.f, vi0 = 0.f, vr1 = 0.f, vi1 = 0.f;
 #pragma unroll 1
-            for (int y16 = 0; y16 < G::kRowsPer; y16 += 16) {
-                const int ys = G::kRowsPer * h + y16;
+            for (int ys = 0; ys < kRows; ys += 16) {
                 float zr[16], zi[16];
                 ld16(z_re + lanes + ys, zr);
                 ld16(z_im + lanes + ys, zi);
@@ -1029,9 +1059,9 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                                ds, dc);
                     float2 d = make_float2(dc, ds);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        r[8 * b + k] = pr;
-                        if (k < 7) {
+                    for (int e = 0; e < 8; ++e) {
+                        r[8 * b + e] = pr;
+                        if (e < 7) {
                             pr = make_float2(fmaf(pr.x, d.x, -pr.y * d.y), fmaf(pr.x, d.y, pr.y * d.x));
                             d = make_float2(fmaf(d.x, ec, -d.y * es), fmaf(d.x, es, d.y * ec));
                         }
@@ -1046,24 +1076,15 @@ __device__ __forceinline__ void epilogue(const HoloDev *__restrict__ holos, cons
                     vi1 = fmaf(r[2 * e + 1].x, zi[2 * e + 1], fmaf(-r[2 * e + 1].y, zr[2 * e + 1], vi1));
                 }
             }
-            float vr = vr0 + vr1, vi = vi0 + vi1;
             fence_before();
             __syncwarp();
             if (lane == 0) arrive(mbar_at(mb, kZEmpty));
-            if (h > 0) m.vh[(h - 1) * kSpotBlock + nl] = make_float2(vr, vi);
-            group_sync<W>();
-            if (h == 0 && n < N) {
-#pragma unroll
-                for (int gg = 0; gg < G::kGroups - 1; ++gg) {
-                    const float2 o2 = m.vh[gg * kSpotBlock + nl];
-                    vr += o2.x;
-                    vi += o2.y;
-                }
+            if (n < N) {
+                const float vr = vr0 + vr1, vi = vi0 + vi1;
                 const size_t off = (size_t)t * N + n;
-                if (pass == kPassFinal) H.part64[off] = make_double2((double)vr, (double)vi);
-                else H.part[off] = make_float2(vr, vi);
+                if (pass == kPassFinal) part64[off] = make_double2((double)vr, (double)vi);
+                else part[off] = make_float2(vr, vi);
             }
-            group_sync<W>();
         }
         if (!ok) break;
     }
@@ -1090,8 +1111,9 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
         for (int b = 0; b < kBarsWs; ++b) {
             // the epilogue's releases arrive once per warp
             // S buffers and info slots go back from the epilogue and the GEMM 1 warp
-            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1)          ? W + 1
-                                 : (b == kZEmpty || (b >= kUStep0 && b < kCsFull)) ? W
+            const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1) ? W + 1
+                                 : b == kZEmpty                               ? kVWarps
+                                 : (b >= kUStep0 && b < kCsFull)              ? kUWarps
                                  : b == kDrain                                             ? 2
                                                                                            : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::saddr(&s_mbar[b])), "r"(cnt));
@@ -1107,7 +1129,7 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     __syncthreads();
     tc::fence_after();
     const uint32_t mb = tc::saddr(&s_mbar[0]);
-    const SmemWs m = carve_ws(smem, W / 4);
+    const SmemWs m = carve_ws(smem);
     unsigned *status = queue + 2;
     if (warp == W) {
         control_load(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
@@ -1115,8 +1137,10 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
         control_gemm1(m, s_info, mb, s_tmem, status);
     } else if (warp == W + 2) {
         control_gemm2(m, &s_g2, mb, s_tmem, status);
+    } else if (warp < kUWarps) {
+        epilogue_u<F16>(m, s_info, &s_g2, mb, s_tmem, status);
     } else {
-        epilogue<W, F16>(holos, slots, m, s_info, &s_g2, mb, s_tmem, status);
+        epilogue_v(s_info, mb, s_tmem, status);
     }
     tc::fence_before();
     __syncthreads();
@@ -1163,7 +1187,7 @@ static int tcws_max_grid_of(int maxN, int sm_count)
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, iter_full_tcws_kernel<W, F16>) != cudaSuccess) return 0;
     const size_t limit = 227 * 1024 - fa.sharedSizeBytes;
-    const size_t smem = tc::ws::smem_bytes_ws(W / 4);
+    const size_t smem = tc::ws::smem_bytes_ws();
     if (smem > limit || (size_t)maxN * sizeof(float2) > 48 * 1024) return 0;
     if (cudaFuncSetAttribute(iter_full_tcws_kernel<W, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess)
@@ -1187,10 +1211,10 @@ static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, in
 {
     (void)cudaGetLastError();
     if (f16)
-        iter_full_tcws_kernel<W, true><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(W / 4), s>>>(
+        iter_full_tcws_kernel<W, true><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(), s>>>(
             holos, slots, nslots, total_tiles, queue);
     else
-        iter_full_tcws_kernel<W, false><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(W / 4), s>>>(
+        iter_full_tcws_kernel<W, false><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(), s>>>(
             holos, slots, nslots, total_tiles, queue);
     // one tail block per slot, plus (compressed launches) blocks that clear the masks
     const dim3 tails((unsigned)nslots, 1u + (subset ? 8u : 0u));
