@@ -398,7 +398,7 @@ def run_compare(args, local):
     waist = 6000.0 / 9.2 * P / 1152
     pupil = dict(aperture="round", waist=waist, subset_mode="windows")
     out = torch.empty(P * P, dtype=torch.float32, device="cuda")
-    methods = [("RS", 1.0, [0])] + [("WGS", 1.0, [1, 2, 3, 5, 8, 12, 20, 30])]
+    methods = [("RS", 1.0, [0])] + [("WGS", 1.0, [1, 2, 3, 5, 8, 12, 20, 30, 50])]
     methods += [("CS-WGS", 2.0 ** -k, [3, 5, 8, 12, 20, 30, 50]) for k in range(1, 9)]
     budgets_ms = [0.25, 0.5, 1.0, 2.0, 4.0]
     result = {}
