@@ -66,10 +66,12 @@ struct HoloDev {
     unsigned char *cstab;   // C blocks for GEMM 2 (split BF16), made once
     unsigned char *cstab16; // the same in FP16 for the half-precision option (nullptr: not made)
     // subset mask of compressed passes on the tensor cores (nullptr: not used):
-    // P rows of mask_words words, bit c % 32 of word c / 32 for pixel column c
+    // P rows of mask_words words, bit c % 32 of word c / 32 for pixel column c.
+    // Iteration j uses the mask at word offset (j & 1) * mask_stride: two masks
+    // (one is drawn while the other is in use), or one when mask_stride is 0.
     uint32_t *mask;
     int mask_words;
-    int pad3;
+    int mask_stride;
 };
 
 // One hologram's share of one persistent launch.
@@ -135,7 +137,9 @@ cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int 
 void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs);   // cs: split BF16 (FP16: half)
 cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count, cudaStream_t s);
 cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
-                                cudaStream_t s);
+                                bool masks, cudaStream_t s);
+cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
+                                   cudaStream_t s);
 
 // Either full-pass kernel, by tile shape (runtime.cu).
 bool shape_supported(TileShape shape);

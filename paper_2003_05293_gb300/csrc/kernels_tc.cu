@@ -326,26 +326,45 @@ __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__rest
 }
 
 // R' = w a e^{i theta} R (GEMM 1's A: 128 rows x 16 spots per block) of the
-// hologram of each slot, from its current spot state; for a compressed pass
-// also the subset mask: bit c of word r * mask_words + c / 32 is set when pixel
-// r P + c belongs to S_j (each of the Mp draws of Section 3 sets its pixel's
-// bit; the mask was cleared after its last use).
+// hologram of each slot, from its current spot state; with `masks`, for a
+// compressed pass also the subset mask (bit c of word r * mask_words + c / 32
+// is set when pixel r P + c belongs to S_j), else a separate launch draws it.
+__device__ __forceinline__ uint32_t *subset_mask(const HoloDev &H, int j)
+{
+    return H.mask + (size_t)(j & 1) * (size_t)H.mask_stride;
+}
+
+// The Mp draws of S_j (Section 3) of the slot's hologram, each setting its
+// pixel's bit in the iteration's mask, which is clear before (the tails of the
+// last launch that used it cleared it).  Grid: blocks x slots.
+__device__ __forceinline__ void scatter_subset(const HoloDev &H, const LaunchSlot &sl)
+{
+    uint32_t *mask = subset_mask(H, sl.j);
+    const SubsetDraw d = subset_draw(H, sl.j);
+    const UDiv dP = udiv_of((uint32_t)H.P);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H.Mp; k += gridDim.x * blockDim.x) {
+        const uint32_t m = subset_pixel(H, d, (uint32_t)k);
+        uint32_t c;
+        const uint32_t r = udiv(m, dP, c);
+        atomicOr(mask + (size_t)r * H.mask_words + (c >> 5), 1u << (c & 31));
+    }
+}
+
+__global__ void __launch_bounds__(256) mask_scatter_kernel(const HoloDev *__restrict__ holos,
+                                                           const LaunchSlot *__restrict__ slots)
+{
+    const LaunchSlot sl = slots[blockIdx.y];
+    const HoloDev H = holos[sl.holo];
+    if (sl.pass == kPassSubset && H.mask) scatter_subset(H, sl);
+}
+
 __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restrict__ holos,
-                                                        const LaunchSlot *__restrict__ slots)
+                                                        const LaunchSlot *__restrict__ slots, int masks)
 {
     const LaunchSlot sl = slots[blockIdx.y];
     const HoloDev H = holos[sl.holo];
     if (!H.rwtab) return;
-    if (sl.pass == kPassSubset && H.mask) {
-        const SubsetDraw d = subset_draw(H, sl.j);
-        const UDiv dP = udiv_of((uint32_t)H.P);
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H.Mp; k += gridDim.x * blockDim.x) {
-            const uint32_t m = subset_pixel(H, d, (uint32_t)k);
-            uint32_t c;
-            const uint32_t r = udiv(m, dP, c);
-            atomicOr(H.mask + (size_t)r * H.mask_words + (c >> 5), 1u << (c & 31));
-        }
-    }
+    if (masks && sl.pass == kPassSubset && H.mask) scatter_subset(H, sl);
     const int P = H.P, N = H.N, half = P >> 1, nc = nchunks(N);
     const int items = ((P + kRows - 1) / kRows) * nc * 256;      // (block, 128 rows x 2 groups)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items; i += gridDim.x * blockDim.x) {
@@ -874,7 +893,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
         if (pass == kPassSubset) {
             const int w0 = x0 >> 5;
             if (gy < P) {
-                const uint32_t *mrow = H.mask + (size_t)gy * H.mask_words;
+                const uint32_t *mrow = subset_mask(H, sl.j) + (size_t)gy * H.mask_words;
                 mword = (uint64_t)__ldg(mrow + w0) | (w0 + 1 < H.mask_words ? (uint64_t)__ldg(mrow + w0 + 1) << 32 : 0ull);
             } else {
                 mword = 0ull;
@@ -1170,10 +1189,11 @@ __global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restri
     const HoloDev &H = holos[sl.holo];
     if (blockIdx.y > 0) {
         if (sl.pass == kPassSubset && H.mask) {
+            uint32_t *mask = tc::subset_mask(H, sl.j);
             const size_t words = (size_t)H.P * H.mask_words;
             for (size_t i = (size_t)(blockIdx.y - 1) * blockDim.x + threadIdx.x; i < words;
                  i += (size_t)(gridDim.y - 1) * blockDim.x)
-                H.mask[i] = 0u;
+                mask[i] = 0u;
         }
         return;
     }
@@ -1249,13 +1269,24 @@ cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count
 }
 
 cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
-                                cudaStream_t s)
+                                bool masks, cudaStream_t s)
 {
     if (nslots <= 0) return cudaSuccess;
     (void)cudaGetLastError();
     // a wide grid: the subset masks' scattered bit sets are latency-bound
     dim3 grid((unsigned)std::max(1, 16 * sm_count / std::max(1, nslots)), (unsigned)nslots);
-    tc::rw_tables_kernel<<<grid, 256, 0, s>>>(holos, slots);
+    tc::rw_tables_kernel<<<grid, 256, 0, s>>>(holos, slots, masks ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
+                                   cudaStream_t s)
+{
+    if (nslots <= 0) return cudaSuccess;
+    (void)cudaGetLastError();
+    // two blocks per SM, which fit beside the persistent kernel they overlap
+    dim3 grid((unsigned)std::max(1, 2 * sm_count / std::max(1, nslots)), (unsigned)nslots);
+    tc::mask_scatter_kernel<<<grid, 256, 0, s>>>(holos, slots);
     return cudaGetLastError();
 }
 

@@ -264,6 +264,9 @@ Fp32Batch::~Fp32Batch()
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (auto e : events) cudaEventDestroy(e);
+    for (cudaEvent_t e : {ev_start, ev_tail[0], ev_tail[1], ev_scat[0], ev_scat[1]})
+        if (e) cudaEventDestroy(e);
+    if (side) cudaStreamDestroy(side);
     if (staging) cudaFreeHost(staging);
 }
 
@@ -327,7 +330,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     if (shape.threads == kSubsetTc)
         for (int h = 0; h < count; ++h) {
             m_off[h] = work;
-            work += align256(sizeof(uint32_t) * (size_t)b->specs[h].P * mask_words_of(b->specs[h].P));
+            work += align256(2 * sizeof(uint32_t) * (size_t)b->specs[h].P * mask_words_of(b->specs[h].P));
         }
     b->mask_bytes = work - b->mask_begin;
     CSWGS_TRY(b->mem.ensure(work));
@@ -389,6 +392,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         if (shape.threads == kSubsetTc) {
             H.mask = reinterpret_cast<uint32_t *>(base + m_off[h]);
             H.mask_words = mask_words_of(s.P);
+            H.mask_stride = s.P * H.mask_words;
         }
         if (uses_tc(shape)) {
             size_t rw, c, cs;
@@ -464,6 +468,11 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     if (timing) {
         b->events.resize(L_max + 2);   // before the preparation, before each step, after the last
         for (auto &e : b->events) CSWGS_CUDA_TRY(cudaEventCreate(&e));
+    }
+    if (shape.threads == kSubsetTc) {
+        CSWGS_CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&b->ev_start, &b->ev_tail[0], &b->ev_tail[1], &b->ev_scat[0], &b->ev_scat[1]})
+            CSWGS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     }
     *out = std::move(b);
     return CSWGS_OK;
@@ -557,6 +566,26 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
     if (uses_tc(b->shape)) CSWGS_CUDA_TRY(launch_tc_const_tables(holos, count, b->plan->sm_count, s));
     const size_t steps = b->l_tiles.size() / 2;
+    // Compressed launches on the tensor cores draw their subset masks on the
+    // side stream, one step ahead: the draw of step L + 1 runs beside the launch
+    // of step L, after the tails of step L - 1 have cleared that mask (each
+    // hologram advances one iteration per step, so it alternates its two masks).
+    const bool side_masks = b->side && launch_uses_tc(b->shape, kLaunchSubset);
+    auto masked = [&](size_t L) { return L < steps && b->l_tiles[2 * L + kLaunchSubset] > 0; };
+    bool tail_rec[2] = {false, false};
+    auto draw = [&](size_t L) -> cswgs_status {
+        if (tail_rec[L & 1]) CSWGS_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_tail[L & 1], 0));
+        const size_t i = 2 * L + kLaunchSubset;
+        CSWGS_CUDA_TRY(launch_tc_mask_scatter(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count,
+                                              b->side));
+        CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_scat[L & 1], b->side, 0));
+        return CSWGS_OK;
+    };
+    if (side_masks) {
+        CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_start, s, 0));   // the masks are clear
+        CSWGS_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_start, 0));
+        if (masked(0)) CSWGS_TRY(draw(0));
+    }
     for (size_t L = 0; L < steps; ++L) {
         if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[L + 1], s, evflag));
         for (int kind = 0; kind < 2; ++kind) {
@@ -564,10 +593,18 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
             const int tiles = b->l_tiles[i];
             if (tiles == 0) continue;
             const int grid = std::min(b->grid[kind], tiles);
+            const bool side_draw = side_masks && kind == kLaunchSubset;
             if (launch_uses_tc(b->shape, kind))
-                CSWGS_CUDA_TRY(launch_tc_rw_tables(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count, s));
+                CSWGS_CUDA_TRY(launch_tc_rw_tables(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count,
+                                                   !side_draw, s));
+            if (side_draw) CSWGS_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_scat[L & 1], 0));
             CSWGS_CUDA_TRY(shape_launch(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
-                                            b->l_maxN[i], queue, grid, s));
+                                        b->l_maxN[i], queue, grid, s));
+            if (side_draw) {
+                CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_tail[L & 1], s, 0));
+                tail_rec[L & 1] = true;
+                if (masked(L + 1)) CSWGS_TRY(draw(L + 1));
+            }
         }
     }
     if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[steps + 1], s, evflag));

@@ -123,6 +123,10 @@ struct Fp32Batch {
     std::vector<cudaEvent_t> events;      // launch boundaries (timing)
     double pairs_total = 0.0, pairs_iter = 0.0;
     size_t mask_begin = 0, mask_bytes = 0;   // subset masks (cleared at the start of every run)
+    // the next compressed launch's subset masks are drawn on a side stream while
+    // the current launch runs (two masks per hologram, by the parity of j)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_tail[2] = {nullptr, nullptr}, ev_scat[2] = {nullptr, nullptr};
     ~Fp32Batch();
 };
 

@@ -218,6 +218,7 @@ void Server::place(Req &r)
         // the subset mask starts clear (each compressed launch's tails clear it again)
         H.mask = reinterpret_cast<uint32_t *>(b + o);
         H.mask_words = mask_words_of(s.P);
+        H.mask_stride = 0;   // one mask: serving draws it in the launch's own table kernel
         const size_t bytes = sizeof(uint32_t) * (size_t)s.P * H.mask_words;
         o += al256(bytes);
         note(cudaMemsetAsync(H.mask, 0, bytes, stream_));
@@ -442,7 +443,7 @@ void Server::loop()
             if (g == grid_for.end())
                 g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
             if (launch_uses_tc(shape_, kind))
-                chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, stream_));
+                chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, true, stream_));
             chk(shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
                              queue, std::min(g->second, group_tiles[kind]), stream_));
         }
