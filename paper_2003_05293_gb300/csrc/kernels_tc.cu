@@ -1284,8 +1284,9 @@ cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots
 {
     if (nslots <= 0) return cudaSuccess;
     (void)cudaGetLastError();
-    // two blocks per SM, which fit beside the persistent kernel they overlap
-    dim3 grid((unsigned)std::max(1, 2 * sm_count / std::max(1, nslots)), (unsigned)nslots);
+    // one block per SM beside the persistent kernel it overlaps (two slowed
+    // that kernel more, one per two SMs delayed the next launch)
+    dim3 grid((unsigned)std::max(1, sm_count / std::max(1, nslots)), (unsigned)nslots);
     tc::mask_scatter_kernel<<<grid, 256, 0, s>>>(holos, slots);
     return cudaGetLastError();
 }
