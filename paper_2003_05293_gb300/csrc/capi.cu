@@ -92,6 +92,54 @@ static cswgs_status solve_fp64(cswgs_plan_s *p, const HoloSpec &h, float *phase_
     return CSWGS_OK;
 }
 
+// Host phase maps go out through a copy kernel where the GPU can write the
+// host buffer itself: pinned memory through its mapped device address, or
+// pageable memory on a device that shares the host's page tables.  Each warp
+// stores 512 contiguous bytes, which the link to host memory takes at a far
+// higher rate than a copy-engine transfer of the same map.  Other buffers
+// (and any not 16-byte aligned) are copied by cudaMemcpyAsync.
+struct MapCopy {
+    const float *src;
+    float *dst;
+    size_t n;
+};
+
+__global__ void __launch_bounds__(256) copy_maps_kernel(const MapCopy *__restrict__ jobs)
+{
+    const MapCopy j = jobs[blockIdx.y];
+    const size_t n4 = j.n / 4, step = (size_t)gridDim.x * blockDim.x;
+    const float4 *s4 = reinterpret_cast<const float4 *>(j.src);
+    float4 *d4 = reinterpret_cast<float4 *>(j.dst);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += step) d4[i] = __ldcs(s4 + i);
+    for (size_t i = 4 * n4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < j.n; i += step) j.dst[i] = j.src[i];
+}
+
+static float *host_direct(const cswgs_plan_s *p, float *h)
+{
+    if (reinterpret_cast<uintptr_t>(h) & 15) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost) return static_cast<float *>(a.devicePointer);
+    if (a.type == cudaMemoryTypeUnregistered && p->pageable_direct) return h;
+    return nullptr;
+}
+
+// Writes the maps of `jobs` out (one launch), on stream s after the solve.
+static cswgs_status copy_maps(cswgs_plan_s *p, DevBuf &buf, const std::vector<MapCopy> &jobs, cudaStream_t s)
+{
+    if (jobs.empty()) return CSWGS_OK;
+    CSWGS_TRY(buf.ensure(sizeof(MapCopy) * jobs.size()));
+    CSWGS_CUDA_TRY(cudaMemcpyAsync(buf.p, jobs.data(), sizeof(MapCopy) * jobs.size(), cudaMemcpyHostToDevice, s));
+    const int n = (int)jobs.size();
+    const dim3 grid((unsigned)std::max(1, 4 * p->sm_count / n), (unsigned)n);
+    copy_maps_kernel<<<grid, 256, 0, s>>>(static_cast<const MapCopy *>(buf.p));
+    CSWGS_CUDA_TRY(cudaGetLastError());
+    return CSWGS_OK;
+}
+
 // FP32 solver: one hologram through a cached single-hologram batch.
 static cswgs_status solve_fp32(cswgs_plan_s *p, HoloSpec h, float *phase_out, int out_on_host,
                                double *e, double *u, double *final_w, double *final_theta,
@@ -128,9 +176,13 @@ static cswgs_status solve_fp32(cswgs_plan_s *p, HoloSpec h, float *phase_out, in
     std::vector<SpotState> st(N);
     if (b->specs[0].final_pass) {
         CSWGS_CUDA_TRY(cudaMemcpyAsync(met.data(), H.metrics, sizeof(double) * (2 + N), cudaMemcpyDeviceToHost, s));
-        if (host_out)
-            CSWGS_CUDA_TRY(cudaMemcpyAsync(phase_out, b->own_phase[0], sizeof(float) * (size_t)H.P * H.P,
-                                           cudaMemcpyDeviceToHost, s));
+        if (host_out) {
+            const size_t n = (size_t)H.P * H.P;
+            if (float *d = host_direct(p, phase_out))
+                CSWGS_TRY(copy_maps(p, b->copy_jobs, {MapCopy{b->own_phase[0], d, n}}, s));
+            else
+                CSWGS_CUDA_TRY(cudaMemcpyAsync(phase_out, b->own_phase[0], sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+        }
     }
     if (final_w || final_theta)
         CSWGS_CUDA_TRY(cudaMemcpyAsync(st.data(), H.state, sizeof(SpotState) * N, cudaMemcpyDeviceToHost, s));
@@ -248,6 +300,12 @@ cswgs_status cswgs_plan_create(cswgs_plan *out, const cswgs_plan_desc *d)
     if (st == CSWGS_OK) {
         cudaError_t e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
         if (e != cudaSuccess) st = set_error(CSWGS_ECUDA, "device attribute: %s", cudaGetErrorString(e));
+        int pageable = 0, shared_tables = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, p->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&shared_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, p->device) !=
+                cudaSuccess)
+            (void)cudaGetLastError();
+        p->pageable_direct = pageable != 0 && shared_tables != 0;
     }
     if (st == CSWGS_OK) {
         if (d->stream) {
@@ -581,12 +639,19 @@ cswgs_status cswgs_solve_batch(cswgs_plan p, const cswgs_request *reqs, int coun
     CSWGS_TRY(batch_set_outputs(b, outs, s));
     CSWGS_TRY(batch_enqueue(b, s));
     std::vector<double> eu(2 * count);
+    std::vector<MapCopy> jobs;
     for (int i = 0; i < count; ++i) {
         CSWGS_CUDA_TRY(cudaMemcpyAsync(&eu[2 * i], b->holos[i].metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        if (reqs[i].out_on_host && reqs[i].phase_out)
-            CSWGS_CUDA_TRY(cudaMemcpyAsync(reqs[i].phase_out, b->own_phase[i],
-                                           sizeof(float) * (size_t)specs[i].P * specs[i].P, cudaMemcpyDeviceToHost, s));
+        if (reqs[i].out_on_host && reqs[i].phase_out) {
+            const size_t n = (size_t)specs[i].P * specs[i].P;
+            if (float *d = host_direct(p, reqs[i].phase_out))
+                jobs.push_back(MapCopy{b->own_phase[i], d, n});
+            else
+                CSWGS_CUDA_TRY(cudaMemcpyAsync(reqs[i].phase_out, b->own_phase[i], sizeof(float) * n,
+                                               cudaMemcpyDeviceToHost, s));
+        }
     }
+    CSWGS_TRY(copy_maps(p, b->copy_jobs, jobs, s));
     CSWGS_TRY(batch_status(b, s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, b->events.front(), b->events.back());

@@ -469,7 +469,9 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         b->events.resize(L_max + 2);   // before the preparation, before each step, after the last
         for (auto &e : b->events) CSWGS_CUDA_TRY(cudaEventCreate(&e));
     }
-    if (shape.threads == kSubsetTc) {
+    bool square = true;
+    for (const HoloDev &H : b->holos) square = square && H.aperture == 0;
+    if (shape.threads == kSubsetTc && square) {
         CSWGS_CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
         for (cudaEvent_t *e : {&b->ev_start, &b->ev_tail[0], &b->ev_tail[1], &b->ev_scat[0], &b->ev_scat[1]})
             CSWGS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));

@@ -124,9 +124,12 @@ struct Fp32Batch {
     double pairs_total = 0.0, pairs_iter = 0.0;
     size_t mask_begin = 0, mask_bytes = 0;   // subset masks (cleared at the start of every run)
     // the next compressed launch's subset masks are drawn on a side stream while
-    // the current launch runs (two masks per hologram, by the parity of j)
+    // the current launch runs (two masks per hologram, by the parity of j), when
+    // every hologram has the square aperture; a round pupil's draws (a row
+    // search each) are too slow to hide and stay in the R' table kernel
     cudaStream_t side = nullptr;
     cudaEvent_t ev_start = nullptr, ev_tail[2] = {nullptr, nullptr}, ev_scat[2] = {nullptr, nullptr};
+    DevBuf copy_jobs;   // host phase maps written out by the copy kernel (cswgs_solve_batch)
     ~Fp32Batch();
 };
 
@@ -147,6 +150,7 @@ struct cswgs_plan_s {
     cswgs_plan_desc desc{};
     int device = 0;
     int sm_count = 0;
+    bool pageable_direct = false;   // kernels may write pageable host memory (shared page tables)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::mutex mu;
