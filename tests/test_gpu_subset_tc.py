@@ -146,6 +146,33 @@ def test_batch_against_cuda_core(plans):
     b.close()
 
 
+def test_square_batch_side_draws(plans):
+    # every hologram square: the subset masks of launch L + 1 are drawn on a
+    # side stream beside launch L, alternating two masks per hologram; three
+    # runs of the same batch (both masks reused and cleared), P not a multiple
+    # of the tile, one to three spot blocks
+    tc, cc = plans
+    pbs = [workloads.problem(P, N, 5.0, 0.125, 9, seed=400 + i)
+           for i, (P, N) in enumerate([(512, 40), (300, 100), (256, 200), (384, 300), (512, 129), (200, 17)])]
+    outs1 = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+    outs2 = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+    b = tc.batch(pbs, outs1)
+    assert b.tile_shape()["threads"] == SUBSET_TC
+    r2 = cc.solve_batch(pbs, outs2)
+    ref = [o.cpu().numpy() for o in outs2]
+    for rep in range(3):
+        b.run()
+        r1 = b.results()
+        for a, c2, o1, o2 in zip(r1, r2, outs1, ref):
+            assert rms_wrapped(o1.cpu().numpy(), o2) < TOL_PHASE_RMS
+            assert abs(a["e"] - c2["e"]) < TOL_EU and abs(a["u"] - c2["u"]) < TOL_EU
+    b.close()
+    # the first hologram against the oracle
+    pb = pbs[0]
+    o = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+    assert rms_wrapped(outs1[0].cpu().numpy(), o["phase"]) < TOL_PHASE_RMS
+
+
 def test_serving(plans):
     # continuous batching: each admitted request gets a clear mask
     tc, cc = plans
