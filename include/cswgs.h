@@ -285,7 +285,8 @@ cswgs_status cswgs_batch_pairs(cswgs_batch b, double *pairs_total, double *pairs
  * thread; for full iterations and the final pass threads per block of the
  * CUDA-core kernel, or a tensor-core kernel (tiles of 128 x 64 pixels,
  * split-BF16 products accumulated in FP32): 2 = the warp-specialised kernel,
- * pipelined across tiles (8 epilogue warps and one control warp); compressed
+ * pipelined across tiles (8 epilogue warps, a producer warp and two MMA
+ * warps); compressed
  * iterations report threads = 1 when they run on that kernel too (u zero
  * outside the subset); and the persistent blocks of each per launch.  Any
  * pointer may be NULL. */

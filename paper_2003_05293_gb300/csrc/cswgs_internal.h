@@ -94,8 +94,8 @@ struct TileShape {
 
 // full_threads value that selects the tensor-core kernel for full iterations
 // and the final pass (kernels_tc.cu, 128 x 64-pixel tiles; warp-specialised
-// and pipelined across tiles: 8 epilogue warps, a producer warp and two MMA warps, the
-// tails in a kernel of their own)
+// and pipelined across tiles: 4 u and 4 V epilogue warps, a producer warp and
+// two MMA warps; the tails in a kernel of their own)
 constexpr int kFullTcWs = 2;
 inline bool is_full_tc(int full_threads) { return full_threads == kFullTcWs; }
 

@@ -34,10 +34,10 @@
 // remade before every launch.  A tile streams its blocks into shared memory
 // with bulk copies (cp.async.bulk, completion counted on an mbarrier) through
 // a ring; a producer warp issues GEMM 1's copies, two issuing warps (GEMM 1,
-// GEMM 2) issue the MMAs and commit them to mbarriers, eight epilogue warps
-// run the CUDA-core stages.  Every wait is
-// bounded and a timeout is recorded in the launch's status word instead of
-// hanging.
+// GEMM 2) issue the MMAs and commit them to mbarriers, and eight epilogue
+// warps run the CUDA-core stages: four turn S into u (epilogue 1), four reduce
+// Z to the spot fields (epilogue 2) one tile behind.  Every wait is bounded
+// and a timeout is recorded in the launch's status word instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
