@@ -78,6 +78,35 @@ def test_batch_against_oracle(plan):
     b.close()
 
 
+def test_batched_form_full_size():
+    # the batched form at full size: 64 holograms, P in {512, 768, 1024, 1152},
+    # N ~ U{10..300}, c = 1/8, 30 iterations, one persistent launch per
+    # iteration on the autotuner's shapes; sampled holograms against the
+    # oracle (the two smallest by P * N, and the largest N at P <= 768) and
+    # against their solo solves, and e, u of every hologram in range
+    from paper_2003_05293_gb300 import Plan
+    pbs = workloads.batch(64, seed=11)
+    with Plan(precision="fp32", max_batch=64) as big:
+        outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+        b = big.batch(pbs, outs)
+        b.run()
+        res = b.results()
+        for r in res:
+            assert 0.0 < r["e"] <= 1.0 and 0.0 < r["u"] <= 1.0
+        order = sorted(range(len(pbs)), key=lambda i: pbs[i].P * pbs[i].N)
+        picks = order[:2] + [max((i for i in range(len(pbs)) if pbs[i].P <= 768), key=lambda i: pbs[i].N)]
+        for i in picks:
+            pb = pbs[i]
+            ref = oracle.solve(pb.P, pb.xyz, c=pb.c, iterations=pb.iterations, seed=pb.seed)
+            assert rms_wrapped(outs[i].cpu().numpy(), ref["phase"]) < TOL_PHASE_RMS
+            assert abs(res[i]["e"] - ref["e"]) < TOL_EU and abs(res[i]["u"] - ref["u"]) < TOL_EU
+            o2 = torch.empty(pb.M, dtype=torch.float32, device="cuda")
+            s = big.solve(pb.xyz, pb.P, pb.c, pb.iterations, pb.seed, out=o2)
+            assert rms_wrapped(outs[i].cpu().numpy(), o2.cpu().numpy()) < TOL_PHASE_RMS
+            assert abs(res[i]["e"] - s["e"]) < TOL_EU and abs(res[i]["u"] - s["u"]) < TOL_EU
+        b.close()
+
+
 def test_solve_batch_host_outputs(plan):
     pbs = small_mix(5, 4)
     outs = [np.empty(pb.M, dtype=np.float32) for pb in pbs]
