@@ -1198,7 +1198,7 @@ __global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restri
         return;
     }
     if (sl.pass == kPassFinal) tail_metrics<256>(H, sl, s_red);
-    else tail_update<256>(H, sl, s_v, s_red);
+    else tail_update<256, true>(H, sl, s_v, s_red);
 }
 
 template <int W, bool F16>

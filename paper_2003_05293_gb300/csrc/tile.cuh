@@ -42,25 +42,62 @@ __device__ __forceinline__ double block_max_f64(double v, double *s_red)
 // Weighted update (Eqs. 4-6) from the per-tile partial fields of one pass:
 // V_n = (1/count) sum_tiles part; w_n <- w_n <|V|> / |V_n|; theta_n <- arg V_n.
 // The tile partials are summed with Kahan compensation.
-template <int THREADS>
+// Compensated sum of spot n's tile partials t = t0, t0 + dt, ... (8 loads in flight).
+__device__ __forceinline__ float4 tile_sum(const HoloDev &H, int n, int t0, int dt, int tiles)
+{
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll 8   // loads issued ahead of the compensated sum's chain
+    for (int t = t0; t < tiles; t += dt) {
+        float2 p = __ldcg(&H.part[(size_t)t * H.N + n]);
+        float yr = p.x - cr, tr = sr + yr;
+        cr = (tr - sr) - yr;
+        sr = tr;
+        float yi = p.y - ci, ti = si + yi;
+        ci = (ti - si) - yi;
+        si = ti;
+    }
+    return make_float4(sr, cr, si, ci);
+}
+
+// With SPLIT (a block of its own per hologram), G groups of threads share a
+// spot's tiles (t = g, g + G, ...) when the block has threads to spare, for
+// G times the loads in flight; each group's compensated sum (s, c) stands for
+// s - c, and the G of them are summed with compensation again.
+template <int THREADS, bool SPLIT = false>
 __device__ void tail_update(const HoloDev &H, const LaunchSlot &sl, float2 *s_v, double *s_red)
 {
     const int N = H.N;
     const float inv = 1.0f / (float)sl.count;
+    const int G = SPLIT ? max(1, min(16, THREADS / max(1, N))) : 1;
+    float4 *s_grp = nullptr;
+    if constexpr (SPLIT) {
+        __shared__ float4 s_grp_buf[THREADS];
+        s_grp = s_grp_buf;
+        if (G > 1) {
+            const int n = threadIdx.x % N, g = threadIdx.x / N;
+            if (g < G) s_grp[g * N + n] = tile_sum(H, n, g, G, sl.tiles);
+            __syncthreads();
+        }
+    }
     double local = 0.0;
     for (int n = threadIdx.x; n < N; n += THREADS) {
-        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-#pragma unroll 8   // loads issued ahead of the compensated sum's chain
-        for (int t = 0; t < sl.tiles; ++t) {
-            float2 p = __ldcg(&H.part[(size_t)t * N + n]);
-            float yr = p.x - cr, tr = sr + yr;
-            cr = (tr - sr) - yr;
-            sr = tr;
-            float yi = p.y - ci, ti = si + yi;
-            ci = (ti - si) - yi;
-            si = ti;
+        float4 q;
+        if (G > 1) {
+            float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+            for (int g = 0; g < G; ++g) {
+                const float4 p = s_grp[g * N + n];
+                float yr = (p.x - p.y) - cr, tr = sr + yr;
+                cr = (tr - sr) - yr;
+                sr = tr;
+                float yi = (p.z - p.w) - ci, ti = si + yi;
+                ci = (ti - si) - yi;
+                si = ti;
+            }
+            q = make_float4(sr, cr, si, ci);
+        } else {
+            q = tile_sum(H, n, 0, 1, sl.tiles);
         }
-        float2 v = make_float2(sr * inv, si * inv);
+        float2 v = make_float2(q.x * inv, q.z * inv);
         s_v[n] = v;
         local += (double)hypotf(v.x, v.y);
     }
