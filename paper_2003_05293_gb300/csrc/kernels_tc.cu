@@ -1180,11 +1180,13 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
 // (blockIdx.y == 0): the weighted update (Eqs. 4-6) from the tile partials, or
 // the metrics.  The other blocks of a compressed slot clear its subset mask
 // for the next draw.
-__global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restrict__ holos,
+constexpr int kTailThreads = 1024;   // a hologram's tile sums take a whole block's loads in flight
+
+__global__ void __launch_bounds__(kTailThreads) tcws_tails_kernel(const HoloDev *__restrict__ holos,
                                                          const LaunchSlot *__restrict__ slots)
 {
     extern __shared__ float2 s_v[];
-    __shared__ double s_red[256 / 32];
+    __shared__ double s_red[kTailThreads / 32];
     const LaunchSlot sl = slots[blockIdx.x];
     const HoloDev &H = holos[sl.holo];
     if (blockIdx.y > 0) {
@@ -1197,8 +1199,8 @@ __global__ void __launch_bounds__(256) tcws_tails_kernel(const HoloDev *__restri
         }
         return;
     }
-    if (sl.pass == kPassFinal) tail_metrics<256>(H, sl, s_red);
-    else tail_update<256, true>(H, sl, s_v, s_red);
+    if (sl.pass == kPassFinal) tail_metrics<kTailThreads, true>(H, sl, s_red);
+    else tail_update<kTailThreads, true>(H, sl, s_v, s_red);
 }
 
 template <int W, bool F16>
@@ -1238,7 +1240,7 @@ static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, in
             holos, slots, nslots, total_tiles, queue);
     // one tail block per slot, plus (compressed launches) blocks that clear the masks
     const dim3 tails((unsigned)nslots, 1u + (subset ? 8u : 0u));
-    tcws_tails_kernel<<<tails, 256, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
+    tcws_tails_kernel<<<tails, kTailThreads, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
     return cudaGetLastError();
 }
 

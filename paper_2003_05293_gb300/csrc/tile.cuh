@@ -71,8 +71,8 @@ __device__ void tail_update(const HoloDev &H, const LaunchSlot &sl, float2 *s_v,
     const int G = SPLIT ? max(1, min(16, THREADS / max(1, N))) : 1;
     float4 *s_grp = nullptr;
     if constexpr (SPLIT) {
-        __shared__ float4 s_grp_buf[THREADS];
-        s_grp = s_grp_buf;
+        __shared__ double2 s_grp_buf[THREADS];
+        s_grp = reinterpret_cast<float4 *>(s_grp_buf);
         if (G > 1) {
             const int n = threadIdx.x % N, g = threadIdx.x / N;
             if (g < G) s_grp[g * N + n] = tile_sum(H, n, g, G, sl.tiles);
@@ -115,19 +115,45 @@ __device__ void tail_update(const HoloDev &H, const LaunchSlot &sl, float2 *s_v,
 // Metrics of the final pass: V_n = sum over the pupil of A e^{i(Phi - phi_n)}
 // (FP64 partials) divided by the pupil's sum of A, I_n = |V_n|^2,
 // e = sum_n I_n, u by Eq. 7.
-template <int THREADS>
+// With SPLIT, G groups of threads share a spot's tiles as in tail_update.
+template <int THREADS, bool SPLIT = false>
 __device__ void tail_metrics(const HoloDev &H, const LaunchSlot &sl, double *s_red)
 {
     const int N = H.N;
     const double inv = 1.0 / H.norm;   // sum of A over the pupil (P^2 for the square uniform grid)
-    double e = 0.0, imax = -1.0, imin = 1e300;
-    for (int n = threadIdx.x; n < N; n += THREADS) {
+    const int G = SPLIT ? max(1, min(16, THREADS / max(1, N))) : 1;
+    auto sum = [&](int n, int t0, int dt) {
         double vr = 0.0, vi = 0.0;
 #pragma unroll 8
-        for (int t = 0; t < sl.tiles; ++t) {
+        for (int t = t0; t < sl.tiles; t += dt) {
             double2 p = __ldcg(&H.part64[(size_t)t * N + n]);
             vr += p.x;
             vi += p.y;
+        }
+        return make_double2(vr, vi);
+    };
+    double2 *s_grp = nullptr;
+    if constexpr (SPLIT) {
+        __shared__ double2 s_grp_buf[THREADS];
+        s_grp = s_grp_buf;
+        if (G > 1) {
+            const int n = threadIdx.x % N, g = threadIdx.x / N;
+            if (g < G) s_grp[g * N + n] = sum(n, g, G);
+            __syncthreads();
+        }
+    }
+    double e = 0.0, imax = -1.0, imin = 1e300;
+    for (int n = threadIdx.x; n < N; n += THREADS) {
+        double vr = 0.0, vi = 0.0;
+        if (G > 1) {
+            for (int g = 0; g < G; ++g) {
+                vr += s_grp[g * N + n].x;
+                vi += s_grp[g * N + n].y;
+            }
+        } else {
+            const double2 v = sum(n, 0, 1);
+            vr = v.x;
+            vi = v.y;
         }
         vr *= inv;
         vi *= inv;
