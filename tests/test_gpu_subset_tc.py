@@ -173,6 +173,32 @@ def test_square_batch_side_draws(plans):
     assert rms_wrapped(outs1[0].cpu().numpy(), o["phase"]) < TOL_PHASE_RMS
 
 
+def test_square_batch_uneven_schedules(plans):
+    # side-stream mask draws when the holograms' schedules differ: compressed
+    # iterations ending at different steps, WGS (no compressed iteration), RS
+    # (no iteration), no full iteration before the final pass; each hologram
+    # equals its solo solve
+    tc, _ = plans
+    pbs = [workloads.problem(256, 60, 5.0, 0.125, 9, seed=500),
+           workloads.problem(384, 100, 5.0, 0.125, 3, seed=501),
+           workloads.problem(256, 40, 5.0, 1.0, 5, seed=502),
+           workloads.problem(200, 30, 5.0, 0.125, 0, seed=503),
+           workloads.problem(320, 129, 5.0, 0.25, 6, seed=504)]
+    pbs[4].extra["full_iterations"] = 0
+    outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+    b = tc.batch(pbs, outs)
+    for rep in range(2):
+        b.run()
+        res = b.results()
+        for pb, out, r in zip(pbs, outs, res):
+            kw = dict(full_iterations=pb.extra.get("full_iterations", 2))
+            o2 = torch.empty(pb.M, dtype=torch.float32, device="cuda")
+            s2 = tc.solve(pb.xyz, pb.P, pb.c, pb.iterations, pb.seed, out=o2, **kw)
+            assert rms_wrapped(out.cpu().numpy(), o2.cpu().numpy()) < TOL_PHASE_RMS
+            assert abs(r["e"] - s2["e"]) < TOL_EU and abs(r["u"] - s2["u"]) < TOL_EU
+    b.close()
+
+
 def test_serving(plans):
     # continuous batching: each admitted request gets a clear mask
     tc, cc = plans
