@@ -8,13 +8,16 @@ per iteration for the whole batch, replayed from a CUDA graph.
 
 Workload: 64 holograms of P = 1152 (M = 1152^2), N = 100 spots, alpha, beta
 ~ U[-P/4, P/4] cycles, gamma ~ U[-10, 10] waves, theta^0 ~ U[0, 2 pi), one
-seed per hologram.  Prints one JSON line (see README of the keys in
-the design doc): holograms/s, p50/p99 latency, the roofline of the iteration
-kernel against the SFU (sine/cosine) pipe, the FP64 GPU baseline, the FP64
-CPU oracle on a bounded sample, and an end-to-end number through the C ABI
-with host buffers.
+seed per hologram.  Prints one JSON line: holograms/s, p50/p99 latency, the
+roofline of the dominant iteration kernel (tensor cores: algorithmic flops
+against the measured dense BF16 peak; CUDA cores: sine/cosine results against
+the SFU peak, or complex multiply-adds against the FP32 peak), the FP64 GPU
+baseline with its per-hologram latency, the compressed-iteration sweep over
+N and c, the headline shape on a rotated 10 x 10 grid, the serving streams
+(Poisson arrivals of mixed requests), the FP64 CPU oracle on a bounded
+sample, and an end-to-end number through the C ABI with host buffers.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--quick]
 """
 from __future__ import annotations
 
@@ -38,14 +41,14 @@ METRIC = "holograms/s and p50/p99 latency at M=1152^2, N=100, e,u>=0.9 vs FP64 G
 SFU_PER_CLK_PER_SM = 16       # sine/cosine results per clock per SM (CUDA arithmetic throughput table)
 FP32_LANES_PER_SM = 128       # FP32 fused multiply-adds per clock per SM
 # DRAM bytes (read + write) per launch of the iteration kernels at the default
-# workload, from one ncu capture of this bench
-# (profiles/iter_kernels_b64_P1152_N100_launches.md), keyed by launch kind and
-# the kernel that ran it (the tile-shape marker): compressed launches on the
-# CUDA-core kernel (256 threads) or on the tensor cores, and full-pixel
-# launches on the warp-specialised tensor-core kernel (2 full iterations + the
-# final pass, averaged; the factor tables are read once per pass, the final
-# pass writes the phase maps).  Each is reported only while the sources of
-# its kernel hash to the value they had when it was measured.
+# workload, from an ncu capture of this bench (a summary sits with the kernel
+# profiles), keyed by launch kind and the kernel that ran it (the tile-shape
+# marker): compressed launches on the CUDA-core kernel (256 threads) or on the
+# tensor cores, and full-pixel launches on the warp-specialised tensor-core
+# kernel (2 full iterations + the final pass, averaged; the factor tables are
+# read once per pass, the final pass writes the phase maps).  Each is reported
+# only while the sources of its kernel hash to the value they had when it was
+# measured.
 TRAFFIC_MEASURED = {("sub", 256): {"sha": "3bdfbecac4b139e7", "bytes": 332928},
                     ("sub", 1): {"sha": "06a47301aabb66a8", "bytes": 257702391},
                     ("full", 2): {"sha": "06a47301aabb66a8", "bytes": 345754197}}
@@ -75,6 +78,26 @@ def measured_traffic(args, tile):
 # full_threads markers of the tensor-core kernels: kernel name, threads per block
 TC_KERNELS = {2: ("iter_full_tcws_kernel (warp-specialised: 8 epilogue warps, a producer warp, a GEMM 1 warp "
                    "and a GEMM 2 warp)", 352)}
+
+
+def kernel_name(tile, kind):
+    """The kernel a launch kind ran on, from the batch's launch shapes."""
+    if kind == "sub":
+        if tile["threads"] == SUBSET_TC:
+            return "iter_full_tcws_kernel (tensor cores: every pixel through both products, u zero outside S_j)"
+        return "iter_subset_kernel<%d, %d> (CUDA cores: the pixels of S_j only, direct phasors)" % (
+            tile["threads"], tile["pixels_per_thread"])
+    if tile["full_threads"] in TC_KERNELS:
+        return TC_KERNELS[tile["full_threads"]][0]
+    return "iter_full_kernel<%d> (CUDA cores, separable)" % tile["full_threads"]
+
+
+def dtype_label(tile):
+    """The arithmetic the path computes in: FP32, or FP32-class split-BF16
+    products accumulated in FP32 on the tensor cores."""
+    if tile["threads"] == SUBSET_TC or tile["full_threads"] in TC_KERNELS:
+        return "f32-class: split-bf16 x3 products, f32 accumulate (tensor cores); f32 epilogues; f64 e, u"
+    return "f32 (f64 e, u)"
 
 
 # threads marker of compressed iterations on the warp-specialised tensor-core
@@ -176,16 +199,19 @@ def parse():
     ap.add_argument("--N", type=int, default=100)
     ap.add_argument("--c", type=float, default=0.125)
     ap.add_argument("--iters", type=int, default=30)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (read, and written when tuning)")
-    ap.add_argument("--serve-rate", type=float, default=1000.0, help="Poisson arrival rate of the serving probe")
-    ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the serving probe's arrival stream")
-    ap.add_argument("--serve-mix", action="store_true",
-                    help="serve the mixed stream (P in {768,1024,1152}, N in {10,100,1000}, gamma +-20, 20 "
-                         "iterations) instead of the headline holograms")
+    ap.add_argument("--serve-rates", default="60,240",
+                    help="Poisson arrival rates (req/s) of the mixed serving streams")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of each mixed arrival stream")
+    ap.add_argument("--serve-headline-rate", type=float, default=1000.0,
+                    help="arrival rate of the extra stream of the batch workload's holograms (3 s)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the compressed-iteration sweep (N x c)")
+    ap.add_argument("--quick", action="store_true",
+                    help="short serving streams (5 s) and no oracle comparisons of the sweep")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-fp16", action="store_true")
     ap.add_argument("--no-scenarios", action="store_true")
@@ -279,10 +305,13 @@ class Clocks:
 
 
 # ------------------------------------------------------------- serving --
-def serve_probe(args, local, stream_handle):
+def serve_probe(args, local, rate, seconds, mix):
     """Continuous batching under a Poisson arrival stream: requests are submitted
     at their arrival times (cswgs_submit) and collected as they finish
-    (cswgs_wait); returns throughput and submit-to-result latency."""
+    (cswgs_wait); returns throughput and submit-to-result latency.  mix: the
+    serving workload's mixed requests (P in {768, 1024, 1152}, N uniform on
+    {10, 100, 1000}, i.e. log-uniform on that grid, gamma ~ U[-20, 20], c = 1/8,
+    20 iterations); else the batch workload's holograms."""
     import queue
     import threading
 
@@ -290,15 +319,16 @@ def serve_probe(args, local, stream_handle):
 
     from paper_2003_05293_gb300 import Plan
 
-    if args.serve_mix:
-        stream = workloads.arrivals(args.serve_rate, args.serve_seconds, seed=7)
-        what = "mixed: P in {768,1024,1152}, N in {10,100,1000}, gamma~U[-20,20], c=1/8, 20 iterations"
+    if mix:
+        stream = workloads.arrivals(rate, seconds, seed=7)
+        what = ("mixed: P in {768,1024,1152}, N uniform on {10,100,1000} (log-uniform on that grid), "
+                "gamma~U[-20,20], c=1/8, 20 iterations")
     else:
         rng = np.random.Generator(np.random.PCG64(7))
         t, stream = 0.0, []
         while True:
-            t += float(rng.exponential(1.0 / args.serve_rate))
-            if t >= args.serve_seconds:
+            t += float(rng.exponential(1.0 / rate))
+            if t >= seconds:
                 break
             stream.append((t, workloads.problem(args.P, args.N, 10.0, args.c, args.iters, seed=10**6 + len(stream))))
         what = "P=%d, N=%d, c=%g, %d iterations (the batch workload's holograms)" % (args.P, args.N, args.c, args.iters)
@@ -339,7 +369,7 @@ def serve_probe(args, local, stream_handle):
     plan.close()
     lat = [r["latency_ms"] for r in results if r["status"] == 0]
     qms = [r["queue_ms"] for r in results if r["status"] == 0]
-    return {"what": what, "rate_hz": args.serve_rate, "seconds": args.serve_seconds, "requests": len(stream),
+    return {"what": what, "rate_hz": rate, "seconds": seconds, "requests": len(stream),
             "completed": len(lat), "holograms_per_s": len(lat) / wall,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(np.max(lat))},
@@ -444,6 +474,144 @@ def run_compare(args, local):
           flush=True)
 
 
+def timed_batch(plan, pbs, outs, flush, stream, steps, warmup, world):
+    """Device time (ms, max over ranks) of `steps` graph replays of a batch, an
+    L2 flush before each (CUDA events on the plan's stream); the results, the
+    per-launch times of the last run and the launch shapes."""
+    import torch
+    b = plan.batch(pbs, outs)
+    for _ in range(warmup):
+        flush.fill_(1)
+        b.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        flush.fill_(1)
+        b.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    res, kt, tile = b.results(), b.kernel_times(), b.tile_shape()
+    b.close()
+    return ms, res, kt, tile
+
+
+def fp64_latency(p64, pbs, stream):
+    """The plain FP64 solver, one hologram at a time: device time of each solve
+    (CUDA events on the plan's stream), holograms/s and p50/p99."""
+    import torch
+    o = torch.empty(max(pb.M for pb in pbs), dtype=torch.float32, device="cuda")
+    pb = pbs[0]
+    p64.solve(pb.xyz, pb.P, pb.c, 2, pb.seed, out=o[:pb.M])      # warm-up
+    torch.cuda.synchronize()
+    ts = []
+    for pb in pbs:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p64.solve(pb.xyz, pb.P, pb.c, pb.iterations, pb.seed, out=o[:pb.M])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return {"value": 1e3 * len(ts) / sum(ts), "unit": "holograms/s", "holograms": len(ts),
+            "latency_ms": {"p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99)),
+                           "all": [round(t, 2) for t in ts]},
+            "what": "plain double-precision kernels, one hologram per solve (device time of each)"}
+
+
+def parity_entry(phase, res, ref, which):
+    d = (np.asarray(phase, dtype=np.float64) - ref["phase"] + np.pi) % (2 * np.pi) - np.pi
+    return {"hologram": which, "phase_rms_rad": float(np.sqrt(np.mean(d * d))),
+            "abs_de": abs(res["e"] - ref["e"]), "abs_du": abs(res["u"] - ref["u"]),
+            "tolerance": {"phase_rms_rad": 1e-3, "abs_de": 1e-3, "abs_du": 1e-3}}
+
+
+def e2e_leg(args, plan, pbs, world, B):
+    """End to end through the C ABI's host-buffer batches: every step copies its
+    hologram requests' spots (host) in and its phase maps and e, u (host) out.
+    Two batches alternate (update and run one, collect the other), so one
+    batch's map copies overlap the other's computation.  Timed with the host
+    clock over K steps, inputs staged and outputs written inside the region."""
+    import torch
+
+    def run(make_out):
+        outs = [[make_out(pb) for pb in pbs] for _ in range(2)]
+        hb = [plan.host_batch(pbs, outs[0]), plan.host_batch(pbs, outs[1])]
+        steps = [[workloads.Problem(P=pb.P, xyz=pb.xyz, amp=pb.amp, c=pb.c, iterations=pb.iterations,
+                                    seed=pb.seed + 7919 * k) for pb in pbs] for k in range(args.e2e_steps)]
+        for b in hb:                      # warm-up: graph capture, first copies
+            b.run()
+        for b in hb:
+            b.results()
+        torch.cuda.synchronize()
+        max_over_ranks(0.0, world, "cuda")
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            b = hb[k % 2]
+            if k >= 2:
+                b.results()
+            b.update(steps[k], outs[k % 2])
+            b.run()
+        for k in range(max(0, args.e2e_steps - 2), args.e2e_steps):
+            hb[k % 2].results()
+        dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        for b in hb:
+            b.close()
+        return B * world * args.e2e_steps / dt
+    v_pageable = run(lambda pb: np.empty(pb.M, dtype=np.float32))
+    v_pinned = run(lambda pb: torch.empty(pb.M, dtype=torch.float32, pin_memory=True).numpy())
+    return {"value": max(v_pageable, v_pinned), "unit": "holograms/s",
+            "h2d_bytes_per_step": int(sum(pb.N * 3 * 8 for pb in pbs)),
+            "d2h_bytes_per_step": int(sum(pb.M * 4 + 16 for pb in pbs)),
+            "api": "cswgs_batch_create_host / cswgs_batch_update / cswgs_batch_run / cswgs_batch_results: host "
+                   "spot arrays in (staged through pinned memory), host phase maps and e, u out; two batches "
+                   "alternate so that one's copies overlap the other's computation",
+            "steps": args.e2e_steps, "pageable_host_outputs": v_pageable, "pinned_host_outputs": v_pinned}
+
+
+def sweep_leg(args, plan, flush, stream, world, B, rank, local):
+    """The precision workload's compressed-iteration sweep at P = args.P: N in
+    {100, 300} x c in {1/4, 1/8, 1/16}, a batch of B holograms each (the
+    autotuner picks the kernels per c), with per-launch times; the FP64 GPU
+    solver at the same shape.  Returns the entries and, per (N, c), the first
+    hologram's problem, map and result for the oracle comparison."""
+    import torch
+
+    from paper_2003_05293_gb300 import Plan
+    runs, keep = [], {}
+    n_sub = args.iters - min(2, args.iters)
+    with Plan(device=local, precision="fp64", stream=stream.cuda_stream) as p64:
+        for N in workloads.LARGE_N:
+            for c in workloads.LARGE_C:
+                pbs = [workloads.problem(args.P, N, 10.0, c, args.iters, seed=rank * 100000 + 50000 + h)
+                       for h in range(B)]
+                outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+                ms, res, kt, tile = timed_batch(plan, pbs, outs, flush, stream, max(3, args.steps // 2),
+                                                args.warmup, world)
+                steps = max(3, args.steps // 2)
+                sub_ms = sum(kt[1:1 + n_sub]) / max(1, n_sub)
+                full_ms = sum(kt[1 + n_sub:]) / max(1, len(kt) - 1 - n_sub)
+                Mp = math.floor(c * args.P * args.P)
+                pairs = B * 2.0 * N * Mp
+                entry = {"N": N, "c": c, "value": job_throughput(B, world, steps, ms), "unit": "holograms/s",
+                         "ms_per_step": ms / steps, "compressed_ms_per_launch": sub_ms,
+                         "full_ms_per_launch": full_ms,
+                         "compressed_kernel": kernel_name(tile, "sub"),
+                         "compressed_method_tflops": 8.0 * pairs / (sub_ms * 1e-3) / 1e12,
+                         "e_mean": float(np.mean([r["e"] for r in res])),
+                         "u_mean": float(np.mean([r["u"] for r in res])), "tile": tile}
+                entry["fp64_gpu"] = fp64_latency(p64, pbs[:3 if N * c > 50 else 5], stream)
+                keep[(N, c)] = (pbs[0], outs[0].cpu().numpy(), res[0])
+                runs.append(entry)
+                del outs
+    return {"P": args.P, "batch": B, "iterations": args.iters,
+            "what": "compressed-iteration sweep of the precision workload: a batch per (N, c), FP32 path as tuned; "
+                    "compressed_method_tflops counts 8 flops per subset pixel-spot pair and pass",
+            "runs": runs}, keep
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -515,13 +683,12 @@ def main():
     # per-launch device times of the last timed step (events inside the graph)
     kts = [batch.kernel_times()]
 
-    # rooflines of the iteration kernel, per launch kind (measured live, CUDA
-    # events around every launch of every timed step):
-    #  - compressed iterations: direct phasors, 2 SFU results (sin, cos) per
-    #    pixel-spot pair and pass -> against the SFU peak;
-    #  - full iterations and the final pass: separable phasors, one complex
-    #    multiply-add (8 flops) per pixel-spot pair and pass -> against the FP32
-    #    FMA peak.
+    # rooflines of the iteration kernels, per launch kind (measured live, CUDA
+    # events recorded inside the graph around every launch of the last timed
+    # step): on the tensor cores algorithmic flops (8 per pixel-spot pair and
+    # pass) against the measured dense BF16 peak; on the CUDA cores 2 SFU
+    # results per pair and pass (compressed launches) against the SFU peak, or
+    # 8 flops per pair and pass (separable full passes) against the FP32 peak.
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
     max_mhz = 2070.0
@@ -545,7 +712,7 @@ def main():
     eu = [(r["e"], r["u"]) for r in res]
     line = {"metric": METRIC, "value": value, "unit": "holograms/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(tile), "data": "synthetic",
             "config": workload_config(args, {"l2": "flushed between steps (256 MB write), inside the timed region",
                                              "parallelism": "replicas" if world > 1 else "single GPU"}),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -600,43 +767,39 @@ def main():
         b16.close()
         p16.close()
 
-    # FP64 GPU baseline (plain double-precision kernels), one hologram at a time
+    # FP64 GPU baseline (plain double-precision kernels), one hologram at a time:
+    # per-hologram device time (CUDA events on the plan's stream)
     if not args.no_fp64:
-        with Plan(device=local, precision="fp64") as p64:
-            pb = pbs[0]
-            o = torch.empty(pb.M, dtype=torch.float32, device="cuda")
-            p64.solve(pb.xyz, pb.P, pb.c, 2, pb.seed, out=o)      # warm-up
-            torch.cuda.synchronize()
-            n64, t0 = 0, time.perf_counter()
-            while n64 < 2:
-                p64.solve(pbs[n64].xyz, pb.P, pb.c, pb.iterations, pbs[n64].seed, out=o)
-                n64 += 1
-            torch.cuda.synchronize()
-            v64 = n64 / (time.perf_counter() - t0)
-        line["fp64_gpu_baseline"] = {"value": v64, "unit": "holograms/s", "holograms": n64,
-                                     "speedup_fp32_batched": value / v64 / world}
+        with Plan(device=local, precision="fp64", stream=stream.cuda_stream) as p64:
+            fp = fp64_latency(p64, pbs[:6], stream)
+        fp["speedup_fp32_batched"] = value / fp["value"] / world
+        line["fp64_gpu_baseline"] = fp
 
     # end to end through the C ABI: host inputs in, host phase maps and e, u out
     if not args.no_e2e:
-        def e2e_run(host_outs):
-            plan.solve_batch(pbs, host_outs)
-            torch.cuda.synchronize()
-            barrier()
-            t0 = time.perf_counter()
-            for _ in range(args.e2e_steps):
-                plan.solve_batch(pbs, host_outs)
-            return B * world * args.e2e_steps / max_over_ranks(time.perf_counter() - t0, world, "cuda")
-        # the phase maps go to ordinary (pageable) numpy arrays; the inputs are
-        # staged by the library through its own pinned block.  Pinned output
-        # buffers, measured beside them, are slower on this host.
-        v_pageable = e2e_run([np.empty(pb.M, dtype=np.float32) for pb in pbs])
-        v_pinned = e2e_run([torch.empty(pb.M, dtype=torch.float32, pin_memory=True).numpy() for pb in pbs])
-        line["e2e"] = {"value": v_pageable, "unit": "holograms/s",
-                       "h2d_bytes_per_step": int(sum(pb.N * 3 * 8 for pb in pbs)),
-                       "d2h_bytes_per_step": int(sum(pb.M * 4 + 16 for pb in pbs)),
-                       "api": "cswgs_solve_batch: host spot arrays in (staged through pinned memory), host phase "
-                              "maps and e, u out",
-                       "pinned_host_outputs": v_pinned}
+        line["e2e"] = e2e_leg(args, plan, pbs, world, B)
+
+    # the headline shape on the paper's regular pattern (a rotated 10 x 10 grid,
+    # one orientation and initial phase per hologram), where e, u >= 0.9 hold
+    gpbs = [workloads.scenario("grid100", args.P, seed=rank * 100000 + h, c=args.c, iterations=args.iters)
+            for h in range(B)]
+    gouts = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in gpbs]
+    gms, gres, gkt, _ = timed_batch(plan, gpbs, gouts, flush, stream, args.steps, args.warmup, world)
+    line["headline_grid100"] = {
+        "value": job_throughput(B, world, args.steps, gms), "unit": "holograms/s", "ms_per_step": gms / args.steps,
+        "e_mean": float(np.mean([r["e"] for r in gres])), "e_min": float(np.min([r["e"] for r in gres])),
+        "u_mean": float(np.mean([r["u"] for r in gres])), "u_min": float(np.min([r["u"] for r in gres])),
+        "what": "the headline batch shape (%d holograms, P=%d, N=100, c=%g, %d iterations) on rotated 10 x 10 "
+                "spot grids (one orientation and initial phase per hologram)" % (B, args.P, args.c, args.iters)}
+    del gouts
+
+    # the compressed-iteration sweep of the precision workload: N in {100, 300}
+    # x c in {1/4, 1/8, 1/16} at P = 1152, a batch each, the FP64 GPU solver
+    # at the same shape; the first hologram of each is compared with the oracle
+    # in the CPU leg below
+    sweep_keep = {}
+    if not args.no_sweep:
+        line["compressed_sweep"], sweep_keep = sweep_leg(args, plan, flush, stream, world, B, rank, local)
 
     # the paper's scenarios (Section 5): 10 orientations and initial phases of
     # each, as one batch through the same path
@@ -705,9 +868,14 @@ def main():
                     "table) into its own %d x %d panel buffer" % (waist, W, Hh)}
         del frames
 
-    # continuous-batching server under a Poisson arrival stream
+    # continuous-batching server under Poisson arrival streams: the serving
+    # workload's mixed requests at each rate, and an extra stream of the batch
+    # workload's holograms
     if not args.no_serve:
-        line["serve"] = serve_probe(args, local, stream.cuda_stream)
+        secs = 5.0 if args.quick else args.serve_seconds
+        runs = [serve_probe(args, local, float(r), secs, True) for r in args.serve_rates.split(",") if r]
+        runs.append(serve_probe(args, local, args.serve_headline_rate, 3.0, False))
+        line["serve"] = runs
 
     # the FP64 CPU oracle on a bounded sample (rank 0, single GPU runs only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -718,16 +886,17 @@ def main():
         dt = time.perf_counter() - t0
         # the same hologram from the timed batch against the oracle (wrapped phase
         # RMS over the map, e and u)
-        ph = outs[0].cpu().numpy().astype(np.float64)
-        d = (ph - ref["phase"] + np.pi) % (2 * np.pi) - np.pi
-        line["parity_vs_oracle"] = {"hologram": "the batch's first (P=%d, N=%d)" % (pb.P, pb.N),
-                                    "phase_rms_rad": float(np.sqrt(np.mean(d * d))),
-                                    "abs_de": abs(res[0]["e"] - ref["e"]), "abs_du": abs(res[0]["u"] - ref["u"]),
-                                    "tolerance": {"phase_rms_rad": 1e-3, "abs_de": 1e-3, "abs_du": 1e-3}}
+        line["parity_vs_oracle"] = parity_entry(outs[0].cpu().numpy(), res[0], ref,
+                                                "the batch's first (P=%d, N=%d)" % (pb.P, pb.N))
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "holograms/s", "cores": oracle.threads(),
                                 "kind": "oracle",
                                 "sample": "1 hologram of the workload (P=%d, N=%d, c=%g, %d iterations), FP64 C "
                                           "with OpenMP, %.1f s" % (pb.P, pb.N, pb.c, pb.iterations, dt)}
+        if not args.quick:
+            for entry in line.get("compressed_sweep", {}).get("runs", []):
+                q, ph, r = sweep_keep[(entry["N"], entry["c"])]
+                ref = oracle.solve(q.P, q.xyz, c=q.c, iterations=q.iterations, seed=q.seed)
+                entry["parity_vs_oracle"] = parity_entry(ph, r, ref, "the batch's first")
     batch.close()
     plan.close()
     if rank == 0:

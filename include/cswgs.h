@@ -295,6 +295,36 @@ cswgs_status cswgs_batch_tile_shape(cswgs_batch b, int *threads, int *pixels_per
 
 cswgs_status cswgs_batch_destroy(cswgs_batch b);
 
+/* Host-buffer batches: the end-to-end form of a batch, for a caller whose
+ * spots and phase maps live in host memory and who solves batch after batch
+ * (the method is that of cswgs_batch_create; this form only moves the data).
+ * As cswgs_batch_create, except that:
+ *  - every request with a phase map asks for a host one (out_on_host = 1;
+ *    pinned memory, or pageable memory on a device that shares the host's
+ *    page tables, is written by a copy kernel, other memory by cudaMemcpyAsync);
+ *  - the batch runs on a stream of its own (not the plan's): each
+ *    cswgs_batch_run queues on it the copy of the staged inputs to the device,
+ *    the batch's graph, e and u into a pinned host block and the phase maps to
+ *    their host buffers, and returns at once;
+ *  - cswgs_batch_results waits for that stream and reports e and u.
+ * Two host batches made from one plan overlap on the device: while one copies
+ * its phase maps out, the other computes.  A caller who alternates them
+ * (update, run one; collect the other's results) keeps the copies off the
+ * device's critical path.  Ownership: the host phase maps must stay valid
+ * until cswgs_batch_results of the run that writes them returns. */
+cswgs_status cswgs_batch_create_host(cswgs_plan p, const cswgs_request *reqs, int count,
+                                     cswgs_batch *out);
+
+/* New inputs and outputs for the next run of a host-buffer batch: spots_xyz,
+ * amplitudes, seed and phase_out (host, or NULL: not written) of each of the
+ * `count` requests are taken; the spots are copied into the batch's pinned
+ * staging block at the call (the caller may reuse its arrays on return).
+ * N, P, subset_fraction, iterations, full_iterations and the pupil must be
+ * those the batch was made with (CSWGS_EINVAL otherwise).  Blocks until the
+ * batch's last run has read its staged inputs (the start of that run), not
+ * until it finishes.  CSWGS_EINVAL for a batch of cswgs_batch_create. */
+cswgs_status cswgs_batch_update(cswgs_batch b, const cswgs_request *reqs, int count);
+
 /* Runs `count` requests (host or device outputs) as one batch, synchronous:
  * the convenience form of create + run + results + destroy, reusing a cached
  * graph when the batch has the same shape as an earlier call. */
@@ -369,6 +399,10 @@ cswgs_status cswgs_sincos_peak(cswgs_plan p, double *sincos_per_s, double *sm_mh
  * the work is queued: synchronise the stream before reading the outputs.
  * The first call on a device looks up the array's device address and the
  * kernel's launch limits; make that first call before any stream capture.
+ * The look-up belongs to the device's CUDA context: after the caller destroys
+ * that context (cudaDeviceReset), the next call looks up again, so that call
+ * too must come before any stream capture.  Launch errors are read without
+ * clearing an error the caller left pending (that error is reported).
  * Every call shares the array and leaves its contents behind (each call
  * clears the parts that must start at zero); calls whose work overlaps on the
  * GPU race on it and must be serialised by the caller. */

@@ -267,6 +267,15 @@ class Plan:
               "cswgs_batch_create")
         return Batch(self, h, len(problems), keep + [outs])
 
+    def host_batch(self, problems, outs=None) -> "HostBatch":
+        """cswgs_batch_create_host: a batch with host inputs and host phase maps
+        (numpy float32 arrays, or None) that runs on a stream of its own."""
+        reqs, keep = self._requests(problems, outs)
+        h = ctypes.c_void_p()
+        check(self.lib.cswgs_batch_create_host(self.handle, reqs, len(problems), ctypes.byref(h)),
+              "cswgs_batch_create_host")
+        return HostBatch(self, h, len(problems), keep + [outs])
+
     def solve_batch(self, problems, outs=None):
         reqs, keep = self._requests(problems, outs)
         res = (cswgs_result * len(problems))()
@@ -367,3 +376,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class HostBatch(Batch):
+    """A cswgs_batch of cswgs_batch_create_host: host spots in, host phase maps
+    out, on the batch's own stream (run() returns once the work is queued)."""
+
+    def update(self, problems, outs=None):
+        """cswgs_batch_update: the next run's spots, seeds and host phase maps."""
+        reqs, keep = self.plan._requests(problems, outs)
+        check(self.lib.cswgs_batch_update(self.handle, reqs, len(problems)), "cswgs_batch_update")
+        # the previous run may still write its maps: its buffers stay referenced
+        # until the run after this one is set up
+        self._keep = [self._keep[-1] if self._keep else None, keep + [outs]]

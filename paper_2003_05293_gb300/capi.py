@@ -100,6 +100,9 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int64)]),
     "cswgs_batch_create": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_request), ctypes.c_int,
                                           ctypes.POINTER(_P)]),
+    "cswgs_batch_create_host": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_request), ctypes.c_int,
+                                               ctypes.POINTER(_P)]),
+    "cswgs_batch_update": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_request), ctypes.c_int]),
     "cswgs_batch_run": (ctypes.c_int, [_P]),
     "cswgs_batch_results": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_result)]),
     "cswgs_batch_kernel_times": (ctypes.c_int, [_P, c_float_p, ctypes.c_int,

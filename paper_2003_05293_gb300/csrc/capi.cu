@@ -205,7 +205,35 @@ static cswgs_status set_device(cswgs_plan_s *p)
     return CSWGS_OK;
 }
 
+// e and u of every hologram of a batch into one host block (pinned memory,
+// written through its device address): one launch instead of a copy per
+// hologram.
+__global__ void eu_gather_kernel(const HoloDev *__restrict__ holos, int count, double *dst)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        dst[2 * i] = holos[i].metrics[0];
+        dst[2 * i + 1] = holos[i].metrics[1];
+    }
+}
+
+// A request of a host-buffer batch's update must keep the batch's shape.
+static bool same_shape(const HoloSpec &a, const HoloSpec &b)
+{
+    return a.P == b.P && a.N == b.N && a.Mp == b.Mp && a.iterations == b.iterations && a.n_full == b.n_full &&
+           a.has_amp == b.has_amp && a.aperture == b.aperture && a.windows == b.windows && a.waist == b.waist &&
+           a.has_slm == b.has_slm;
+}
+
 }  // namespace cswgs
+
+cswgs_batch_s::~cswgs_batch_s()
+{
+    if (stream) cudaStreamSynchronize(stream);
+    b.reset();
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (eu_host) cudaFreeHost(eu_host);
+    if (stream) cudaStreamDestroy(stream);
+}
 
 using namespace cswgs;
 
@@ -493,7 +521,109 @@ cswgs_status cswgs_batch_run(cswgs_batch b)
     cswgs_plan_s *p = b->plan;
     std::lock_guard<std::mutex> lk(p->mu);
     CSWGS_TRY(set_device(p));
-    return batch_enqueue(b->b.get(), p->stream);
+    if (!b->host) return batch_enqueue(b->b.get(), p->stream);
+    // host-buffer batch, all on its own stream: staged inputs in, the graph,
+    // e and u out, the phase maps out
+    Fp32Batch *fb = b->b.get();
+    cudaStream_t s = b->stream;
+    CSWGS_TRY(batch_upload_inputs(fb, s));
+    CSWGS_CUDA_TRY(cudaEventRecord(b->ev_in, s));
+    CSWGS_TRY(batch_enqueue(fb, s));
+    eu_gather_kernel<<<1, 128, 0, s>>>(fb->holos_d.as<HoloDev>(), b->count, b->eu_host);
+    CSWGS_CUDA_TRY(cudaGetLastError());
+    std::vector<MapCopy> jobs;
+    for (int i = 0; i < b->count; ++i) {
+        float *dst = b->host_out[i];
+        if (!dst) continue;
+        const size_t n = (size_t)fb->specs[i].P * fb->specs[i].P;
+        if (float *d = host_direct(p, dst))
+            jobs.push_back(MapCopy{fb->own_phase[i], d, n});
+        else
+            CSWGS_CUDA_TRY(cudaMemcpyAsync(dst, fb->own_phase[i], sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    }
+    return copy_maps(p, b->jobs, jobs, s);
+}
+
+static cswgs_status host_batch_fill(cswgs_batch b, const cswgs_request *reqs, std::vector<HoloSpec> &specs,
+                                    bool first)
+{
+    Fp32Batch *fb = b->b.get();
+    bool changed = false;
+    for (int i = 0; i < b->count; ++i) {
+        if (!first) {
+            if (!same_shape(specs[i], fb->specs[i]) || (reqs[i].out_on_host == 0 && reqs[i].phase_out))
+                return set_error(CSWGS_EINVAL, "request %d: a host batch's update keeps each hologram's shape "
+                                               "(N, P, c, iterations, pupil) and takes host phase maps only", i);
+            fb->specs[i].xyz = std::move(specs[i].xyz);
+            fb->specs[i].amp = std::move(specs[i].amp);
+            fb->specs[i].seed = specs[i].seed;
+            if (fb->holos[i].seed != fb->specs[i].seed) {
+                fb->holos[i].seed = fb->specs[i].seed;
+                changed = true;
+            }
+            batch_restage(fb, i);
+        }
+        b->host_out[i] = reqs[i].phase_out;
+    }
+    if (changed)
+        CSWGS_CUDA_TRY(cudaMemcpyAsync(fb->holos_d.p, fb->holos.data(), sizeof(HoloDev) * b->count,
+                                       cudaMemcpyHostToDevice, b->stream));
+    return CSWGS_OK;
+}
+
+cswgs_status cswgs_batch_create_host(cswgs_plan p, const cswgs_request *reqs, int count, cswgs_batch *out)
+{
+    if (!p || !out) return set_error(CSWGS_EINVAL, "NULL plan or output");
+    *out = nullptr;
+    if (p->desc.precision == CSWGS_FP64)
+        return set_error(CSWGS_EINVAL, "graph batches run the FP32 solver; this plan is FP64");
+    std::vector<HoloSpec> specs;
+    CSWGS_TRY(specs_from_requests(p, reqs, count, &specs));
+    for (int i = 0; i < count; ++i)
+        if (!reqs[i].out_on_host && reqs[i].phase_out)
+            return set_error(CSWGS_EINVAL, "request %d: a host batch writes host phase maps only", i);
+    std::lock_guard<std::mutex> lk(p->mu);
+    CSWGS_TRY(set_device(p));
+    auto *bb = new (std::nothrow) cswgs_batch_s();
+    if (!bb) return set_error(CSWGS_ENOMEM, "host allocation");
+    bb->plan = p;
+    bb->count = count;
+    bb->host = true;
+    bb->host_out.assign(count, nullptr);
+    cswgs_status st = batch_build_host(p, specs, true, true, &bb->b);
+    auto cuda = [&](cudaError_t e, const char *what) {
+        if (st == CSWGS_OK && e != cudaSuccess)
+            st = set_error(e == cudaErrorMemoryAllocation ? CSWGS_ENOMEM : CSWGS_ECUDA, "%s: %s", what,
+                           cudaGetErrorString(e));
+    };
+    if (st == CSWGS_OK) cuda(cudaStreamCreateWithFlags(&bb->stream, cudaStreamNonBlocking), "stream");
+    if (st == CSWGS_OK) cuda(cudaEventCreateWithFlags(&bb->ev_in, cudaEventDisableTiming), "event");
+    if (st == CSWGS_OK)
+        cuda(cudaMallocHost(reinterpret_cast<void **>(&bb->eu_host), sizeof(double) * 2 * count), "pinned e, u");
+    if (st == CSWGS_OK) st = host_batch_fill(bb, reqs, specs, true);
+    if (st == CSWGS_OK) st = batch_set_outputs(bb->b.get(), std::vector<float *>(count, nullptr), bb->stream);
+    if (st == CSWGS_OK) cuda(cudaStreamSynchronize(bb->stream), "set-up");
+    if (st != CSWGS_OK) {
+        delete bb;
+        return st;
+    }
+    *out = bb;
+    return CSWGS_OK;
+}
+
+cswgs_status cswgs_batch_update(cswgs_batch b, const cswgs_request *reqs, int count)
+{
+    if (!b || !reqs) return set_error(CSWGS_EINVAL, "NULL batch or requests");
+    if (!b->host) return set_error(CSWGS_EINVAL, "cswgs_batch_update takes a batch of cswgs_batch_create_host");
+    if (count != b->count) return set_error(CSWGS_EINVAL, "update of %d holograms for a batch of %d", count, b->count);
+    cswgs_plan_s *p = b->plan;
+    std::vector<HoloSpec> specs;
+    CSWGS_TRY(specs_from_requests(p, reqs, count, &specs));
+    std::lock_guard<std::mutex> lk(p->mu);
+    CSWGS_TRY(set_device(p));
+    // the staging block is rewritten: the last run must have copied it in
+    CSWGS_CUDA_TRY(cudaEventSynchronize(b->ev_in));
+    return host_batch_fill(b, reqs, specs, false);
 }
 
 cswgs_status cswgs_batch_results(cswgs_batch b, cswgs_result *results)
@@ -503,6 +633,19 @@ cswgs_status cswgs_batch_results(cswgs_batch b, cswgs_result *results)
     std::lock_guard<std::mutex> lk(p->mu);
     CSWGS_TRY(set_device(p));
     Fp32Batch *fb = b->b.get();
+    if (b->host) {
+        CSWGS_TRY(batch_status(fb, b->stream));   // synchronises the batch's stream
+        float ms = 0.f;
+        if (fb->timing) cudaEventElapsedTime(&ms, fb->events.front(), fb->events.back());
+        for (int i = 0; i < b->count; ++i) {
+            results[i].status = CSWGS_OK;
+            results[i].e = b->eu_host[2 * i];
+            results[i].u = b->eu_host[2 * i + 1];
+            results[i].latency_ms = ms;
+            results[i].queue_ms = 0.0;
+        }
+        return CSWGS_OK;
+    }
     std::vector<double> eu(2 * b->count);
     for (int i = 0; i < b->count; ++i)
         CSWGS_CUDA_TRY(cudaMemcpyAsync(&eu[2 * i], fb->holos[i].metrics, 2 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -562,10 +705,9 @@ cswgs_status cswgs_batch_destroy(cswgs_batch b)
     {
         std::lock_guard<std::mutex> lk(p->mu);
         cudaSetDevice(p->device);
-        cudaStreamSynchronize(p->stream);
-        b->b.reset();
+        cudaStreamSynchronize(b->host ? b->stream : p->stream);
+        delete b;
     }
-    delete b;
     return CSWGS_OK;
 }
 

@@ -72,29 +72,64 @@ __global__ void noalloc_prep_kernel(HoloDev H)
 
 // Set-up of one device, done by the first call on it: the scratch array's
 // device address (in host code its name is only a stand-in), the kernel's
-// shared-memory limit and its resident grid.
+// shared-memory limit and its resident grid.  The set-up belongs to the
+// device's current CUDA context: a caller that destroys the primary context
+// (cudaDeviceReset) gets a new one, whose first call here runs the set-up
+// again instead of using an address of the old context.
 struct NoAllocDevice {
-    std::once_flag once;
-    cudaError_t err = cudaSuccess;
+    std::mutex mu;
+    bool ready = false;
+    unsigned long long ctx = 0;   // id of the context the set-up was made in
     unsigned char *base = nullptr;
     int grid = 0;
 };
 static NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
-static void noalloc_setup(NoAllocDevice &d, int device)
+// Id of the calling thread's current context (driver entry points looked up
+// through the runtime, so the library needs no link to the driver library).
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+static cudaError_t current_context_id(unsigned long long *id)
 {
-    d.err = cudaGetSymbolAddress(reinterpret_cast<void **>(&d.base), g_noalloc_scratch);
-    if (d.err != cudaSuccess) return;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        err = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void **>(&get_current), 12000,
+                                               cudaEnableDefault, &q1);
+        if (err == cudaSuccess)
+            err = cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void **>(&get_id), 12000,
+                                                   cudaEnableDefault, &q2);
+        if (err == cudaSuccess && (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess))
+            err = cudaErrorNotSupported;
+    });
+    if (err != cudaSuccess) return err;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return cudaErrorDeviceUninitialized;
+    if (get_id(ctx, id) != 0) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
+static cudaError_t noalloc_setup(NoAllocDevice &d, int device)
+{
+    unsigned char *base = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(reinterpret_cast<void **>(&base), g_noalloc_scratch);
+    if (err != cudaSuccess) return err;
     const size_t smem = tile_smem_bytes(kNoAllocThreads, kNoAllocMaxN, true);
-    d.err = cudaFuncSetAttribute(noalloc_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (d.err != cudaSuccess) return;
+    err = cudaFuncSetAttribute(noalloc_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
     int per_sm = 0, sms = 0;
-    d.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_iter_kernel, kNoAllocThreads, smem);
-    if (d.err != cudaSuccess) return;
-    d.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (d.err != cudaSuccess) return;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_iter_kernel, kNoAllocThreads, smem);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (err != cudaSuccess) return err;
+    if (per_sm * sms <= 0) return cudaErrorInvalidConfiguration;
+    d.base = base;
     d.grid = per_sm * sms;
-    if (d.grid <= 0) d.err = cudaErrorInvalidConfiguration;
+    return cudaSuccess;
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -123,6 +158,8 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
     const int tp = kNoAllocThreads * kNoAllocPPT;
     const int full_tiles = full_pass_tiles(P, kNoAllocThreads);
     const int sub_tiles = (Mp + tp - 1) / tp;
+    // iterations write FP32 tile partials (compressed or full-pixel tiles);
+    // only the final pass writes the FP64 ones
     const size_t tiles = (size_t)(sub_tiles > full_tiles ? sub_tiles : full_tiles);
     size_t off = 0;
     const size_t o_queue = off; off += 256;
@@ -130,7 +167,7 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
     const size_t o_coef = off; off += al256(sizeof(int4) * N);
     const size_t o_state = off; off += al256(sizeof(SpotState) * N);
     const size_t o_part = off; off += al256(sizeof(float2) * tiles * N);
-    const size_t o_part64 = off; off += al256(sizeof(double2) * tiles * N);
+    const size_t o_part64 = off; off += al256(sizeof(double2) * (size_t)full_tiles * N);
     const size_t o_metrics = off; off += al256(sizeof(double) * (2 + N));
     if (off > kNoAllocScratchBytes)
         return set_error(CSWGS_EINVAL, "P=%d, N=%d needs %zu scratch bytes; the allocation-free solve has %zu", P, N,
@@ -140,12 +177,30 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
     CSWGS_CUDA_TRY(cudaGetDevice(&device));
     if (device < 0 || device >= kNoAllocMaxDevices)
         return set_error(CSWGS_EINVAL, "device %d beyond the %d supported", device, kNoAllocMaxDevices);
+    // the caller's current context, or the device's primary context when the
+    // thread has none yet (cudaSetDevice binds it and allocates nothing)
+    unsigned long long ctx = 0;
+    if (current_context_id(&ctx) != cudaSuccess) {
+        CSWGS_CUDA_TRY(cudaSetDevice(device));
+        CSWGS_CUDA_TRY(current_context_id(&ctx));
+    }
     NoAllocDevice &d = g_noalloc_dev[device];
-    std::call_once(d.once, noalloc_setup, std::ref(d), device);
-    if (d.err != cudaSuccess)
-        return set_error(CSWGS_ECUDA, "allocation-free solve set-up on device %d: %s", device, cudaGetErrorString(d.err));
-
-    unsigned char *b = d.base;
+    unsigned char *b = nullptr;
+    int dgrid = 0;
+    {
+        std::lock_guard<std::mutex> lk(d.mu);
+        if (!d.ready || d.ctx != ctx) {
+            d.ready = false;
+            const cudaError_t e = noalloc_setup(d, device);
+            if (e != cudaSuccess)
+                return set_error(CSWGS_ECUDA, "allocation-free solve set-up on device %d: %s", device,
+                                 cudaGetErrorString(e));
+            d.ctx = ctx;
+            d.ready = true;
+        }
+        b = d.base;
+        dgrid = d.grid;
+    }
     HoloDev H;
     std::memset(&H, 0, sizeof H);
     H.P = P;
@@ -168,9 +223,10 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CSWGS_CUDA_TRY(cudaMemsetAsync(b, 0, 512, s));   // work queue and arrival counter start at zero
-    (void)cudaGetLastError();
+    // launch errors are read with cudaPeekAtLastError, which leaves an error
+    // the caller had pending in place (it is reported, not consumed)
     noalloc_prep_kernel<<<(N + 127) / 128, 128, 0, s>>>(H);
-    CSWGS_CUDA_TRY(cudaGetLastError());
+    CSWGS_CUDA_TRY(cudaPeekAtLastError());
     const size_t smem = tile_smem_bytes(kNoAllocThreads, N, true);
     // the schedule of cswgs_solve: the last two iterations over all pixels, then the final pass
     const int n_full = iterations < 2 ? iterations : 2;
@@ -182,9 +238,9 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
         sl.count = sl.pass == kPassSubset ? Mp : M;
         sl.tiles = sl.pass == kPassSubset ? sub_tiles : full_tiles;
         sl.tile_begin = 0;
-        const int grid = sl.tiles < d.grid ? sl.tiles : d.grid;
+        const int grid = sl.tiles < dgrid ? sl.tiles : dgrid;
         noalloc_iter_kernel<<<grid, kNoAllocThreads, smem, s>>>(H, sl, N, queue);
-        CSWGS_CUDA_TRY(cudaGetLastError());
+        CSWGS_CUDA_TRY(cudaPeekAtLastError());
     }
     if (eu_out)
         CSWGS_CUDA_TRY(cudaMemcpyAsync(eu_out, H.metrics, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s));

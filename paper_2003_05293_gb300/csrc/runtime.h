@@ -174,6 +174,15 @@ struct cswgs_batch_s {
     int count = 0;
     float last_ms = 0.f;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
+    // host-buffer batches (cswgs_batch_create_host): a stream of their own, the
+    // caller's host phase maps of the next run, e and u landing in pinned memory
+    bool host = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr;          // the last run has read the staged inputs
+    double *eu_host = nullptr;            // pinned, 2 per hologram
+    std::vector<float *> host_out;        // per hologram: host phase map of the next run, or NULL
+    cswgs::DevBuf jobs;                   // map copies of the last run
+    ~cswgs_batch_s();
 };
 
 namespace cswgs {

@@ -2,10 +2,13 @@
 // iterations: threads per block and pixels per thread; full passes: threads
 // per block).  Key: (largest P rounded up to 128, work-weighted spot
 // count rounded up to a power of two, batch size rounded up to a power of
-// two).  Each candidate runs a synthetic batch of that key's size (one
-// compressed iteration, one full iteration, the final pass); the fastest
-// compressed-iteration shape and the fastest full-pass shape win.  Results live in the plan and,
-// when the plan names a cache file, in a small JSON file.
+// two, subset fraction c as the nearest power of two: a compressed launch on
+// the CUDA cores costs c times a full one, on the tensor cores about as much
+// as a full one, so the winner changes with c).  Each candidate runs a
+// synthetic batch of that key's size (one compressed iteration, one full
+// iteration, the final pass); the fastest compressed-iteration shape and the
+// fastest full-pass shape win.  Results live in the plan and, when the plan
+// names a cache file, in a small JSON file.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -29,7 +32,23 @@ static int pow2_ceil(int x)
 
 struct TuneKey {
     int P, N, B;
+    int cexp;   // c = 2^-cexp (0 .. 16)
 };
+
+// The subset fraction of a batch, weighted by each hologram's compressed
+// work (pixels x spots x compressed iterations); 1 when none has any.
+static double batch_c(const std::vector<HoloSpec> &specs)
+{
+    double wsum = 0.0, cw = 0.0;
+    for (auto &s : specs) {
+        const int F = std::min(s.n_full, s.iterations);
+        const double M = (double)s.P * s.P, D = s.D > 0 ? (double)s.D : M;
+        const double w = M * s.N * (double)(s.iterations - F), c = (double)s.Mp / D;
+        wsum += w;
+        cw += w * c;
+    }
+    return wsum > 0.0 ? cw / wsum : 1.0;
+}
 
 static TuneKey key_of(const std::vector<HoloSpec> &specs)
 {
@@ -46,6 +65,8 @@ static TuneKey key_of(const std::vector<HoloSpec> &specs)
     k.P = ((P + 127) / 128) * 128;
     k.N = std::max(16, pow2_ceil(N));
     k.B = pow2_ceil((int)specs.size());
+    const double c = batch_c(specs);
+    k.cexp = std::min(16, std::max(0, (int)std::lround(-std::log2(std::max(c, 1e-9)))));
     return k;
 }
 
@@ -53,7 +74,7 @@ std::string tune_key(const std::vector<HoloSpec> &specs, bool fp16)
 {
     TuneKey k = key_of(specs);
     char buf[64];
-    snprintf(buf, sizeof buf, "P%d_N%d_B%d%s", k.P, k.N, k.B, fp16 ? "_H" : "");
+    snprintf(buf, sizeof buf, "P%d_N%d_B%d_c%d%s", k.P, k.N, k.B, k.cexp, fp16 ? "_H" : "");
     return buf;
 }
 
@@ -153,13 +174,13 @@ TileShape tuned_shape(cswgs_plan_s *p, const std::vector<HoloSpec> &specs)
     auto it = p->tune.find(key);
     if (it != p->tune.end()) return it->second;
     // tune now, with the schedule's own mix of compressed and full iterations
-    double wsub = 0.0, wfull = 0.0, c = 0.125;
+    double wsub = 0.0, wfull = 0.0;
     for (auto &s : specs) {
         int F = std::min(s.n_full, s.iterations);
         wsub += s.iterations - F;
         wfull += F;
-        c = (double)s.Mp / ((double)s.P * s.P);
     }
+    const double c = std::ldexp(1.0, -key_of(specs).cexp);   // the key's c: one tuning per bucket
     if (!specs.empty()) {
         wsub /= specs.size();
         wfull /= specs.size();
@@ -198,7 +219,7 @@ void tune_load(cswgs_plan_s *p)
     std::stringstream ss;
     ss << f.rdbuf();
     std::string s = ss.str();
-    // entries look like "P1152_N128_B64": [256, 4, 128]
+    // entries look like "P1152_N128_B64_c3": [256, 4, 128]
     size_t pos = 0;
     while ((pos = s.find('"', pos)) != std::string::npos) {
         size_t end = s.find('"', pos + 1);
@@ -220,7 +241,7 @@ void tune_save(cswgs_plan_s *p)
     std::string tmp = p->tune_path + ".tmp";
     FILE *f = fopen(tmp.c_str(), "w");
     if (!f) return;
-    fprintf(f, "{\n  \"format\": \"cswgs-tune-2\",\n  \"entries\": {");
+    fprintf(f, "{\n  \"format\": \"cswgs-tune-3\",\n  \"entries\": {");
     bool first = true;
     for (auto &kv : p->tune) {
         fprintf(f, "%s\n    \"%s\": [%d, %d, %d]", first ? "" : ",", kv.first.c_str(), kv.second.threads,

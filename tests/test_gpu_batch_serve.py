@@ -149,6 +149,43 @@ def test_pinned_and_pageable_host_outputs(plan):
     assert np.all(host >= 0) and rms_wrapped(host, ph) < TOL_SAME_PHASE and abs(r["e"] - s["e"]) < TOL_SAME_EU
 
 
+def test_host_batches_alternating_equal_solve_batch(plan):
+    # two host-buffer batches, each run on its own stream, alternated over four
+    # steps with new spots and seeds each step (update, run one; collect the
+    # other): every step's host maps and e, u equal the synchronous batch
+    # solve of the same inputs
+    shape = small_mix(5, 40)
+    steps = [shape] + [[workloads.problem(ref.P, ref.N, 5.0, ref.c, ref.iterations, seed=100 * k + i)
+                        for i, ref in enumerate(shape)] for k in range(1, 4)]   # same shapes, new spots and seeds
+    outs = [[np.full(pb.M, -1.0, dtype=np.float32) for pb in st] for st in steps]
+    pinned = [torch.empty(pb.M, dtype=torch.float32, pin_memory=True).numpy() for pb in shape]
+    hb = [plan.host_batch(shape, pinned), plan.host_batch(shape, pinned)]
+    res = [None] * 4
+    for k in range(4):
+        b = hb[k % 2]
+        if k >= 2:
+            res[k - 2] = b.results()
+        b.update(steps[k], outs[k])
+        b.run()
+    res[2], res[3] = hb[0].results(), hb[1].results()
+    for b in hb:
+        b.close()
+    for k in range(4):
+        want = [np.full(pb.M, -1.0, dtype=np.float32) for pb in steps[k]]
+        ref = plan.solve_batch(steps[k], want)
+        for o, w, r, q in zip(outs[k], want, res[k], ref):
+            assert np.all(o >= 0) and np.array_equal(o, w)
+            assert r["e"] == q["e"] and r["u"] == q["u"]
+    # a host batch takes host maps only, and keeps its shape on update
+    with pytest.raises(Exception):
+        plan.host_batch(shape, [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in shape])
+    hb = plan.host_batch(shape)
+    bad = [workloads.problem(shape[0].P * 2, shape[0].N, 5.0, shape[0].c, shape[0].iterations, seed=1)] + shape[1:]
+    with pytest.raises(Exception):
+        hb.update(bad)
+    hb.close()
+
+
 def test_serving_mixed_stream_equals_solo():
     from paper_2003_05293_gb300 import Plan
     with Plan(precision="fp32", max_batch=4) as p:

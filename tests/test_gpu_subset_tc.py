@@ -5,7 +5,6 @@ mask made from the subset draw before each launch), so the sums of Eqs. 1 and
 path through their tune caches and compared with the FP64 oracle (teacher-
 forced compressed iterations, free-running solves, the round pupil with
 windows) and with the CUDA-core compressed kernel (batches, serving)."""
-import json
 import math
 
 import numpy as np
@@ -13,7 +12,7 @@ import pytest
 
 import oracle
 import workloads
-from gpu_helpers import TOL_EU, TOL_PHASE_RMS, oracle_states, rms_wrapped
+from gpu_helpers import TOL_EU, TOL_PHASE_RMS, oracle_states, rms_wrapped, write_pinned_tune_cache
 
 pytestmark = pytest.mark.gpu
 
@@ -25,10 +24,7 @@ FULL_WS = 2            # the warp-specialised full-pass kernel
 
 def _plan(path, sub, full, **kw):
     from paper_2003_05293_gb300 import Plan
-    entries = {"P%d_N%d_B%d" % (128 * p, 2 ** n, 2 ** b): [sub[0], sub[1], full]
-               for p in range(1, 11) for n in range(4, 11) for b in range(0, 7)}
-    path.write_text(json.dumps({"format": "cswgs-tune-2", "entries": entries}))
-    return Plan(precision="fp32", tune_cache=str(path), **kw)
+    return Plan(precision="fp32", tune_cache=write_pinned_tune_cache(path, sub[0], sub[1], full), **kw)
 
 
 @pytest.fixture(scope="module")
@@ -221,10 +217,8 @@ def test_serving(plans):
 def half_plan(tmp_path_factory):
     from paper_2003_05293_gb300 import Plan
     path = tmp_path_factory.mktemp("half") / "h.json"
-    entries = {"P%d_N%d_B%d_H" % (128 * p, 2 ** n, 2 ** b): [SUBSET_TC, 1, FULL_WS]
-               for p in range(1, 11) for n in range(4, 11) for b in range(0, 7)}
-    path.write_text(json.dumps({"format": "cswgs-tune-2", "entries": entries}))
-    plan = Plan(precision="fp32_fp16sincos", tune_cache=str(path))
+    plan = Plan(precision="fp32_fp16sincos",
+                tune_cache=write_pinned_tune_cache(path, SUBSET_TC, 1, FULL_WS, half=True))
     yield plan
     plan.close()
 

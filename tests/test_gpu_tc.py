@@ -7,7 +7,6 @@ kernel is compared with the FP64 oracle (teacher-forced full iterations, the
 final pass, free-running solves) and with the CUDA-core kernel, over
 grid sides that do and do not divide into the 128 x 64 tiles, spot counts
 below and above the 128 of one spot block, the round pupil, and SLM frames."""
-import json
 import math
 
 import numpy as np
@@ -15,7 +14,7 @@ import pytest
 
 import oracle
 import workloads
-from gpu_helpers import TOL_EU, TOL_PHASE_RMS, oracle_states, rms_wrapped
+from gpu_helpers import TOL_EU, TOL_PHASE_RMS, oracle_states, rms_wrapped, write_pinned_tune_cache
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +29,7 @@ def _plan(tmp_path, full):
     # one full-pass kernel: P rounded up to 128, N and the batch size to powers of two
     from paper_2003_05293_gb300 import Plan
     path = tmp_path / ("tune_%d.json" % full)
-    entries = {"P%d_N%d_B%d" % (128 * p, 2 ** n, 2 ** b): [256, 4, full]
-               for p in range(1, 11) for n in range(4, 11) for b in range(0, 5)}
-    path.write_text(json.dumps({"format": "cswgs-tune-2", "entries": entries}))
-    return Plan(precision="fp32", tune_cache=str(path))
+    return Plan(precision="fp32", tune_cache=write_pinned_tune_cache(path, 256, 4, full, batch_pow2=range(0, 5)))
 
 
 @pytest.fixture(scope="module")
