@@ -82,6 +82,8 @@ struct LaunchSlot {
     int tile_begin;   // first work item of this slot in the launch
     int tiles;        // work items of this slot
     int count;        // pixels of the pass (Mp or M)
+    int strip;        // tensor-core kernel: tiles of one row block per work item (1 elsewhere)
+    int pad;
 };
 
 // Tile shapes of the two FP32 iteration kernels.
@@ -90,6 +92,7 @@ struct TileShape {
     int ppt;            // compressed iterations: pixels per thread
     int full_threads;   // full iterations and final pass: threads per block, or kFullTcWs
     int fp16 = 0;       // compressed iterations use the half-precision sincos
+    int strip = 0;      // tensor-core launches: tiles per work item (0: chosen per launch)
 };
 
 // full_threads value that selects the tensor-core kernel for full iterations
@@ -140,6 +143,12 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
                                 bool masks, cudaStream_t s);
 cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
                                    cudaStream_t s);
+// Work items of a tensor-core launch: chooses the strip length (tiles of one
+// row block per work item, 1 for holograms of more than one GEMM 2 spot
+// block; `forced` > 0 takes that length) and rewrites each slot's strip, tiles
+// and tile_begin; P[i], N[i] are slot i's hologram sizes.  Returns the
+// launch's work items.
+int full_tc_assign_strips(LaunchSlot *slots, int nslots, const int *P, const int *N, int grid, int forced);
 
 // Either full-pass kernel, by tile shape (runtime.cu).
 bool shape_supported(TileShape shape);

@@ -29,15 +29,15 @@
 // The operands are factor tables in global memory, laid out block by block
 // exactly as the MMAs read them from shared memory (no-swizzle K-major core
 // matrices, 8 rows x 16 bytes): C (per 64 columns and 16 spots) and C for
-// GEMM 2 (per 64 columns and 128 spots) depend on the spots only and are made
-// once per hologram; R' (per 128 rows and 16 spots) carries w and theta and is
-// remade before every launch.  A tile streams its blocks into shared memory
+// GEMM 2 (per 16 columns, one K-step, and 128 spots) depend on the spots only
+// and are made once per hologram; R' (per 128 rows and 16 spots) carries w and
+// theta and is remade before every launch.  A tile streams its blocks into shared memory
 // with bulk copies (cp.async.bulk, completion counted on an mbarrier) through
 // a ring; a producer warp issues GEMM 1's copies, two issuing warps (GEMM 1,
 // GEMM 2) issue the MMAs and commit them to mbarriers, and eight epilogue
 // warps run the CUDA-core stages: four turn S into u (epilogue 1), four reduce
-// Z to the spot fields (epilogue 2) one tile behind.  Every wait is bounded
-// and a timeout is recorded in the launch's status word instead of hanging.
+// Z to the spot fields (epilogue 2) once per strip of tiles along a row block.  Every wait is bounded and a timeout is recorded in the launch's status
+// word instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -60,8 +60,10 @@ constexpr uint32_t kA1 = kRows * kChunk * 2;        // R' component [128 rows][1
 constexpr uint32_t kB1 = 3 * kCols * kChunk * 2;    // stacked C half [-C_im | C_re | C_im][16 spots]
 constexpr uint32_t kB1Win = kCols * kChunk * 2;     // byte offset of the [C_re | C_im] window
 constexpr uint32_t kStage = 4 * kA1 + 2 * kB1;      // one GEMM 1 stage: R' (4 components), C (hi, lo)
-constexpr uint32_t kU = kRows * kCols * 2;          // u component [128 rows][64 columns]
+constexpr uint32_t kUc = kRows * 16 * 2;            // u component of one GEMM 2 K-step [128 rows][16 columns]
+constexpr uint32_t kUSlot = 4 * kUc;                // u of one K-step (4 components)
 constexpr uint32_t kCs = kSpotBlock * kCols * 2;    // C component [128 spots][64 columns]
+constexpr uint32_t kCk = kSpotBlock * 16 * 2;       // C component of one GEMM 2 K-step [128 spots][16 columns]
 
 __host__ __device__ inline int tiles(int P) { return ((P + kRows - 1) / kRows) * ((P + kCols - 1) / kCols); }
 
@@ -229,6 +231,50 @@ __device__ __forceinline__ void put8h(unsigned char *base, uint32_t stride, uint
     *reinterpret_cast<uint4 *>(base + stride + off) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
 }
 
+// Eight complex values of u, split for GEMM 2 and packed (the four BF16
+// component rows, or the two FP16 ones), to be stored once their slot is free.
+struct Packed8 {
+    uint32_t w[4][4];
+};
+
+template <bool F16>
+__device__ __forceinline__ Packed8 pack8(const float2 *v)
+{
+    Packed8 p;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 a = v[2 * q], b = v[2 * q + 1];
+        if (F16) {
+            p.w[0][q] = h2_bits(__floats2half2_rn(a.x, b.x));
+            p.w[1][q] = h2_bits(__floats2half2_rn(a.y, b.y));
+            p.w[2][q] = p.w[3][q] = 0u;
+        } else {
+            const __nv_bfloat162 rh = __floats2bfloat162_rn(a.x, b.x), ih = __floats2bfloat162_rn(a.y, b.y);
+            const float2 rf = __bfloat1622float2(rh), jf = __bfloat1622float2(ih);
+            p.w[0][q] = bf16x2_bits(rh);
+            p.w[1][q] = bf16x2_bits(__floats2bfloat162_rn(a.x - rf.x, b.x - rf.y));
+            p.w[2][q] = bf16x2_bits(ih);
+            p.w[3][q] = bf16x2_bits(__floats2bfloat162_rn(a.y - jf.x, b.y - jf.y));
+        }
+    }
+    return p;
+}
+
+// The rows of a Packed8 at byte offset `off` of the component tiles `stride`
+// bytes apart: split BF16 re hi, re lo, im hi, im lo; FP16 re, im.
+template <bool F16>
+__device__ __forceinline__ void store8(unsigned char *base, uint32_t stride, uint32_t off, const Packed8 &p)
+{
+    if (F16) {
+        *reinterpret_cast<uint4 *>(base + off) = make_uint4(p.w[0][0], p.w[0][1], p.w[0][2], p.w[0][3]);
+        *reinterpret_cast<uint4 *>(base + stride + off) = make_uint4(p.w[1][0], p.w[1][1], p.w[1][2], p.w[1][3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(base + c * stride + off) = make_uint4(p.w[c][0], p.w[c][1], p.w[c][2], p.w[c][3]);
+    }
+}
+
 
 // ------------------------------------------------------------- factor tables --
 // Items of eight phasors; consecutive threads take consecutive rows of one
@@ -266,7 +312,8 @@ __device__ __forceinline__ void put8_stacked(unsigned char *base, uint32_t re_of
 
 // C (GEMM 1's B: per block of 64 columns and 16 spots, each half a 192-row
 // tile [-C_im | C_re | C_im] with row = column within each third) and C for
-// GEMM 2 (128 spots x 64 columns per block; split BF16, and for the
+// GEMM 2 (128 spots x 64 columns per block, stored K-step by K-step: 4 x [the
+// components of 128 spots x 16 columns]; split BF16, and for the
 // half-precision option also FP16 re and im) of hologram blockIdx.y, from its
 // spot coefficients.
 __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__restrict__ holos, int count)
@@ -308,8 +355,12 @@ __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__rest
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v[e] = make_float2(0.f, 0.f);
             }
-            put8(H.cstab + (size_t)blk * (4 * kCs), kCs, core_off(nl, 8 * g, kCols), v);
-            if (H.cstab16) put8h(H.cstab16 + (size_t)blk * (2 * kCs), kCs, core_off(nl, 8 * g, kCols), v);
+            // K-step g / 2 of the block, column group g % 2 of the K-step
+            const int ks = g >> 1;
+            put8(H.cstab + (size_t)blk * (4 * kCs) + (size_t)ks * (4 * kCk), kCk, core_off(nl, 8 * (g & 1), 16), v);
+            if (H.cstab16)
+                put8h(H.cstab16 + (size_t)blk * (2 * kCs) + (size_t)ks * (2 * kCk), kCk, core_off(nl, 8 * (g & 1), 16),
+                      v);
         }
     }
 }
@@ -385,74 +436,91 @@ __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restric
 // V warps (epilogue 2).  The producer runs ahead of the GEMM 1 warp by the
 // ring's depth: a tcgen05.mma issue waits for the tensor pipe, so copies
 // issued from the MMA warp would start one stage late.
+// A work item is a strip: LaunchSlot::strip consecutive tiles of one row block
+// of a hologram.  Since V_n = sum_y conj(R_n(y)) Z(n, y) takes the same R_n(y)
+// for every tile of a row block, GEMM 2 accumulates Z(n, y) over the strip's
+// tiles and the V warps reduce it once per strip; a hologram with more than
+// one GEMM 2 spot block (Z holds one) takes strips of one tile.
 // Tensor memory holds two S buffers (columns 256..383 and 384..511; tile k
 // uses buffer k & 1) and Z (columns 0..255).  GEMM 1 runs ahead into the next
 // tile's back-propagation while the u warps turn S into u; the GEMM 2 warp
 // streams the tile's C block in meanwhile and follows the u warps K-step by
-// K-step; the V warps reduce Z of tile k while the u warps already work on
-// tile k + 1 (the next GEMM 2 waits for both).  The per-hologram tails (Eqs.
-// 4-6, or the metrics) run in a small kernel right after the launch, so tiles
-// neither fence nor count arrivals.
+// K-step; the u warps write a K-step's columns of u as soon as GEMM 2 of the
+// previous tile has read them.  The per-hologram tails (Eqs. 4-6, or the
+// metrics) run in a small kernel right after the launch, so tiles neither
+// fence nor count arrivals.
 // Hand-overs, all mbarriers:
-//   ready[2]          producer -> GEMM 1, u and V warps: work item k in info slot k & 1
+//   ready[2]          producer -> GEMM 1, u and V warps: tile k in info slot k & 1
 //   full[r], empty[r] GEMM 1 operand ring: copies landed / MMAs done
 //   s_full[2]         GEMM 1 of the tile in that S buffer is done
 //   s_empty[2]        the u warps have read that S buffer and info slot, the V and
 //                     GEMM 1 warps that info slot
-//   g2_info           u warps -> GEMM 2 warp: the tile's C blocks (or done)
+//   g2_info           u warps -> GEMM 2 warp: the tile's C blocks and its place in
+//                     its strip (or done)
 //   u_step[4]         the u warps have written u's columns of one K-step of GEMM 2
+//   u_free[4]         GEMM 2 has read them (one phase per tile with products, so
+//                     that no wait is two phases short)
 //   cs_full           GEMM 2's C block has landed
-//   z_full            GEMM 2 of a spot block is done (C block buffer free)
+//   cs_free           the MMAs that read it are done (its buffer is free)
+//   z_full            a Z accumulation is done: a strip, or one spot block of a tile
 //   z_empty           the V warps have read Z
-//   g2_done           GEMM 2 of a tile is done: u and the operand slot are free
-//                     (one phase per tile, so that the u warps, which skip the
-//                     spot blocks, never wait two phases ahead)
 //   drain             both issuing warps' last commits, before tensor memory is freed
-// Every wait is
-// bounded; a timeout ends the loop of the side that saw it and sets the
-// status word, and the other side's waits then run out in turn.
+// Every wait is bounded; a timeout ends the loop of the side that saw it and
+// sets the status word, and the other side's waits then run out in turn.
 namespace ws {
 
-constexpr int kRing = 3;
+constexpr int kRingMax = 4;
 constexpr uint32_t kS0 = 256;       // S buffers at columns 256 and 384, Z at 0
 constexpr int kTmemColsWs = 512;
+constexpr int kKSteps = kCols / 16; // GEMM 2 K-steps per tile
 
 enum Bar {
     kReady0 = 0,
     kFull0 = 2,
-    kEmpty0 = kFull0 + kRing,
-    kSFull0 = kEmpty0 + kRing,
+    kEmpty0 = kFull0 + kRingMax,
+    kSFull0 = kEmpty0 + kRingMax,
     kSEmpty0 = kSFull0 + 2,
-    kUStep0 = kSEmpty0 + 2,   // u's columns of GEMM 2's K-step 0 .. 3 are written
-    kCsFull = kUStep0 + kCols / 16,
-    kZFull,
+    kUStep0 = kSEmpty0 + 2,       // u's columns of GEMM 2's K-step 0 .. 3 are written
+    kUFree0 = kUStep0 + kKSteps,  // ... and GEMM 2 has read them
+    kCsFull = kUFree0 + kKSteps,  // GEMM 2's C block has landed
+    kCsFree,                      // the MMAs that read it are done
+    kZFull,                       // a Z accumulation is done
     kZEmpty,
     kG2Info,    // the u warps have published the next tile's GEMM 2 operands
-    kG2Done,    // GEMM 2 of a tile (its last spot block) is done
     kDrain,     // both issuing warps' last commits (2 arrivals)
     kBarsWs
 };
 
 // The GEMM 2 warp's work item, published by the u warps when they take up a
-// tile with products (a single slot: the next one is written only after that
-// tile's GEMM 2 is done).
+// tile with products (a single slot: the next one is written only after the
+// GEMM 2 warp has issued that tile's first K-step, so it has read it).
 struct G2Info {
     const unsigned char *cstab;   // GEMM 2's C blocks in the launch's format
     int nsb, cb, done, f16;
+    int first, last;              // the tile opens / closes its strip's Z accumulation
 };
 
-// A published work item: the tile, and copies of its launch slot and its
+// A published tile: its work item (strip), its tile index in the hologram's
+// pass, its place in the strip, and copies of its launch slot and its
 // hologram's descriptor (staged by the producer warp so that the other warps
 // read them from shared memory).
 struct Info {
-    int item, empty, done, pad;
+    int item, empty, done, tile;
+    int first, last;   // the first / last tile with products of the strip
+    int zero, pad;     // zero: the strip's last tile, and the strip has no products
     LaunchSlot sl;
     HoloDev H;
 };
 
+
 // The epilogue warps: 4 u warps (epilogue 1, warps 0 .. 3) and 4 V warps
 // (epilogue 2, warps 4 .. 7), each group one warp per TMEM lane quadrant, each
 // with its own named barrier.
+// The epilogue warps: 4 u warps (epilogue 1, warps 0 .. 3) and 4 V warps
+// (epilogue 2, warps 4 .. 7), each group one warp per TMEM lane quadrant, each
+// with its own named barrier.  (Eight warps sharing both epilogues were
+// measured: 5 % slower, and 12 % at more than one GEMM 2 spot block, where
+// epilogue 2 of every tile no longer overlaps epilogue 1 of the next.)
 constexpr int kUWarps = 4, kVWarps = 4;
 constexpr int kBarU = 1, kBarV = 2;
 
@@ -463,23 +531,30 @@ struct Cfg {
     static constexpr int kThreads = kEpi + 96;        // and the producer, GEMM 1 and GEMM 2 warps
 };
 
-// Dynamic shared memory: the GEMM 1 ring, GEMM 2's C block and u (and 128
-// bytes to align the base; the no-swizzle layouts and the bulk copies need 16).
-__host__ __device__ constexpr size_t smem_bytes_ws()
-{
-    return 128 + (size_t)kRing * kStage + 4 * (size_t)kCs + 4 * (size_t)kU;
-}
+// Shared-memory layout of the kernel with US slots of u (one K-step each;
+// GEMM 2 of more than one spot block re-reads all of a tile's u, so US = 4):
+// the GEMM 1 ring, GEMM 2's C block and u (and 128 bytes to align the base;
+// the no-swizzle layouts and the bulk copies need 16).  (Two u slots and a
+// fourth ring stage were measured: the epilogue then waits for GEMM 2 to free
+// a slot, 7 % slower at N = 100.)
+template <int US>
+struct Lay {
+    static_assert(US == kKSteps, "u slots");
+    static constexpr int kRing = 3;
+    static constexpr size_t kSmem = 128 + (size_t)kRing * kStage + 4 * (size_t)kCs + (size_t)US * kUSlot;
+};
 
 struct SmemWs {
     unsigned char *ring, *cs, *u;
 };
 
+template <int US>
 __device__ __forceinline__ SmemWs carve_ws(unsigned char *raw)
 {
     unsigned char *b = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~(uintptr_t)127);
     SmemWs m;
     m.ring = b;
-    m.cs = m.ring + kRing * kStage;
+    m.cs = m.ring + Lay<US>::kRing * kStage;
     m.u = m.cs + 4 * kCs;
     return m;
 }
@@ -534,7 +609,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity)
 
 // An issuing warp's pipeline state, the same in every lane and all scalars.
 // GEMM 1 chunks go round the ring in order, so chunk q (counted over the
-// block's tiles) is stage q % kRing's (q / kRing)-th use and both ring waits
+// block's tiles) is stage q % R's (q / R)-th use (R the ring's depth) and both ring waits
 // take their parity from q; the other barriers count their phases.  The whole
 // warp runs the loop and waits; one elected lane issues the copies, MMAs,
 // commits and arrivals.
@@ -544,7 +619,7 @@ struct Ctl {
     uint32_t ring, cs, u;   // shared addresses of the ring, GEMM 2's C block and u
     uint32_t ql;      // GEMM 1 chunks loaded
     uint32_t qm;      // GEMM 1 chunks multiplied
-    uint32_t nz;      // GEMM 2 spot blocks issued
+    uint32_t nz;      // Z accumulations closed
     uint32_t ncs;     // GEMM 2 C blocks loaded
     uint32_t nu;      // u hand-overs taken
 };
@@ -552,12 +627,13 @@ struct Ctl {
 // GEMM 1's operands of one tile, issued by the producer warp: for each chunk of
 // 16 spots, R' of row block rb and the stacked C of column block cb into the
 // next ring stage once the GEMM 1 warp's products have released it.
+template <int R>
 __device__ __forceinline__ bool load_gemm1(Ctl &C, const HoloDev &H, int rb, int cb)
 {
     const int nc = nchunks(H.N);
     for (int c = 0; c < nc; ++c) {
-        const uint32_t s = C.ql % kRing;
-        if (C.ql >= (uint32_t)kRing && !warp_wait(mbar_at(C.mb, kEmpty0 + s), C.ql / kRing - 1u)) return false;
+        const uint32_t s = C.ql % R;
+        if (C.ql >= (uint32_t)R && !warp_wait(mbar_at(C.mb, kEmpty0 + s), C.ql / R - 1u)) return false;
         if (elect_one()) {
             const uint32_t stg = C.ring + s * kStage, full = mbar_at(C.mb, kFull0 + s);
             expect_tx(full, kStage);
@@ -575,14 +651,15 @@ __device__ __forceinline__ bool load_gemm1(Ctl &C, const HoloDev &H, int rb, int
 // split operands' hi hi, hi lo and lo hi terms of R'_re [C_re | C_im] and
 // R'_im [-C_im | C_re]), issued as each ring stage lands.  The stage goes back
 // to the producer when its MMAs complete.
+template <int R>
 __device__ __forceinline__ bool gemm1(Ctl &C, int nc, int j)
 {
     const uint32_t id = idesc(kRows, 2 * kCols, 0);
     const uint32_t s_acc = C.tmem + kS0 + 2 * kCols * j;   // [S_re | S_im]
     const uint64_t ring0 = desc(C.ring, 128, 256);
     for (int c = 0; c < nc; ++c) {
-        const uint32_t s = C.qm % kRing;
-        if (!warp_wait(mbar_at(C.mb, kFull0 + s), C.qm / kRing)) return false;
+        const uint32_t s = C.qm % R;
+        if (!warp_wait(mbar_at(C.mb, kFull0 + s), C.qm / R)) return false;
         // A: R' re hi, re lo, im hi, im lo; B: [C_re | C_im] and [-C_im | C_re] windows, hi and lo
         const uint64_t st = ring0 + ((uint64_t)(s * kStage) >> 4);
         const uint64_t arh = st, arl = st + (kA1 >> 4), aih = st + (2 * kA1 >> 4), ail = st + (3 * kA1 >> 4);
@@ -606,71 +683,84 @@ __device__ __forceinline__ bool gemm1(Ctl &C, int nc, int j)
 }
 
 // GEMM 2 of one tile: Z = conj(C)^T u, one block of 128 spots at a time, into
-// columns 0..255; each block's C streams in once the previous GEMM 2 is done
-// with the buffer (block 0 while u is still being written).  Split BF16
-// operands (4 components each), or FP16 re and im for the half-precision
-// option.
+// columns 0..255; each block's C (its four K-steps one after the other)
+// streams in once the MMAs that read the previous one are done (block 0 while
+// u is still being written).  Split BF16 operands (4 components each), or FP16
+// re and im for the half-precision option.  The first tile of a strip (and
+// each spot block past the first) opens a Z accumulation, once the epilogue
+// has read the last one; the last tile of a strip (and each spot block but the
+// last) closes it.  After each K-step of the last spot block, u's columns of
+// that K-step go back to the epilogue warps.
+template <int US>
 __device__ __forceinline__ bool gemm2(Ctl &C, const G2Info &g)
 {
     const int f16 = g.f16;
-    const uint32_t comps = f16 ? 2u : 4u;
+    const uint32_t comps = f16 ? 2u : 4u, kbytes = comps * kCk;
     const uint32_t id = idesc(kSpotBlock, kRows, 0, f16 ? 0 : 1), idn = idesc(kSpotBlock, kRows, 1, f16 ? 0 : 1);
     const uint32_t z_re = C.tmem, z_im = C.tmem + kRows;
-    const uint64_t cs0 = desc(C.cs, 128, (kCols / 8) * 128);
-    const uint64_t u0 = desc(C.u, 128, (kCols / 8) * 128);
+    const uint64_t cs0 = desc(C.cs, 128, 256);                       // [128 spots][16 columns] per component
+    const uint64_t u0 = desc(C.u, 128, 256);                         // [128 rows][16 columns] per component
     for (int sb = 0; sb < g.nsb; ++sb) {
-        if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZFull), C.nz - 1u)) return false;
+        if (C.ncs > 0 && !warp_wait(mbar_at(C.mb, kCsFree), C.ncs - 1u)) return false;
         if (elect_one()) {
             const uint32_t full = mbar_at(C.mb, kCsFull);
-            expect_tx(full, comps * kCs);
-            const unsigned char *src = g.cstab + ((size_t)g.cb * g.nsb + sb) * (comps * kCs);
-            for (uint32_t q = 0; q < comps; ++q) bulk_load(C.cs + q * kCs, src + q * kCs, kCs, full);
+            expect_tx(full, kKSteps * kbytes);
+            bulk_load(C.cs, g.cstab + ((size_t)g.cb * g.nsb + sb) * (kKSteps * kbytes), kKSteps * kbytes, full);
         }
         __syncwarp();
         C.ncs++;
-        // the epilogue has read the previous Z
-        if (C.nz > 0 && !warp_wait(mbar_at(C.mb, kZEmpty), C.nz - 1u)) return false;
+        const bool opens = sb > 0 || g.first, closes = sb < g.nsb - 1 || g.last;
+        // a new accumulation overwrites Z: the epilogue has read the last one
+        if (opens && C.nz > 0 && !warp_wait(mbar_at(C.mb, kZEmpty), C.nz - 1u)) return false;
         if (!warp_wait(mbar_at(C.mb, kCsFull), C.ncs - 1u)) return false;
         fence_after();
-        // on a tile's first spot block, each K-step waits for its columns of u
-        for (int ks = 0; ks < kCols / 16; ++ks) {
+        for (int ks = 0; ks < kKSteps; ++ks) {
+            // on a tile's first spot block, each K-step waits for its columns of u
             if (sb == 0) {
                 if (!warp_wait(mbar_at(C.mb, kUStep0 + ks), C.nu)) return false;
                 fence_after();
             }
+            const uint32_t acc = (opens && ks == 0) ? 0u : 1u;
+            const uint64_t cs = cs0 + ((uint64_t)(ks * kbytes) >> 4);
+            const uint64_t us = u0 + ((uint64_t)((ks % US) * kUSlot) >> 4);   // u's slot of this K-step
             if (f16) {
                 // conj(C) u: Z_re = C_re u_re + C_im u_im, Z_im = C_re u_im - C_im u_re
-                const uint64_t cr = cs0 + ((uint64_t)(ks * 256) >> 4), ci = cs0 + ((uint64_t)(kCs + ks * 256) >> 4);
-                const uint64_t ur = u0 + ((uint64_t)(ks * 256) >> 4), ui = u0 + ((uint64_t)(kU + ks * 256) >> 4);
+                const uint64_t cr = cs, ci = cs + ((uint64_t)kCk >> 4);
+                const uint64_t ur = us, ui = us + ((uint64_t)kUc >> 4);
                 if (elect_one()) {
-                    const uint32_t acc = ks > 0 ? 1u : 0u;
                     mma(z_re, cr, ur, id, acc);
                     mma(z_re, ci, ui, id, 1u);
                     mma(z_im, cr, ui, id, acc);
                     mma(z_im, ci, ur, idn, 1u);
+                    if (sb == g.nsb - 1) commit(mbar_at(C.mb, kUFree0 + ks));
                 }
             } else {
                 uint64_t a[4], b[4];
                 for (int q = 0; q < 4; ++q) {
-                    a[q] = cs0 + ((uint64_t)(q * kCs + ks * 256) >> 4);
-                    b[q] = u0 + ((uint64_t)(q * kU + ks * 256) >> 4);
+                    a[q] = cs + ((uint64_t)(q * kCk) >> 4);
+                    b[q] = us + ((uint64_t)(q * kUc) >> 4);
                 }
-                if (elect_one()) complex_mma(z_re, z_im, a, b, id, idn, ks > 0 ? 1u : 0u, 1);
+                if (elect_one()) {
+                    complex_mma(z_re, z_im, a, b, id, idn, acc, 1);
+                    if (sb == g.nsb - 1) commit(mbar_at(C.mb, kUFree0 + ks));
+                }
             }
+            __syncwarp();
         }
         if (sb == 0) C.nu++;
         if (elect_one()) {
-            commit(mbar_at(C.mb, kZFull));
-            if (sb == g.nsb - 1) commit(mbar_at(C.mb, kG2Done));
+            commit(mbar_at(C.mb, kCsFree));
+            if (closes) commit(mbar_at(C.mb, kZFull));
         }
         __syncwarp();
-        C.nz++;
+        if (closes) C.nz++;
     }
     return true;
 }
 
 // Every MMA of an issuing warp done before tensor memory is freed, and every
 // copy of a warp landed before shared memory is; true when all ended in time.
+template <int R>
 __device__ __forceinline__ bool drain(const Ctl &C, bool mmas)
 {
     bool drained = true;
@@ -679,8 +769,8 @@ __device__ __forceinline__ bool drain(const Ctl &C, bool mmas)
         __syncwarp();
         drained = warp_wait(mbar_at(C.mb, kDrain), 0u);
     }
-    for (uint32_t s = 0; s < (uint32_t)kRing; ++s) {
-        const uint32_t loads = (C.ql + kRing - 1u - s) / kRing;   // chunks q < ql with q % kRing == s
+    for (uint32_t s = 0; s < (uint32_t)R; ++s) {
+        const uint32_t loads = (C.ql + R - 1u - s) / R;   // chunks q < ql with q % R == s
         if (loads) drained &= warp_wait(mbar_at(C.mb, kFull0 + s), loads - 1u);
     }
     if (C.ncs) drained &= warp_wait(mbar_at(C.mb, kCsFull), C.ncs - 1u);
@@ -701,6 +791,7 @@ __device__ __forceinline__ Ctl ctl_init(const SmemWs &m, uint32_t mb, uint32_t t
 
 // The GEMM 2 warp: per tile with products, its operands as the epilogue
 // publishes them, then GEMM 2 once u is ready.
+template <int US>
 __device__ __noinline__ void control_gemm2(const SmemWs &m, const G2Info *g2, uint32_t mb, uint32_t tmem,
                                            unsigned *status)
 {
@@ -711,15 +802,16 @@ __device__ __noinline__ void control_gemm2(const SmemWs &m, const G2Info *g2, ui
         if (!ok) break;
         const G2Info g = *g2;
         if (g.done) break;
-        ok = gemm2(C, g);
+        ok = gemm2<US>(C, g);
         if (!ok) break;
     }
-    const bool drained = drain(C, true);
+    const bool drained = drain<Lay<US>::kRing>(C, true);
     if ((!ok || !drained) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
 
 // The GEMM 1 warp: per published tile with products, GEMM 1 into S buffer j
 // as the producer's stages land; then it gives info slot j back.
+template <int R>
 __device__ __noinline__ void control_gemm1(const SmemWs &m, const Info *info, uint32_t mb, uint32_t tmem,
                                            unsigned *status)
 {
@@ -733,20 +825,22 @@ __device__ __noinline__ void control_gemm1(const SmemWs &m, const Info *info, ui
         if (done) break;
         if (!empty) {
             fence_after();
-            ok = gemm1(C, nchunks(N), j);
+            ok = gemm1<R>(C, nchunks(N), j);
         }
         __syncwarp();
         if ((threadIdx.x & 31) == 0) arrive(mbar_at(mb, kSEmpty0 + j));
         if (!ok) break;
     }
-    const bool drained = drain(C, true);
+    const bool drained = drain<R>(C, true);
     if ((!ok || !drained) && (threadIdx.x & 31) == 0) atomicOr(status, 1u);
 }
 
-// The producer warp: takes work items, publishes them, and loads GEMM 1's
-// operand stages of each (running up to the ring's depth ahead of the MMAs).
-// The pop of the next item and the global loads of the item's slot and
-// descriptor are issued ahead of the waits they would otherwise follow.
+// The producer warp: takes work items (strips), publishes their tiles one by
+// one, and loads GEMM 1's operand stages of each (running up to the ring's
+// depth ahead of the MMAs).  The pop of the next item and the global loads of
+// the item's slot and descriptor are issued ahead of the waits they would
+// otherwise follow.
+template <int R>
 __device__ __noinline__ void control_load(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots,
                                            int nslots, int total_tiles, unsigned *queue, const SmemWs &m,
                                            Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
@@ -761,15 +855,18 @@ __device__ __noinline__ void control_load(const HoloDev *__restrict__ holos, con
     int item = total_tiles;
     if (lane0) item = (int)atomicAdd(queue, 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
-    for (uint32_t k = 0;; ++k) {
-        const int j = k & 1;
-        bool fin = item >= total_tiles;
+    uint32_t k = 0;   // tiles published
+    for (bool stop = false; !stop;) {
+        const bool fin = item >= total_tiles || !ok;
         // the next item's pop is in flight while this one is published and multiplied
         int next = total_tiles;
         if (lane0 && !fin) next = (int)atomicAdd(queue, 1u);
         const HoloDev *Hp = nullptr;
         LaunchSlot sl{};
         uint32_t hw[kHPer];
+        // the strip: row block rb, column tiles c0 .. c1 - 1, the ones with
+        // products cf .. cl (a round pupil is convex: they are contiguous)
+        int rb = 0, c0 = 0, c1 = 1, col_tiles = 1, cf = -1, cl = -1;
         if (!fin) {
             while (slot + 1 < nslots && slots[slot + 1].tile_begin <= item) ++slot;
             sl = slots[slot];
@@ -780,50 +877,116 @@ __device__ __noinline__ void control_load(const HoloDev *__restrict__ holos, con
                 const int w = lane + 32 * i;
                 hw[i] = w < kHWords ? __ldg(src + w) : 0u;
             }
+            col_tiles = (Hp->P + kCols - 1) / kCols;
+            const int S = max(1, sl.strip), per_row = (col_tiles + S - 1) / S;
+            const int s_loc = item - sl.tile_begin;
+            rb = s_loc / per_row;
+            c0 = (s_loc % per_row) * S;
+            c1 = min(c0 + S, col_tiles);
+            for (int c = c0; c < c1; ++c)
+                if (!tile_outside(*Hp, rb * col_tiles + c)) {
+                    if (cf < 0) cf = c;
+                    cl = c;
+                }
         }
-        // S buffer j and info slot j are free once the epilogue and the GEMM 1
-        // warp are done with tile k - 2
-        if (k >= 2 && ok) ok = warp_wait(mbar_at(mb, kSEmpty0 + j), (k >> 1) - 1u);
-        fin = fin || !ok;
-        bool empty = true;
-        int rb = 0, cb = 0;
-        if (fin) {
-            if (lane0) info[j].done = 1;
-        } else {
-            const int t = item - sl.tile_begin;
-            const int col_tiles = (Hp->P + kCols - 1) / kCols;
-            rb = t / col_tiles;
-            cb = t % col_tiles;
-            empty = tile_outside(*Hp, t);
-            if (lane0) {
-                info[j].item = item;
-                info[j].empty = empty ? 1 : 0;
-                info[j].done = 0;
-                info[j].sl = sl;
-            }
-            uint32_t *dst = reinterpret_cast<uint32_t *>(&info[j].H);
+        for (int c = c0; c < c1; ++c) {
+            const int j = k & 1;
+            // S buffer j and info slot j are free once the epilogue and the GEMM 1
+            // warp are done with tile k - 2
+            if (k >= 2 && ok) ok = warp_wait(mbar_at(mb, kSEmpty0 + j), (k >> 1) - 1u);
+            stop = fin || !ok;
+            const bool empty = stop || cf < 0 || c < cf || c > cl;
+            if (stop) {
+                if (lane0) info[j].done = 1;
+            } else {
+                if (lane0) {
+                    info[j].item = item;
+                    info[j].tile = rb * col_tiles + c;
+                    info[j].empty = empty ? 1 : 0;
+                    info[j].done = 0;
+                    info[j].first = c == cf ? 1 : 0;
+                    info[j].last = c == cl ? 1 : 0;
+                    info[j].zero = (cf < 0 && c == c1 - 1) ? 1 : 0;
+                    info[j].sl = sl;
+                }
+                uint32_t *dst = reinterpret_cast<uint32_t *>(&info[j].H);
 #pragma unroll
-            for (int i = 0; i < kHPer; ++i) {
-                const int w = lane + 32 * i;
-                if (w < kHWords) dst[w] = hw[i];
+                for (int i = 0; i < kHPer; ++i) {
+                    const int w = lane + 32 * i;
+                    if (w < kHWords) dst[w] = hw[i];
+                }
             }
+            __syncwarp();
+            if (lane0) arrive(mbar_at(mb, kReady0 + j));
+            ++k;
+            if (stop) break;
+            if (!empty) ok = load_gemm1<R>(C, *Hp, rb, c);
         }
-        __syncwarp();
-        if (lane0) arrive(mbar_at(mb, kReady0 + j));
-        if (!empty && ok) ok = load_gemm1(C, *Hp, rb, cb);
-        if (fin || !ok) break;
         item = __shfl_sync(0xffffffffu, next, 0);
     }
-    const bool drained = drain(C, false);
+    const bool drained = drain<R>(C, false);
     if ((!ok || !drained) && lane0) atomicOr(status, 1u);
 }
 
+// The partial V_n = sum_y conj(R_n(y)) Z(n, y) of spot n of a closed Z
+// accumulation (a strip at row block y0) over the tile's 128 rows.  R_n(y)
+// along the rows by recurrence: its phase is quadratic in y, so R(y + 1) =
+// R(y) D(y) and D(y + 1) = D(y) E with the constant E = e^{i (2 pi 2 Gh / 2^32
+// + 2 gl)}; R and D are evaluated directly every 8 rows (the product's
+// rounding grows with the run length).  Every lane computes (a lane past N
+// uses spot N - 1's factors and stores nothing): no divergent branch in the
+// row loop.
+__device__ __forceinline__ float2 strip_dot(uint32_t z_re, uint32_t z_im, const int4 *coef, int n, int N, int y0,
+                                            int half)
+{
+    const int4 cf = coef[min(n, N - 1)];
+    const int32_t tilt = cf.y, Gh = cf.z;
+    const float gl = __int_as_float(cf.w);
+    float es, ec;
+    sincos_fix(kFixRound + 2u * (uint32_t)Gh, fmaf(2.f, gl, -kTwoPiF), es, ec);
+    float vr0 = 0.f, vi0 = 0.f, vr1 = 0.f, vi1 = 0.f;
+#pragma unroll 1
+    for (int ys = 0; ys < kRows; ys += 16) {
+        float zr[16], zi[16];
+        ld16(z_re + ys, zr);
+        ld16(z_im + ys, zi);
+        float2 r[16];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int u0 = y0 + ys + 8 * b - half, du = 2 * u0 + 1;
+            float2 pr = spot_factor(tilt, Gh, gl, u0, kFixRound, 1.f);
+            float ds, dc;
+            sincos_fix(kFixRound + (uint32_t)tilt + (uint32_t)Gh * (uint32_t)du, fmaf(gl, (float)du, -kTwoPiF), ds,
+                       dc);
+            float2 d = make_float2(dc, ds);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                r[8 * b + e] = pr;
+                if (e < 7) {
+                    pr = make_float2(fmaf(pr.x, d.x, -pr.y * d.y), fmaf(pr.x, d.y, pr.y * d.x));
+                    d = make_float2(fmaf(d.x, ec, -d.y * es), fmaf(d.x, es, d.y * ec));
+                }
+            }
+        }
+        ld_wait();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            vr0 = fmaf(r[2 * e].x, zr[2 * e], fmaf(r[2 * e].y, zi[2 * e], vr0));
+            vi0 = fmaf(r[2 * e].x, zi[2 * e], fmaf(-r[2 * e].y, zr[2 * e], vi0));
+            vr1 = fmaf(r[2 * e + 1].x, zr[2 * e + 1], fmaf(r[2 * e + 1].y, zi[2 * e + 1], vr1));
+            vi1 = fmaf(r[2 * e + 1].x, zi[2 * e + 1], fmaf(-r[2 * e + 1].y, zr[2 * e + 1], vi1));
+        }
+    }
+    return make_float2(vr0 + vr1, vi0 + vi1);
+}
+
 // The u warps (epilogue 1): per tile, u = A S / |S| (with Phi and the gray
-// level in the final pass) into GEMM 2's B operand, K-step by K-step.  u is
-// free for the tile once GEMM 2 of the previous tile with products is done.
-// A tile outside the pupil gets its zero partials (and, in the final pass,
-// phase 0 and gray lut[0]) here.
-template <bool F16>
+// level in the final pass) into GEMM 2's B operand, K-step by K-step: K-step
+// ks goes to u's slot ks % US once GEMM 2 has read that slot's last K-step
+// (computed first, stored after the wait).  A tile outside the pupil gets, in
+// the final pass, phase 0 and gray lut[0] here, and a strip with no tile
+// inside the pupil its zero partials.
+template <bool F16, int US>
 __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2Info *g2, uint32_t mb, uint32_t tmem,
                                            unsigned *status)
 {
@@ -831,7 +994,8 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
     const int tid = threadIdx.x, lane = tid & 31, q = tid >> 5;   // warps 0 .. 3: TMEM lane quadrant q
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
     // phases seen: s_full[j] once per tile with products (low half: j = 0,
-    // high half: j = 1); g2_done once per tile with products
+    // high half: j = 1); n_p: tiles with products taken up (u_free[ks]
+    // completes once per such tile)
     uint32_t n_s = 0u, n_p = 0u;
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
@@ -839,29 +1003,34 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
         ok = group_and<kBarU, kT>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
         if (!ok) break;
         if (info[j].done) {
-            // the GEMM 2 warp is done with the operand slot once its last GEMM 2 is
-            if (n_p > 0u) ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kG2Done), n_p));
+            // the GEMM 2 warp has read the last published operands once it has
+            // issued that tile's first K-step
+            if (n_p > 0u) ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kUFree0), n_p));
             if (ok && tid == 0) {
                 g2->done = 1;
                 arrive(mbar_at(mb, kG2Info));
             }
             break;
         }
-        const int item = info[j].item, empty = info[j].empty;
+        const int item = info[j].item, empty = info[j].empty, t = info[j].tile;
+        const int first = info[j].first, last = info[j].last, zero = info[j].zero;
         const LaunchSlot sl = info[j].sl;
         const HoloDev H = info[j].H;   // by value: global stores below cannot alias it
-        const int t = item - sl.tile_begin;
         const int P = H.P, N = H.N, half = P >> 1, pass = sl.pass;
         const int col_tiles = (P + kCols - 1) / kCols;
         const int y0 = (t / col_tiles) * kRows, x0 = (t % col_tiles) * kCols;
         if (empty) {
-            // wholly outside the round pupil: zero partials; in the final pass
-            // phase 0 (gray lut[0]) over its grid pixels
+            // wholly outside the round pupil: in the final pass phase 0 (gray
+            // lut[0]) over its grid pixels; a strip without products has zero
+            // partials
             __syncwarp();
             if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
-            for (int n = tid; n < N; n += kT) {
-                if (pass == kPassFinal) H.part64[(size_t)t * N + n] = make_double2(0.0, 0.0);
-                else H.part[(size_t)t * N + n] = make_float2(0.f, 0.f);
+            if (zero) {
+                const size_t s_loc = (size_t)(item - sl.tile_begin);
+                for (int n = tid; n < N; n += kT) {
+                    if (pass == kPassFinal) H.part64[s_loc * N + n] = make_double2(0.0, 0.0);
+                    else H.part[s_loc * N + n] = make_float2(0.f, 0.f);
+                }
             }
             if (pass == kPassFinal) {
                 const int rows = min(kRows, P - y0), cols = min(kCols, P - x0);
@@ -888,10 +1057,10 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                 mword = 0ull;
             }
         }
-        // u and the single GEMM 2 operand slot are free once GEMM 2 of the
-        // previous tile with products is done
+        // the single GEMM 2 operand slot is free once GEMM 2 has issued the
+        // previous tile's first K-step
         if (n_p > 0u) {
-            ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kG2Done), n_p));
+            ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kUFree0), n_p));
             if (!ok) break;
         }
         if (tid == 0) {
@@ -900,6 +1069,8 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
             g2->cb = t % col_tiles;
             g2->done = 0;
             g2->f16 = F16 ? 1 : 0;
+            g2->first = first;
+            g2->last = last;
             arrive(mbar_at(mb, kG2Info));
         }
         n_p++;
@@ -916,14 +1087,14 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
             int xl = 0, xr = gy < P ? P - 1 : -1;
             if (H.aperture != 0) {
                 const int D = R2 - yq2;
-                int w = -1;
+                int wr = -1;
                 if (D >= 0) {
-                    w = (int)sqrtf((float)D);   // within 1 of floor(sqrt(D))
-                    if ((w + 1) * (w + 1) <= D) ++w;
-                    if (w * w > D) --w;
+                    wr = (int)sqrtf((float)D);   // within 1 of floor(sqrt(D))
+                    if ((wr + 1) * (wr + 1) <= D) ++wr;
+                    if (wr * wr > D) --wr;
                 }
-                xl = max(xl, half - w);
-                xr = min(xr, half + w);
+                xl = max(xl, half - wr);
+                xr = min(xr, half + wr);
             }
             const float kA = H.kA;
             // the row's 16 columns of each K-step, with the Gaussian beam's
@@ -931,7 +1102,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
             auto ksteps = [&](auto gauss_tag) {
                 constexpr bool kGauss = decltype(gauss_tag)::value;
 #pragma unroll 1
-                for (int ks = 0; ks < kCols / 16; ++ks) {
+                for (int ks = 0; ks < kKSteps; ++ks) {
                     const int xs = 16 * ks, gx0 = x0 + xs;
                     // the pixels that carry u: in the row's span and, in a
                     // compressed pass, in S_j (the rest add nothing to Eq. 3's sum)
@@ -943,6 +1114,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                     ld16(s_re + lanes + xs, sr);
                     ld16(s_im + lanes + xs, si);
                     ld_wait();
+                    Packed8 pk[2];
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {
                         float2 u[8];
@@ -969,8 +1141,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                             const float ur = lit ? a * rs : amp, ui = lit ? b * rs : 0.f;   // S = 0: phase 0
                             u[e] = make_float2(valid ? ur : 0.f, valid ? ui : 0.f);
                         }
-                        if (F16) put8h(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
-                        else put8(m.u, kU, core_off(row, xs + 8 * g, kCols), u);
+                        pk[g] = pack8<F16>(u);
                     }
                     if (pass == kPassFinal && gy < P) {
 #pragma unroll
@@ -990,14 +1161,28 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                             if (H.slm) write_gray4(H, gy, col, o + 4 * g);
                         }
                     }
+                    // u's slot of this K-step is free once GEMM 2 has read its last
+                    // K-step (US earlier in GEMM 2's order: of this tile, or of the
+                    // previous tile with products); K-step 0's was waited for above
+                    // (the condition is the same in every thread of the group, so
+                    // the named barrier of the vote stays matched)
+                    const int pks = (ks + kKSteps - US) % kKSteps;
+                    const uint32_t pcount = ks >= US ? n_p : n_p - 1u;
+                    if (pcount > 0u && !(ks == 0 && US == kKSteps) &&
+                        !group_and<kBarU, kT>(wait_newest(mbar_at(mb, kUFree0 + pks), pcount)))
+                        return false;
+                    unsigned char *slot = m.u + (ks % US) * kUSlot;
+                    store8<F16>(slot, kUc, core_off(row, 0, 16), pk[0]);
+                    store8<F16>(slot, kUc, core_off(row, 8, 16), pk[1]);
                     // this K-step's columns of u are in place
                     fence_async_smem();
                     __syncwarp();
                     if (lane == 0) arrive(mbar_at(mb, kUStep0 + ks));
                 }
+                return true;
             };
-            if (kA != 0.f) ksteps(std::true_type{});
-            else ksteps(std::false_type{});
+            ok = kA != 0.f ? ksteps(std::true_type{}) : ksteps(std::false_type{});
+            if (!ok) break;
         }
         fence_before();
         __syncwarp();
@@ -1006,23 +1191,23 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
     if (!ok && tid == 0) atomicOr(status, 1u);
 }
 
-// The V warps (epilogue 2): per tile with products and spot block, the tile's
-// partial V_n = sum_y conj(R_n(y)) Z(n, y), one spot per thread over all 128
-// rows, while the u warps go on with the next tile.
+// The V warps (epilogue 2): per strip (after the GEMM 2 of its last tile with
+// products) and spot block, the strip's partial V_n = sum_y conj(R_n(y))
+// Z(n, y), one spot per thread over all 128 rows, while the u warps go on with
+// the next tiles.
 __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
 {
     constexpr int kT = 32 * kVWarps;
     const int tid = threadIdx.x - 32 * kUWarps, lane = tid & 31, q = tid >> 5;   // TMEM lane quadrant q
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
-    const uint32_t z_re = tmem, z_im = tmem + kRows;
-    uint32_t n_z = 0u;   // z_full phases seen
+    uint32_t n_z = 0u;   // Z accumulations reduced
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
         ok = group_and<kBarV, kT>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
         if (!ok) break;
         if (info[j].done) break;
-        const int item = info[j].item, empty = info[j].empty;
+        const int item = info[j].item, empty = info[j].empty, t = info[j].tile, last = info[j].last;
         const int tile_begin = info[j].sl.tile_begin, pass = info[j].sl.pass;
         const int P = info[j].H.P, N = info[j].H.N;
         const int4 *coef = info[j].H.coef;
@@ -1031,67 +1216,23 @@ __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32
         // the info slot is read: it goes back with this group's arrival
         __syncwarp();
         if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
-        if (empty) continue;
-        const int t = item - tile_begin, half = P >> 1;
+        if (empty || !last) continue;
+        const int s_loc = item - tile_begin, half = P >> 1;
         const int y0 = (t / ((P + kCols - 1) / kCols)) * kRows;
         for (int sb = 0; sb * kSpotBlock < N; ++sb) {
             n_z++;
             ok = group_and<kBarV, kT>(wait_newest(mbar_at(mb, kZFull), n_z));
             if (!ok) break;
             fence_after();
-            // every lane computes (a lane past N uses spot N - 1's factors and
-            // stores nothing): no divergent branch in the row loop
             const int n = sb * kSpotBlock + 32 * q + lane;
-            const int4 cf = coef[min(n, N - 1)];
-            const int32_t tilt = cf.y, Gh = cf.z;
-            const float gl = __int_as_float(cf.w);
-            // R_n(y) along the rows by recurrence: its phase is quadratic in y,
-            // so R(y + 1) = R(y) D(y) and D(y + 1) = D(y) E with the constant
-            // E = e^{i (2 pi 2 Gh / 2^32 + 2 gl)}; R and D are evaluated directly
-            // every 8 rows (the product's rounding grows with the run length)
-            float es, ec;
-            sincos_fix(kFixRound + 2u * (uint32_t)Gh, fmaf(2.f, gl, -kTwoPiF), es, ec);
-            float vr0 = 0.f, vi0 = 0.f, vr1 = 0.f, vi1 = 0.f;
-#pragma unroll 1
-            for (int ys = 0; ys < kRows; ys += 16) {
-                float zr[16], zi[16];
-                ld16(z_re + lanes + ys, zr);
-                ld16(z_im + lanes + ys, zi);
-                float2 r[16];
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int u0 = y0 + ys + 8 * b - half, du = 2 * u0 + 1;
-                    float2 pr = spot_factor(tilt, Gh, gl, u0, kFixRound, 1.f);
-                    float ds, dc;
-                    sincos_fix(kFixRound + (uint32_t)tilt + (uint32_t)Gh * (uint32_t)du, fmaf(gl, (float)du, -kTwoPiF),
-                               ds, dc);
-                    float2 d = make_float2(dc, ds);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        r[8 * b + e] = pr;
-                        if (e < 7) {
-                            pr = make_float2(fmaf(pr.x, d.x, -pr.y * d.y), fmaf(pr.x, d.y, pr.y * d.x));
-                            d = make_float2(fmaf(d.x, ec, -d.y * es), fmaf(d.x, es, d.y * ec));
-                        }
-                    }
-                }
-                ld_wait();
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    vr0 = fmaf(r[2 * e].x, zr[2 * e], fmaf(r[2 * e].y, zi[2 * e], vr0));
-                    vi0 = fmaf(r[2 * e].x, zi[2 * e], fmaf(-r[2 * e].y, zr[2 * e], vi0));
-                    vr1 = fmaf(r[2 * e + 1].x, zr[2 * e + 1], fmaf(r[2 * e + 1].y, zi[2 * e + 1], vr1));
-                    vi1 = fmaf(r[2 * e + 1].x, zi[2 * e + 1], fmaf(-r[2 * e + 1].y, zr[2 * e + 1], vi1));
-                }
-            }
+            const float2 v = strip_dot(tmem + lanes, tmem + kRows + lanes, coef, n, N, y0, half);
             fence_before();
             __syncwarp();
             if (lane == 0) arrive(mbar_at(mb, kZEmpty));
             if (n < N) {
-                const float vr = vr0 + vr1, vi = vi0 + vi1;
-                const size_t off = (size_t)t * N + n;
-                if (pass == kPassFinal) part64[off] = make_double2((double)vr, (double)vi);
-                else part[off] = make_float2(vr, vi);
+                const size_t off = (size_t)s_loc * N + n;
+                if (pass == kPassFinal) part64[off] = make_double2((double)v.x, (double)v.y);
+                else part[off] = make_float2(v.x, v.y);
             }
         }
         if (!ok) break;
@@ -1103,7 +1244,7 @@ __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32
 
 }  // namespace tc
 
-template <int W, bool F16>
+template <int W, bool F16, int US>
 __global__ void __launch_bounds__(tc::ws::Cfg<W>::kThreads, 1)
 iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__restrict__ slots, int nslots,
                       int total_tiles, unsigned *queue)
@@ -1121,9 +1262,9 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
             // S buffers and info slots go back from the epilogue and the GEMM 1 warp
             const uint32_t cnt = (b == kSEmpty0 || b == kSEmpty0 + 1) ? W + 1
                                  : b == kZEmpty                               ? kVWarps
-                                 : (b >= kUStep0 && b < kCsFull)              ? kUWarps
-                                 : b == kDrain                                             ? 2
-                                                                                           : 1;
+                                 : (b >= kUStep0 && b < kUStep0 + kKSteps)    ? kUWarps
+                                 : b == kDrain                                ? 2
+                                                                              : 1;
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::saddr(&s_mbar[b])), "r"(cnt));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1137,16 +1278,17 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     __syncthreads();
     tc::fence_after();
     const uint32_t mb = tc::saddr(&s_mbar[0]);
-    const SmemWs m = carve_ws(smem);
+    const SmemWs m = carve_ws<US>(smem);
+    constexpr int R = Lay<US>::kRing;
     unsigned *status = queue + 2;
     if (warp == W) {
-        control_load(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
+        control_load<R>(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
     } else if (warp == W + 1) {
-        control_gemm1(m, s_info, mb, s_tmem, status);
+        control_gemm1<R>(m, s_info, mb, s_tmem, status);
     } else if (warp == W + 2) {
-        control_gemm2(m, &s_g2, mb, s_tmem, status);
+        control_gemm2<US>(m, &s_g2, mb, s_tmem, status);
     } else if (warp < kUWarps) {
-        epilogue_u<F16>(m, s_info, &s_g2, mb, s_tmem, status);
+        epilogue_u<F16, US>(m, s_info, &s_g2, mb, s_tmem, status);
     } else {
         epilogue_v(s_info, mb, s_tmem, status);
     }
@@ -1192,41 +1334,48 @@ __global__ void __launch_bounds__(kTailThreads) tcws_tails_kernel(const HoloDev 
     else tail_update<kTailThreads, true>(H, sl, s_v, s_red);
 }
 
-template <int W, bool F16>
+template <int W, bool F16, int US>
 static int tcws_max_grid_of(int maxN, int sm_count)
 {
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, iter_full_tcws_kernel<W, F16>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, iter_full_tcws_kernel<W, F16, US>) != cudaSuccess) return 0;
     const size_t limit = 227 * 1024 - fa.sharedSizeBytes;
-    const size_t smem = tc::ws::smem_bytes_ws();
+    const size_t smem = tc::ws::Lay<US>::kSmem;
     if (smem > limit || (size_t)maxN * sizeof(float2) > 48 * 1024) return 0;
-    if (cudaFuncSetAttribute(iter_full_tcws_kernel<W, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(iter_full_tcws_kernel<W, F16, US>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)limit) != cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iter_full_tcws_kernel<W, F16>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iter_full_tcws_kernel<W, F16, US>,
                                                       tc::ws::Cfg<W>::kThreads, smem) != cudaSuccess)
         return 0;
     return std::min(per_sm, 1) * sm_count;   // a block holds all 512 tensor-memory columns
 }
 
+// Resident blocks of the kernel (both precisions; sets their shared-memory limit).
 template <int W>
 static int tcws_max_grid(int maxN, int sm_count)
 {
-    return std::min(tcws_max_grid_of<W, false>(maxN, sm_count), tcws_max_grid_of<W, true>(maxN, sm_count));
+    constexpr int K4 = tc::ws::kKSteps;
+    return std::min(tcws_max_grid_of<W, false, K4>(maxN, sm_count), tcws_max_grid_of<W, true, K4>(maxN, sm_count));
+}
+
+template <int W, bool F16, int US>
+static void tcws_launch_one(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles,
+                            unsigned *queue, int grid, cudaStream_t s)
+{
+    iter_full_tcws_kernel<W, F16, US><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::Lay<US>::kSmem, s>>>(
+        holos, slots, nslots, total_tiles, queue);
 }
 
 template <int W>
 static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
                                unsigned *queue, int grid, bool subset, int f16, cudaStream_t s)
 {
+    constexpr int K4 = tc::ws::kKSteps;
     (void)cudaGetLastError();
-    if (f16)
-        iter_full_tcws_kernel<W, true><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(), s>>>(
-            holos, slots, nslots, total_tiles, queue);
-    else
-        iter_full_tcws_kernel<W, false><<<grid, tc::ws::Cfg<W>::kThreads, tc::ws::smem_bytes_ws(), s>>>(
-            holos, slots, nslots, total_tiles, queue);
+    if (f16) tcws_launch_one<W, true, K4>(holos, slots, nslots, total_tiles, queue, grid, s);
+    else tcws_launch_one<W, false, K4>(holos, slots, nslots, total_tiles, queue, grid, s);
     // one tail block per slot, plus (compressed launches) blocks that clear the masks
     const dim3 tails((unsigned)nslots, 1u + (subset ? 8u : 0u));
     tcws_tails_kernel<<<tails, kTailThreads, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
@@ -1237,6 +1386,50 @@ static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, in
 constexpr int kWsWarps = 8;
 
 int full_tc_tiles(int P) { return tc::tiles(P); }
+
+// Strip length of a launch: the one that minimises an estimate of its time in
+// tile times, (tiles + f items) / grid + S / 2: the work spread over the
+// resident blocks, a flush per work item (epilogue 2 and the hand-over of Z,
+// f = 1/2 a tile), and the tail left by the last strips (half a strip); or the
+// forced length.  A hologram with more than one spot block per GEMM 2 takes
+// strips of one tile.
+int full_tc_assign_strips(LaunchSlot *slots, int nslots, const int *P, const int *N, int grid, int forced)
+{
+    using namespace tc;
+    grid = std::max(1, grid);
+    auto cols = [&](int i) { return (P[i] + kCols - 1) / kCols; };
+    auto rows = [&](int i) { return (P[i] + kRows - 1) / kRows; };
+    auto strip_of = [&](int i, int S) { return nspotblocks(N[i]) == 1 ? std::min(S, cols(i)) : 1; };
+    double tiles = 0.0;
+    int smax = 1;
+    for (int i = 0; i < nslots; ++i) {
+        tiles += (double)rows(i) * cols(i);
+        if (nspotblocks(N[i]) == 1) smax = std::max(smax, cols(i));
+    }
+    int best = forced > 0 ? forced : 1;
+    double best_cost = 1e300;
+    for (int S = 1; S <= smax && forced <= 0; ++S) {
+        double items = 0.0;
+        for (int i = 0; i < nslots; ++i) {
+            const int st = strip_of(i, S);
+            items += (double)rows(i) * ((cols(i) + st - 1) / st);
+        }
+        const double cost = (tiles + 0.5 * items) / grid + 0.5 * S;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = S;
+        }
+    }
+    int begin = 0;
+    for (int i = 0; i < nslots; ++i) {
+        const int st = strip_of(i, best);
+        slots[i].strip = st;
+        slots[i].tiles = rows(i) * ((cols(i) + st - 1) / st);
+        slots[i].tile_begin = begin;
+        begin += slots[i].tiles;
+    }
+    return begin;
+}
 
 int full_tc_max_grid(int variant, int maxN, int sm_count)
 {

@@ -238,6 +238,8 @@ extern "C" cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const doubl
         sl.count = sl.pass == kPassSubset ? Mp : M;
         sl.tiles = sl.pass == kPassSubset ? sub_tiles : full_tiles;
         sl.tile_begin = 0;
+        sl.strip = 1;
+        sl.pad = 0;
         const int grid = sl.tiles < dgrid ? sl.tiles : dgrid;
         noalloc_iter_kernel<<<grid, kNoAllocThreads, smem, s>>>(H, sl, N, queue);
         CSWGS_CUDA_TRY(cudaPeekAtLastError());

@@ -410,6 +410,12 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         }
     }
 
+    for (int kind = 0; kind < 2; ++kind) {
+        b->grid[kind] = shape_max_grid(shape, kind, b->maxN, p->sm_count);
+        if (b->grid[kind] <= 0)
+            return set_error(CSWGS_ECUDA, "tile shape %dx%d / %d cannot be resident with N=%d", shape.threads,
+                             shape.ppt, shape.full_threads, b->maxN);
+    }
     // launch schedule: step L advances every hologram that still has work, with
     // one launch of each kernel kind that has slots in it
     int L_max = 0;
@@ -435,12 +441,24 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
                 sl.count = pass_count(s, pass);
                 sl.tiles = pass_tiles(pass, s.P, s.Mp, shape);
                 sl.tile_begin = tiles;
+                sl.strip = 1;
+                sl.pad = 0;
                 tiles += sl.tiles;
                 mN = std::max(mN, s.N);
                 slots.push_back(sl);
                 double pr = 2.0 * (double)s.N * (double)sl.count;
                 pairs_total += pr;
                 if (pass != kPassFinal) pairs_iter += pr;
+            }
+            if (tiles > 0 && launch_uses_tc(shape, kind)) {
+                // the tensor-core kernel takes strips of tiles along a row block
+                std::vector<int> sP, sN;
+                for (size_t i = first; i < slots.size(); ++i) {
+                    sP.push_back(b->specs[slots[i].holo].P);
+                    sN.push_back(b->specs[slots[i].holo].N);
+                }
+                tiles = full_tc_assign_strips(slots.data() + first, (int)slots.size() - first, sP.data(), sN.data(),
+                                              b->grid[kind], shape.strip);
             }
             b->l_slot0.push_back(first);
             b->l_nslots.push_back((int)slots.size() - first);
@@ -459,12 +477,6 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
                                   cudaMemcpyHostToDevice));
     CSWGS_CUDA_TRY(cudaMemset(b->queue_d.p, 0, 256));
     CSWGS_CUDA_TRY(cudaMemset(b->mem.p, 0, work));
-    for (int kind = 0; kind < 2; ++kind) {
-        b->grid[kind] = shape_max_grid(shape, kind, b->maxN, p->sm_count);
-        if (b->grid[kind] <= 0)
-            return set_error(CSWGS_ECUDA, "tile shape %dx%d / %d cannot be resident with N=%d", shape.threads,
-                             shape.ppt, shape.full_threads, b->maxN);
-    }
     if (timing) {
         b->events.resize(L_max + 2);   // before the preparation, before each step, after the last
         for (auto &e : b->events) CSWGS_CUDA_TRY(cudaEventCreate(&e));

@@ -416,11 +416,28 @@ void Server::loop()
                 sl.count = pass == kPassSubset ? r->spec.Mp : r->spec.D;
                 sl.tiles = pass_tiles(pass, r->spec.P, r->spec.Mp, shape_);
                 sl.tile_begin = group_tiles[kind];
+                sl.strip = 1;
+                sl.pad = 0;
                 group_tiles[kind] += sl.tiles;
                 group_slots[kind]++;
                 group_maxN[kind] = std::max(group_maxN[kind], r->spec.N);
                 if (pass == kPassFinal) finishing.push_back(r);
             }
+        }
+        // the tensor-core kernel takes strips of tiles along a row block
+        for (int kind = 0, first = 0; kind < 2; first += group_slots[kind], ++kind) {
+            if (group_tiles[kind] == 0 || !launch_uses_tc(shape_, kind)) continue;
+            auto key = std::make_pair(kind, group_maxN[kind]);
+            auto g = grid_for.find(key);
+            if (g == grid_for.end())
+                g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
+            std::vector<int> sP, sN;
+            for (int i = first; i < first + group_slots[kind]; ++i) {
+                sP.push_back(master_[sbuf[i].holo].P);
+                sN.push_back(master_[sbuf[i].holo].N);
+            }
+            group_tiles[kind] = full_tc_assign_strips(sbuf + first, group_slots[kind], sP.data(), sN.data(),
+                                                      std::max(1, g->second), shape_.strip);
         }
         const int64_t serial = serial_++;
         HoloDev *hbuf = holos_h_[serial & 1];

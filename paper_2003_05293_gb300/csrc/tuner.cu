@@ -219,7 +219,8 @@ void tune_load(cswgs_plan_s *p)
     std::stringstream ss;
     ss << f.rdbuf();
     std::string s = ss.str();
-    // entries look like "P1152_N128_B64_c3": [256, 4, 128]
+    // entries look like "P1152_N128_B64_c3": [256, 4, 128] or, with a strip
+    // length for the tensor-core launches, [1, 1, 2, 6]
     size_t pos = 0;
     while ((pos = s.find('"', pos)) != std::string::npos) {
         size_t end = s.find('"', pos + 1);
@@ -228,10 +229,11 @@ void tune_load(cswgs_plan_s *p)
         pos = end + 1;
         if (key.empty() || key[0] != 'P') continue;
         const int fp16 = key.size() > 2 && key.compare(key.size() - 2, 2, "_H") == 0 ? 1 : 0;
-        int t = 0, k = 0, f = 0;
-        if (sscanf(s.c_str() + pos, " : [ %d , %d , %d ]", &t, &k, &f) == 3 &&
-            shape_supported(TileShape{t, k, f, fp16}))
-            p->tune[key] = TileShape{t, k, f, fp16};
+        int t = 0, k = 0, f = 0, st = 0;
+        const int got = sscanf(s.c_str() + pos, " : [ %d , %d , %d , %d ]", &t, &k, &f, &st);
+        if (got < 3) continue;
+        if (got < 4 || st < 0 || st > 4096) st = 0;
+        if (shape_supported(TileShape{t, k, f, fp16, st})) p->tune[key] = TileShape{t, k, f, fp16, st};
     }
 }
 
@@ -244,8 +246,8 @@ void tune_save(cswgs_plan_s *p)
     fprintf(f, "{\n  \"format\": \"cswgs-tune-3\",\n  \"entries\": {");
     bool first = true;
     for (auto &kv : p->tune) {
-        fprintf(f, "%s\n    \"%s\": [%d, %d, %d]", first ? "" : ",", kv.first.c_str(), kv.second.threads,
-                kv.second.ppt, kv.second.full_threads);
+        fprintf(f, "%s\n    \"%s\": [%d, %d, %d, %d]", first ? "" : ",", kv.first.c_str(), kv.second.threads,
+                kv.second.ppt, kv.second.full_threads, kv.second.strip);
         first = false;
     }
     fprintf(f, "\n  }\n}\n");
