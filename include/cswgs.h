@@ -410,6 +410,22 @@ cswgs_status cswgs_solve_noalloc(const double *spots_xyz, const double *amplitud
                                  double subset_fraction, int iterations, uint64_t seed,
                                  float *phase_out, double *eu_out, void *stream);
 
+/* --------------------------------------------------- test of the waits --- */
+
+/* A test of the tensor-core kernel's bounded waits (the paper has no
+ * counterpart: it is the library's own safeguard).  Every wait of that kernel
+ * on another of its warps (an mbarrier) gives up after a bounded number of
+ * polls, records the time-out in the launch's status word and lets the
+ * kernel end, so that a stalled hand-over returns CSWGS_ETIMEOUT instead of
+ * hanging the GPU.  With withhold_first_item != 0, every later FP32 solve or
+ * batch run of this plan launches the kernel with its producer warp holding
+ * back the first work item: every other warp's first wait runs out, before
+ * any bulk copy or MMA is issued, and the solve reports CSWGS_ETIMEOUT (its
+ * outputs are undefined).  wait_polls != 0 sets the poll limit of every wait
+ * (0: the default, 2^20).  Both 0 (the default) turn the test off; the plan
+ * then solves as before.  Not for the serving loop. */
+cswgs_status cswgs_plan_test_waits(cswgs_plan p, int withhold_first_item, unsigned wait_polls);
+
 /* ---------------------------------------------------------------- misc --- */
 
 int cswgs_abi_version(void);

@@ -317,6 +317,11 @@ class Plan:
         check(self.lib.cswgs_serve_stats_get(self.handle, ctypes.byref(s)), "cswgs_serve_stats_get")
         return {k: getattr(s, k) for k, _ in s._fields_}
 
+    def test_waits(self, withhold_first_item: bool, wait_polls: int = 0):
+        """cswgs_plan_test_waits: the test of the tensor-core kernel's bounded waits."""
+        check(self.lib.cswgs_plan_test_waits(self.handle, 1 if withhold_first_item else 0, int(wait_polls)),
+              "cswgs_plan_test_waits")
+
     # ------------------------------------------------------ tuning/probes --
     def autotune(self, P: int, N: int, c: float) -> float:
         ms = ctypes.c_double()

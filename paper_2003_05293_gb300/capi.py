@@ -118,6 +118,7 @@ SIGNATURES = {
     "cswgs_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "cswgs_serve_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(cswgs_serve_stats)]),
     "cswgs_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, c_double_p]),
+    "cswgs_plan_test_waits": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_uint]),
     "cswgs_sincos_peak": (ctypes.c_int, [_P, c_double_p, c_double_p]),
     "cswgs_solve_noalloc": (ctypes.c_int, [c_double_p, c_double_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_int, ctypes.c_uint64, c_float_p, c_double_p, ctypes.c_void_p]),

@@ -807,6 +807,15 @@ cswgs_status cswgs_solve_batch(cswgs_plan p, const cswgs_request *reqs, int coun
     return CSWGS_OK;
 }
 
+cswgs_status cswgs_plan_test_waits(cswgs_plan p, int withhold_first_item, unsigned wait_polls)
+{
+    if (!p) return set_error(CSWGS_EINVAL, "NULL plan");
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->test_withhold = withhold_first_item ? 1u : 0u;
+    p->test_polls = wait_polls;
+    return CSWGS_OK;
+}
+
 cswgs_status cswgs_autotune(cswgs_plan p, int P, int N, double subset_fraction, double *best_ms)
 {
     if (!p) return set_error(CSWGS_EINVAL, "NULL plan");

@@ -53,7 +53,10 @@ constexpr int kRows = 128;          // tile rows (GEMM 1 M, GEMM 2 N)
 constexpr int kCols = 64;           // tile columns (GEMM 2 K; GEMM 1 N is re and im of them)
 constexpr int kChunk = 16;          // spots per GEMM 1 instruction (K)
 constexpr int kSpotBlock = 128;     // spots per GEMM 2 instruction (M)
-constexpr uint32_t kWaitPolls = 1u << 20;
+constexpr uint32_t kWaitPolls = 1u << 20;   // polls of a bounded wait, unless a launch asks for fewer
+
+// The launch's poll limit (set by thread 0 before the first block barrier).
+__shared__ uint32_t s_wait_polls;
 
 // component tiles (bytes): GEMM 1 operands per stage, GEMM 2 operands
 constexpr uint32_t kA1 = kRows * kChunk * 2;        // R' component [128 rows][16 spots]
@@ -121,7 +124,8 @@ __device__ __forceinline__ void commit(uint32_t mbar)
 // Bounded wait for phase `parity` of an mbarrier; false when it ran out.
 __device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity)
 {
-    for (uint32_t it = 0; it < kWaitPolls; ++it) {
+    const uint32_t polls = s_wait_polls;
+    for (uint32_t it = 0; it < polls; ++it) {
         uint32_t ok;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
@@ -1256,7 +1260,12 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     __shared__ G2Info s_g2;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5;
+    // queue[3] != 0 (a test of the bounded waits): the producer publishes no
+    // work item, so every other role's first wait runs out, before any copy
+    // or MMA is issued; queue[4] != 0: the poll limit of every wait
+    const bool withhold = queue[3] != 0u;
     if (tid == 0) {
+        tc::s_wait_polls = queue[4] != 0u ? queue[4] : tc::kWaitPolls;
         for (int b = 0; b < kBarsWs; ++b) {
             // the epilogue's releases arrive once per warp
             // S buffers and info slots go back from the epilogue and the GEMM 1 warp
@@ -1282,7 +1291,7 @@ iter_full_tcws_kernel(const HoloDev *__restrict__ holos, const LaunchSlot *__res
     constexpr int R = Lay<US>::kRing;
     unsigned *status = queue + 2;
     if (warp == W) {
-        control_load<R>(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
+        if (!withhold) control_load<R>(holos, slots, nslots, total_tiles, queue, m, s_info, mb, s_tmem, status);
     } else if (warp == W + 1) {
         control_gemm1<R>(m, s_info, mb, s_tmem, status);
     } else if (warp == W + 2) {

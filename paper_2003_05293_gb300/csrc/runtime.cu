@@ -574,7 +574,8 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     const LaunchSlot *slots = b->slots_d.as<LaunchSlot>();
     unsigned *queue = b->queue_d.as<unsigned>();
     const int count = (int)b->holos.size();
-    CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned), s));
+    // work queue, blocks done, status word (a bounded wait inside a kernel that ran out)
+    CSWGS_CUDA_TRY(cudaMemsetAsync(queue, 0, 3 * sizeof(unsigned), s));
     if (b->mask_bytes) CSWGS_CUDA_TRY(cudaMemsetAsync(b->mem.as<char>() + b->mask_begin, 0, b->mask_bytes, s));
     if (b->timing) CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->events[0], s, evflag));
     CSWGS_CUDA_TRY(launch_prep_fp32(holos, count, b->maxN, s));
@@ -646,6 +647,14 @@ cswgs_status batch_enqueue(Fp32Batch *b, cudaStream_t s)
         CSWGS_CUDA_TRY(e);
         b->graph = g;
         CSWGS_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    }
+    // the plan's bounded-wait test words (queue[3], queue[4]), when they changed
+    const unsigned want[2] = {b->plan->test_withhold, b->plan->test_polls};
+    if (want[0] != b->test_words[0] || want[1] != b->test_words[1]) {
+        CSWGS_CUDA_TRY(cudaMemcpyAsync(b->queue_d.as<unsigned>() + 3, want, sizeof want, cudaMemcpyHostToDevice, s));
+        CSWGS_CUDA_TRY(cudaStreamSynchronize(s));   // `want` lives on this stack frame
+        b->test_words[0] = want[0];
+        b->test_words[1] = want[1];
     }
     CSWGS_CUDA_TRY(cudaGraphLaunch(b->exec, s));
     return CSWGS_OK;

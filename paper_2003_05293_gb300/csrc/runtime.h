@@ -130,6 +130,7 @@ struct Fp32Batch {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_start = nullptr, ev_tail[2] = {nullptr, nullptr}, ev_scat[2] = {nullptr, nullptr};
     DevBuf copy_jobs;   // host phase maps written out by the copy kernel (cswgs_solve_batch)
+    unsigned test_words[2] = {0u, 0u};   // bounded-wait test words last written to the queue
     ~Fp32Batch();
 };
 
@@ -166,6 +167,8 @@ struct cswgs_plan_s {
     std::mutex pupil_mu;
     std::map<int, std::unique_ptr<cswgs::DevBuf>> pupil_rows;
     std::unique_ptr<cswgs::Server> server;
+    // test of the tensor-core kernel's bounded waits (cswgs_plan_test_waits)
+    unsigned test_withhold = 0u, test_polls = 0u;
 };
 
 struct cswgs_batch_s {
