@@ -85,6 +85,9 @@ def kernel_name(tile, kind):
     if kind == "sub":
         if tile["threads"] == SUBSET_TC:
             return "iter_full_tcws_kernel (tensor cores: every pixel through both products, u zero outside S_j)"
+        if tile["threads"] == SUBSET_GATHER:
+            return ("iter_subset_gather_kernel (CUDA cores: the pixels of S_j only, one complex multiply-add per "
+                    "pair and pass from the separable factors)")
         return "iter_subset_kernel<%d, %d> (CUDA cores: the pixels of S_j only, direct phasors)" % (
             tile["threads"], tile["pixels_per_thread"])
     if tile["full_threads"] in TC_KERNELS:
@@ -101,8 +104,10 @@ def dtype_label(tile):
 
 
 # threads marker of compressed iterations on the warp-specialised tensor-core
-# kernel (dense products, u zero outside the subset)
+# kernel (dense products, u zero outside the subset), and on the subset-only
+# gather kernel (CUDA cores, separable factors)
 SUBSET_TC = 1
+SUBSET_GATHER = 3
 
 
 def tensor_peak():
@@ -134,7 +139,24 @@ def subset_roofline(tile, pairs_sub_launch, n_sub, sub_ms, full_ms, sm_count, ma
                           "outside the subset (%d per step, %.1f%% of the step)" % (n_sub, share),
                 "issued_tensor_flops_per_algorithmic": 3.0 * args.P * args.P / max(1, Mp),
                 "ms_per_launch": sub_ms / max(1, n_sub),
+                "sincos_equivalent": {
+                    "achieved": 2.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e9 if n_sub else 0.0,
+                    "sfu_peak": sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9, "unit": "G sincos/s",
+                    "what": "the method's sine/cosine results per second (2 per subset pixel-spot pair and pass) "
+                            "that the separable tensor-core products stand in for, against the SFU's peak: the "
+                            "SFU roofline of a direct-phasor kernel does not bound this one"},
                 "tile": {"threads": TC_KERNELS[2][1], "blocks": tile["blocks"], "pixels": "128 rows x 64 columns"}}
+    if tile["threads"] == SUBSET_GATHER:
+        fma_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12     # TFLOP/s
+        ach = 8.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e12 if n_sub else 0.0
+        return {"bound": "alu", "pipe": "FP32 FMA", "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s",
+                "frac": ach / fma_peak, "traffic": traffic,
+                "peak_basis": "%d SMs x %d lanes x 2 flops x %.0f MHz (of derived)"
+                              % (sm_count, FP32_LANES_PER_SM, max_mhz),
+                "flops_basis": "8 flops (complex multiply-add) per subset pixel-spot pair and pass",
+                "kernel": "iter_subset_gather_kernel on compressed launches: the pixels of S_j only (%d per step, "
+                          "%.1f%% of the step)" % (n_sub, share),
+                "ms_per_launch": sub_ms / max(1, n_sub)}
     sfu_peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6 / 1e9           # G sin-or-cos/s
     ach = 2.0 * pairs_sub_launch * n_sub / (sub_ms * 1e-3) / 1e9 if n_sub else 0.0
     return {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": ach, "peak": sfu_peak,
@@ -147,15 +169,19 @@ def subset_roofline(tile, pairs_sub_launch, n_sub, sub_ms, full_ms, sm_count, ma
 
 
 def launches_per_step(tile, n_sub, n_full):
-    """Kernel launches of one batch step: the per-spot preparation, the
-    tensor-core constant tables (once per hologram), every compressed
-    iteration, and per full pass the kernel plus, on the tensor cores, its R'
-    table kernel and, for the warp-specialised kernel, its tails kernel."""
+    """Kernel launches of one batch step (square pupils): the per-spot
+    preparation, the tensor-core constant tables (once per hologram); per
+    compressed iteration on the tensor cores its R' tables, the kernel, the
+    tails and the subset-mask draws (side stream), on the gather kernel the
+    mask draws, the kernel and the tails, on the direct-phasor kernel one
+    launch; per full pass the kernel plus, on the tensor cores, its R' tables
+    and its tails."""
     ft = tile["full_threads"]
-    sub_tc = tile["threads"] == SUBSET_TC
-    tc = ft in TC_KERNELS or sub_tc
-    per_sub = 3 if sub_tc else 1      # tables + mask, the kernel, the tails
-    return 1 + (1 if tc else 0) + n_sub * per_sub + n_full * (1 + (1 if ft in TC_KERNELS else 0) + (1 if ft == 2 else 0))
+    sub = tile["threads"]
+    tc = ft in TC_KERNELS or sub == SUBSET_TC
+    per_sub = 4 if sub == SUBSET_TC else (3 if sub == SUBSET_GATHER else 1)
+    per_full = 3 if ft in TC_KERNELS else 1
+    return 1 + (1 if tc else 0) + n_sub * per_sub + n_full * per_full
 
 
 def full_roofline(tile, achieved_tflops, fma_peak, sm_count, max_mhz, traffic, n_launches, full_ms):
@@ -211,6 +237,8 @@ def parse():
                     help="arrival rate of the extra stream of the batch workload's holograms (3 s)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the compressed-iteration sweep (N x c)")
     ap.add_argument("--no-grid100", action="store_true", help="skip the headline shape on rotated 10 x 10 grids")
+    ap.add_argument("--no-sfu-leg", action="store_true",
+                    help="skip the CUDA-core compressed-iteration kernel timed at the workload")
     ap.add_argument("--quick", action="store_true",
                     help="short serving streams (5 s) and no oracle comparisons of the sweep")
     ap.add_argument("--no-serve", action="store_true")
@@ -572,6 +600,44 @@ def e2e_leg(args, plan, pbs, world, B):
             "steps": args.e2e_steps, "pageable_host_outputs": v_pageable, "pinned_host_outputs": v_pinned}
 
 
+def sfu_leg(args, pbs, flush, stream, world, local, sm_count, max_mhz, probe):
+    """The batch with its compressed iterations pinned to the CUDA-core kernel
+    (256 threads x 4 pixels: the pixels of S_j only, each phasor a fixed-point
+    argument and two SFU results), full passes as tuned: compressed ms per
+    launch and the SFU fraction (2 sine-or-cosine results per subset pixel-spot
+    pair and pass)."""
+    import tempfile
+
+    import torch
+
+    from paper_2003_05293_gb300 import Plan
+    B = len(pbs)
+    entries = {"P%d_N%d_B%d_c%d" % (128 * p, 2 ** n, 2 ** b, c): [256, 4, 2]
+               for p in range(1, 17) for n in range(4, 13) for b in range(0, 8) for c in range(0, 17)}
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune_sfu.json")
+        with open(path, "w") as f:
+            json.dump({"format": "cswgs-tune-3", "entries": entries}, f)
+        with Plan(device=local, precision="fp32", max_batch=max(64, B), max_N=max(1024, args.N),
+                  stream=stream.cuda_stream, tune_cache=path) as plan:
+            outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+            steps = max(3, args.steps // 2)
+            ms, res, kt, tile = timed_batch(plan, pbs, outs, flush, stream, steps, args.warmup, world)
+    n_sub = args.iters - min(2, args.iters)
+    sub_ms = sum(kt[1:1 + n_sub]) / max(1, n_sub)
+    Mp = math.floor(args.c * args.P * args.P)
+    pairs = B * 2.0 * args.N * Mp
+    sfu_peak = sm_count * SFU_PER_CLK_PER_SM * max_mhz * 1e6
+    ach = 2.0 * pairs / (sub_ms * 1e-3)
+    return {"value": job_throughput(B, world, steps, ms), "unit": "holograms/s", "compressed_ms_per_launch": sub_ms,
+            "kernel": kernel_name(tile, "sub"),
+            "sfu_roofline": {"bound": "alu", "pipe": "SFU sine/cosine", "achieved": ach / 1e9, "peak": sfu_peak / 1e9,
+                             "unit": "G sincos/s", "frac": ach / sfu_peak,
+                             "peak_basis": "%d SMs x %d/clk x %.0f MHz (probe measured %.0f G/s)"
+                                           % (sm_count, SFU_PER_CLK_PER_SM, max_mhz, probe / 1e9)},
+            "what": "compressed iterations on the CUDA cores (the subset's pixels only), full passes on the tensor cores"}
+
+
 def sweep_leg(args, plan, flush, stream, world, B, rank, local):
     """The precision workload's compressed-iteration sweep at P = args.P: N in
     {100, 300} x c in {1/4, 1/8, 1/16}, a batch of B holograms each (the
@@ -580,9 +646,21 @@ def sweep_leg(args, plan, flush, stream, world, B, rank, local):
     hologram's problem, map and result for the oracle comparison."""
     import torch
 
+    import tempfile
+
     from paper_2003_05293_gb300 import Plan
     runs, keep = [], {}
     n_sub = args.iters - min(2, args.iters)
+    # a plan with the compressed iterations pinned to the subset-only gather kernel
+    tmp = tempfile.TemporaryDirectory()
+    gpath = os.path.join(tmp.name, "tune_gather.json")
+    with open(gpath, "w") as f:
+        json.dump({"format": "cswgs-tune-3",
+                   "entries": {"P%d_N%d_B%d_c%d" % (128 * p, 2 ** n, 2 ** b, c): [SUBSET_GATHER, 1, 2]
+                               for p in range(1, 17) for n in range(4, 13) for b in range(0, 8) for c in range(17)}},
+                  f)
+    gplan = Plan(device=local, precision="fp32", max_batch=max(64, B), max_N=1024, stream=stream.cuda_stream,
+                 tune_cache=gpath)
     with Plan(device=local, precision="fp64", stream=stream.cuda_stream) as p64:
         for N in workloads.LARGE_N:
             for c in workloads.LARGE_C:
@@ -603,10 +681,17 @@ def sweep_leg(args, plan, flush, stream, world, B, rank, local):
                          "compressed_method_tflops": 8.0 * pairs / (sub_ms * 1e-3) / 1e12,
                          "e_mean": float(np.mean([r["e"] for r in res])),
                          "u_mean": float(np.mean([r["u"] for r in res])), "tile": tile}
-                entry["fp64_gpu"] = fp64_latency(p64, pbs[:3 if N * c > 50 else 5], stream)
                 keep[(N, c)] = (pbs[0], outs[0].cpu().numpy(), res[0])
+                if N <= 192:
+                    gms, gres, gkt, gtile = timed_batch(gplan, pbs, outs, flush, stream, 3, args.warmup, world)
+                    entry["gather_compressed_ms_per_launch"] = sum(gkt[1:1 + n_sub]) / max(1, n_sub)
+                    entry["gather_value"] = job_throughput(B, world, 3, gms)
+                    entry["gather_kernel"] = kernel_name(gtile, "sub")
+                entry["fp64_gpu"] = fp64_latency(p64, pbs[:3 if N * c > 50 else 5], stream)
                 runs.append(entry)
                 del outs
+    gplan.close()
+    tmp.cleanup()
     return {"P": args.P, "batch": B, "iterations": args.iters,
             "what": "compressed-iteration sweep of the precision workload: a batch per (N, c), FP32 path as tuned; "
                     "compressed_method_tflops counts 8 flops per subset pixel-spot pair and pass",
@@ -767,6 +852,13 @@ def main():
                                "tile": t16, "what": what16}
         b16.close()
         p16.close()
+
+    # the CUDA-core compressed-iteration kernel (direct phasors on the SFU, the
+    # pixels of S_j only) at the same workload, pinned through a tune cache:
+    # its time per launch and its fraction of the SFU's sine/cosine peak, beside
+    # the tensor-core kernel the autotuner picks
+    if not args.no_sfu_leg:
+        line["cuda_core_compressed"] = sfu_leg(args, pbs, flush, stream, world, local, sm_count, max_mhz, probe)
 
     # FP64 GPU baseline (plain double-precision kernels), one hologram at a time:
     # per-hologram device time (CUDA events on the plan's stream)

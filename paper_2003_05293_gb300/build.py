@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libcswgs.so")
 SOURCES = ["kernels_fp32.cu", "kernels_fp64.cu", "runtime.cu", "tuner.cu", "capi.cu", "serve.cu",
-           "noalloc.cu", "kernels_tc.cu"]
+           "noalloc.cu", "kernels_tc.cu", "kernels_gather.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

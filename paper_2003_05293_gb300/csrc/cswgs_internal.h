@@ -111,13 +111,21 @@ constexpr int kSubsetTc = 1;
 // The two iteration kernels: compressed-iteration tiles, separable full-pass tiles.
 enum LaunchKind : int { kLaunchSubset = 0, kLaunchFull = 1 };
 
-// Whether a batch needs the tensor-core factor tables, and whether a launch of
-// a kind runs on a tensor-core kernel.
+// threads value that runs the compressed iterations on the subset-only gather
+// kernel (kernels_gather.cu): the pixels of S_j only, on the CUDA cores, each
+// pair one complex multiply-add per pass with the separable factors of Eq. 2;
+// spots up to 192
+constexpr int kSubsetGather = 3;
+
+// Whether a batch needs the tensor-core factor tables, whether a launch of a
+// kind runs on a tensor-core kernel (R' tables before it), and whether its
+// compressed launches read the subset bit masks.
 inline bool uses_tc(TileShape s) { return is_full_tc(s.full_threads) || s.threads == kSubsetTc; }
 inline bool launch_uses_tc(TileShape s, int kind)
 {
     return kind == kLaunchSubset ? s.threads == kSubsetTc : is_full_tc(s.full_threads);
 }
+inline bool uses_masks(TileShape s) { return s.threads == kSubsetTc || s.threads == kSubsetGather; }
 inline int mask_words_of(int P) { return (P + 31) / 32; }
 
 // Kernel launchers (kernels_fp32.cu).
@@ -143,6 +151,14 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
                                 bool masks, cudaStream_t s);
 cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
                                    cudaStream_t s);
+cudaError_t launch_tc_tails(const HoloDev *holos, const LaunchSlot *slots, int nslots, int maxN, bool subset,
+                            cudaStream_t s);
+// Subset-only gather kernel (kernels_gather.cu): work items per hologram,
+// resident blocks (0: N too large), launch (the kernel and the tails).
+int subset_gather_items(int P);
+int subset_gather_max_grid(int maxN, int sm_count);
+cudaError_t launch_subset_gather(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_items, int maxN,
+                                 unsigned *queue, int grid, cudaStream_t s);
 // Work items of a tensor-core launch: chooses the strip length (tiles of one
 // row block per work item, 1 for holograms of more than one GEMM 2 spot
 // block; `forced` > 0 takes that length) and rewrites each slot's strip, tiles

@@ -371,12 +371,8 @@ __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__rest
 
 // R' = w a e^{i theta} R (GEMM 1's A: 128 rows x 16 spots per block) of the
 // hologram of each slot, from its current spot state; with `masks`, for a
-// compressed pass also the subset mask (bit c of word r * mask_words + c / 32
-// is set when pixel r P + c belongs to S_j), else a separate launch draws it.
-__device__ __forceinline__ uint32_t *subset_mask(const HoloDev &H, int j)
-{
-    return H.mask + (size_t)(j & 1) * (size_t)H.mask_stride;
-}
+// compressed pass also the subset mask (subset_mask), else a separate launch
+// draws it.
 
 // The Mp draws of S_j (Section 3) of the slot's hologram, each setting its
 // pixel's bit in the iteration's mask, which is clear before (the tails of the
@@ -1331,7 +1327,7 @@ __global__ void __launch_bounds__(kTailThreads) tcws_tails_kernel(const HoloDev 
     const HoloDev &H = holos[sl.holo];
     if (blockIdx.y > 0) {
         if (sl.pass == kPassSubset && H.mask) {
-            uint32_t *mask = tc::subset_mask(H, sl.j);
+            uint32_t *mask = subset_mask(H, sl.j);
             const size_t words = (size_t)H.P * H.mask_words;
             for (size_t i = (size_t)(blockIdx.y - 1) * blockDim.x + threadIdx.x; i < words;
                  i += (size_t)(gridDim.y - 1) * blockDim.x)
@@ -1377,6 +1373,17 @@ static void tcws_launch_one(const HoloDev *holos, const LaunchSlot *slots, int n
         holos, slots, nslots, total_tiles, queue);
 }
 
+// The per-hologram tails of a launch whose kernel writes tile partials and no
+// tail of its own: one block per slot, plus (compressed launches) blocks that
+// clear the subset masks.
+cudaError_t launch_tc_tails(const HoloDev *holos, const LaunchSlot *slots, int nslots, int maxN, bool subset,
+                            cudaStream_t s)
+{
+    const dim3 tails((unsigned)nslots, 1u + (subset ? 8u : 0u));
+    tcws_tails_kernel<<<tails, kTailThreads, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
+    return cudaGetLastError();
+}
+
 template <int W>
 static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, int nslots, int total_tiles, int maxN,
                                unsigned *queue, int grid, bool subset, int f16, cudaStream_t s)
@@ -1385,10 +1392,9 @@ static cudaError_t tcws_launch(const HoloDev *holos, const LaunchSlot *slots, in
     (void)cudaGetLastError();
     if (f16) tcws_launch_one<W, true, K4>(holos, slots, nslots, total_tiles, queue, grid, s);
     else tcws_launch_one<W, false, K4>(holos, slots, nslots, total_tiles, queue, grid, s);
-    // one tail block per slot, plus (compressed launches) blocks that clear the masks
-    const dim3 tails((unsigned)nslots, 1u + (subset ? 8u : 0u));
-    tcws_tails_kernel<<<tails, kTailThreads, (size_t)maxN * sizeof(float2), s>>>(holos, slots);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_tc_tails(holos, slots, nslots, maxN, subset, s);
 }
 
 // epilogue warps of the warp-specialised kernel

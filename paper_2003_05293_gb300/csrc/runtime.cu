@@ -201,7 +201,7 @@ bool shape_supported(TileShape shape)
 {
     // the CUDA-core kernels the shape names, with stand-ins for the tensor-core ones
     TileShape cuda_core = shape;
-    if (shape.threads == kSubsetTc) {
+    if (shape.threads == kSubsetTc || shape.threads == kSubsetGather) {
         cuda_core.threads = 256;
         cuda_core.ppt = 4;
     }
@@ -214,6 +214,7 @@ int shape_max_grid(TileShape shape, int kind, int maxN, int sm_count)
     if (kind == kLaunchFull && is_full_tc(shape.full_threads))
         return full_tc_max_grid(shape.full_threads, maxN, sm_count);
     if (kind == kLaunchSubset && shape.threads == kSubsetTc) return full_tc_max_grid(kFullTcWs, maxN, sm_count);
+    if (kind == kLaunchSubset && shape.threads == kSubsetGather) return subset_gather_max_grid(maxN, sm_count);
     return iter_fp32_max_grid(shape, kind, maxN, sm_count);
 }
 
@@ -229,6 +230,8 @@ cudaError_t shape_launch(TileShape shape, int kind, const HoloDev *holos, const 
         return launch_full_tc(shape.full_threads, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
     if (kind == kLaunchSubset && shape.threads == kSubsetTc)
         return launch_subset_tc(holos, slots, nslots, total_tiles, maxN, queue, grid, shape.fp16, s);
+    if (kind == kLaunchSubset && shape.threads == kSubsetGather)
+        return launch_subset_gather(holos, slots, nslots, total_tiles, maxN, queue, grid, s);
     return launch_iter_fp32(shape, kind, holos, slots, nslots, total_tiles, maxN, queue, grid, s);
 }
 
@@ -237,7 +240,8 @@ TileShape full_fallback(TileShape shape, int maxN, int sm_count)
     // past the tensor-core kernel's spot limit the CUDA-core kernels take over
     if (shape.full_threads == kFullTcWs && full_tc_max_grid(kFullTcWs, maxN, sm_count) <= 0)
         shape.full_threads = 256;
-    if (shape.threads == kSubsetTc && full_tc_max_grid(kFullTcWs, maxN, sm_count) <= 0) {
+    if ((shape.threads == kSubsetTc && full_tc_max_grid(kFullTcWs, maxN, sm_count) <= 0) ||
+        (shape.threads == kSubsetGather && subset_gather_max_grid(maxN, sm_count) <= 0)) {
         shape.threads = 256;
         shape.ppt = 4;
     }
@@ -248,6 +252,7 @@ int pass_tiles(int pass, int P, int Mp, TileShape shape)
 {
     if (pass != kPassSubset) return shape_full_tiles(P, shape);
     if (shape.threads == kSubsetTc) return full_tc_tiles(P);
+    if (shape.threads == kSubsetGather) return subset_gather_items(P);
     const int tp = shape.threads * shape.ppt;
     return (Mp + tp - 1) / tp;
 }
@@ -324,10 +329,11 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
         }
         b->maxN = std::max(b->maxN, s.N);
     }
-    // subset masks of compressed passes on the tensor cores, one block for all
+    // subset masks of compressed passes on the tensor cores or the gather
+    // kernel, one block for all
     std::vector<size_t> m_off(count, 0);
     b->mask_begin = work;
-    if (shape.threads == kSubsetTc)
+    if (uses_masks(shape))
         for (int h = 0; h < count; ++h) {
             m_off[h] = work;
             work += align256(2 * sizeof(uint32_t) * (size_t)b->specs[h].P * mask_words_of(b->specs[h].P));
@@ -389,7 +395,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             w += align256(sizeof(float) * (size_t)M);
         }
         H.phase_out = b->own_phase[h];
-        if (shape.threads == kSubsetTc) {
+        if (uses_masks(shape)) {
             H.mask = reinterpret_cast<uint32_t *>(base + m_off[h]);
             H.mask_words = mask_words_of(s.P);
             H.mask_stride = s.P * H.mask_words;
@@ -483,7 +489,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     }
     bool square = true;
     for (const HoloDev &H : b->holos) square = square && H.aperture == 0;
-    if (shape.threads == kSubsetTc && square) {
+    if (uses_masks(shape) && square) {
         CSWGS_CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
         for (cudaEvent_t *e : {&b->ev_start, &b->ev_tail[0], &b->ev_tail[1], &b->ev_scat[0], &b->ev_scat[1]})
             CSWGS_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
@@ -585,7 +591,7 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     // side stream, one step ahead: the draw of step L + 1 runs beside the launch
     // of step L, after the tails of step L - 1 have cleared that mask (each
     // hologram advances one iteration per step, so it alternates its two masks).
-    const bool side_masks = b->side && launch_uses_tc(b->shape, kLaunchSubset);
+    const bool side_masks = b->side && uses_masks(b->shape);
     auto masked = [&](size_t L) { return L < steps && b->l_tiles[2 * L + kLaunchSubset] > 0; };
     bool tail_rec[2] = {false, false};
     auto draw = [&](size_t L) -> cswgs_status {
@@ -612,6 +618,8 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
             if (launch_uses_tc(b->shape, kind))
                 CSWGS_CUDA_TRY(launch_tc_rw_tables(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count,
                                                    !side_draw, s));
+            else if (kind == kLaunchSubset && uses_masks(b->shape) && !side_draw)
+                CSWGS_CUDA_TRY(launch_tc_mask_scatter(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count, s));
             if (side_draw) CSWGS_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_scat[L & 1], 0));
             CSWGS_CUDA_TRY(shape_launch(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
                                         b->l_maxN[i], queue, grid, s));

@@ -152,7 +152,7 @@ size_t Server::footprint(const HoloSpec &s) const
         b += al256(rw) + al256(c) + al256(cs);
         if (shape_.fp16 && shape_.threads == kSubsetTc) b += al256(cs / 2);
     }
-    if (shape_.threads == kSubsetTc) b += al256(sizeof(uint32_t) * (size_t)s.P * mask_words_of(s.P));
+    if (uses_masks(shape_)) b += al256(sizeof(uint32_t) * (size_t)s.P * mask_words_of(s.P));
     return b;
 }
 
@@ -214,7 +214,7 @@ void Server::place(Req &r)
             o += al256(cs / 2);
         }
     }
-    if (shape_.threads == kSubsetTc) {
+    if (uses_masks(shape_)) {
         // the subset mask starts clear (each compressed launch's tails clear it again)
         H.mask = reinterpret_cast<uint32_t *>(b + o);
         H.mask_words = mask_words_of(s.P);
@@ -461,6 +461,8 @@ void Server::loop()
                 g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
             if (launch_uses_tc(shape_, kind))
                 chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, true, stream_));
+            else if (kind == kLaunchSubset && uses_masks(shape_))
+                chk(launch_tc_mask_scatter(holos, sd + first, group_slots[kind], p_->sm_count, stream_));
             chk(shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
                              queue, std::min(g->second, group_tiles[kind]), stream_));
         }

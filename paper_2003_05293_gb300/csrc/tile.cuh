@@ -351,6 +351,14 @@ __device__ __forceinline__ uint32_t subset_pixel(const HoloDev &H, const SubsetD
     return pupil_pixel(H, permute_domain(kk, (uint32_t)H.D, H.fa, d.fb, d.K));
 }
 
+// The subset mask of iteration j of a compressed pass on the tensor cores or
+// the subset-only gather kernel: bit c of word r * mask_words + c / 32 is set
+// when pixel r P + c belongs to S_j (two masks per hologram, by the parity of j).
+__device__ __forceinline__ uint32_t *subset_mask(const HoloDev &H, int j)
+{
+    return H.mask + (size_t)(j & 1) * (size_t)H.mask_stride;
+}
+
 // Pupil amplitude A = exp(-rho^2 / waist^2) = exp2(-kA rho^2) (Eq. 3's A;
 // Section 4's Gaussian beam), 1 for a uniform pupil.
 __device__ __forceinline__ float pupil_amp(const HoloDev &H, float rho2)

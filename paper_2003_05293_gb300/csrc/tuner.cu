@@ -78,12 +78,13 @@ std::string tune_key(const std::vector<HoloSpec> &specs, bool fp16)
     return buf;
 }
 
-// Candidates: compressed-iteration kernel (threads, pixels per thread, or the
-// masked tensor-core pass) and full-pass kernel (threads, or a tensor-core
-// kernel); the two kinds run as separate launches, so each is tuned on its
+// Candidates: compressed-iteration kernel (threads, pixels per thread, the
+// masked tensor-core pass, or the subset-only gather kernel) and full-pass
+// kernel (threads, or a tensor-core kernel); the two kinds run as separate launches, so each is tuned on its
 // own launches.
-static const int kSubCandidates[][2] = {{128, 2}, {128, 4}, {128, 8}, {256, 2}, {256, 4},
-                                        {256, 8}, {512, 1}, {512, 2}, {512, 4}, {kSubsetTc, 1}};
+static const int kSubCandidates[][2] = {{128, 2}, {128, 4}, {128, 8}, {256, 2},  {256, 4},
+                                        {256, 8}, {512, 1}, {512, 2}, {512, 4}, {kSubsetTc, 1},
+                                        {kSubsetGather, 1}};
 static const int kFullCandidates[] = {128, 256, 512, kFullTcWs};
 
 static std::vector<HoloSpec> synthetic(const TuneKey &k, double c)
