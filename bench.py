@@ -690,12 +690,29 @@ def sweep_leg(args, plan, flush, stream, world, B, rank, local):
                 entry["fp64_gpu"] = fp64_latency(p64, pbs[:3 if N * c > 50 else 5], stream)
                 runs.append(entry)
                 del outs
+    # the serving workload's smallest clouds: the tensor-core kernel pads the
+    # spots to a 128-spot block, the gather kernel to a multiple of 32
+    small = []
+    for N in (10,):
+        for c in workloads.LARGE_C:
+            pbs = [workloads.problem(args.P, N, 10.0, c, args.iters, seed=rank * 100000 + 70000 + h) for h in range(B)]
+            outs = [torch.empty(pb.M, dtype=torch.float32, device="cuda") for pb in pbs]
+            ms, res, kt, tile = timed_batch(plan, pbs, outs, flush, stream, 3, args.warmup, world)
+            gms, gres, gkt, gtile = timed_batch(gplan, pbs, outs, flush, stream, 3, args.warmup, world)
+            small.append({"N": N, "c": c, "value": job_throughput(B, world, 3, ms),
+                          "compressed_ms_per_launch": sum(kt[1:1 + n_sub]) / max(1, n_sub),
+                          "compressed_kernel": kernel_name(tile, "sub"),
+                          "gather_compressed_ms_per_launch": sum(gkt[1:1 + n_sub]) / max(1, n_sub),
+                          "gather_value": job_throughput(B, world, 3, gms),
+                          "e_mean": float(np.mean([r["e"] for r in res])),
+                          "gather_e_mean": float(np.mean([r["e"] for r in gres]))})
+            del outs
     gplan.close()
     tmp.cleanup()
     return {"P": args.P, "batch": B, "iterations": args.iters,
             "what": "compressed-iteration sweep of the precision workload: a batch per (N, c), FP32 path as tuned; "
                     "compressed_method_tflops counts 8 flops per subset pixel-spot pair and pass",
-            "runs": runs}, keep
+            "runs": runs, "small_n": small}, keep
 
 
 def main():
