@@ -595,8 +595,9 @@ def e2e_leg(args, plan, pbs, world, B):
             "h2d_bytes_per_step": int(sum(pb.N * 3 * 8 for pb in pbs)),
             "d2h_bytes_per_step": int(sum(pb.M * 4 + 16 for pb in pbs)),
             "api": "cswgs_batch_create_host / cswgs_batch_update / cswgs_batch_run / cswgs_batch_results: host "
-                   "spot arrays in (staged through pinned memory), host phase maps and e, u out; two batches "
-                   "alternate so that one's copies overlap the other's computation",
+                   "spot arrays in (staged through pinned memory), host phase maps (pinned: copy engines; pageable: "
+                   "the copy kernel) and e, u out; two batches alternate so that one's copies overlap the other's "
+                   "computation",
             "steps": args.e2e_steps, "pageable_host_outputs": v_pageable, "pinned_host_outputs": v_pinned}
 
 

@@ -300,8 +300,10 @@ cswgs_status cswgs_batch_destroy(cswgs_batch b);
  * (the method is that of cswgs_batch_create; this form only moves the data).
  * As cswgs_batch_create, except that:
  *  - every request with a phase map asks for a host one (out_on_host = 1;
- *    pinned memory, or pageable memory on a device that shares the host's
- *    page tables, is written by a copy kernel, other memory by cudaMemcpyAsync);
+ *    pinned memory is written by cudaMemcpyAsync on the copy engines, which
+ *    leave the SMs to the other batch's iterations; pageable memory on a
+ *    device that shares the host's page tables by a copy kernel; other memory
+ *    by cudaMemcpyAsync);
  *  - the batch runs on a stream of its own (not the plan's): each
  *    cswgs_batch_run queues on it the copy of the staged inputs to the device,
  *    the batch's graph, e and u into a pinned host block and the phase maps to

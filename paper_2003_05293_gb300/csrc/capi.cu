@@ -127,6 +127,16 @@ static float *host_direct(const cswgs_plan_s *p, float *h)
     return nullptr;
 }
 
+static bool is_pinned(const float *h)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 // Writes the maps of `jobs` out (one launch), on stream s after the solve.
 static cswgs_status copy_maps(cswgs_plan_s *p, DevBuf &buf, const std::vector<MapCopy> &jobs, cudaStream_t s)
 {
@@ -531,12 +541,17 @@ cswgs_status cswgs_batch_run(cswgs_batch b)
     CSWGS_TRY(batch_enqueue(fb, s));
     eu_gather_kernel<<<1, 128, 0, s>>>(fb->holos_d.as<HoloDev>(), b->count, b->eu_host);
     CSWGS_CUDA_TRY(cudaGetLastError());
+    // pinned maps go out on the copy engines: host batches are meant to
+    // alternate, and the engines leave the SMs to the other batch's
+    // iterations (the copy kernel would share them); pageable maps the GPU can
+    // write go through the copy kernel
     std::vector<MapCopy> jobs;
     for (int i = 0; i < b->count; ++i) {
         float *dst = b->host_out[i];
         if (!dst) continue;
         const size_t n = (size_t)fb->specs[i].P * fb->specs[i].P;
-        if (float *d = host_direct(p, dst))
+        float *d = is_pinned(dst) ? nullptr : host_direct(p, dst);
+        if (d)
             jobs.push_back(MapCopy{fb->own_phase[i], d, n});
         else
             CSWGS_CUDA_TRY(cudaMemcpyAsync(dst, fb->own_phase[i], sizeof(float) * n, cudaMemcpyDeviceToHost, s));
