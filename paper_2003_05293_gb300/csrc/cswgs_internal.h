@@ -148,8 +148,9 @@ cudaError_t launch_subset_tc(const HoloDev *holos, const LaunchSlot *slots, int 
 void full_tc_table_bytes(int P, int N, size_t *rw, size_t *c, size_t *cs);   // cs: split BF16 (FP16: half)
 cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count, cudaStream_t s);
 cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
-                                bool masks, cudaStream_t s);
-cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
+                                cudaStream_t s);
+// subset masks of a launch's compressed slots (holograms at most maxP pixels a side)
+cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int maxP, int sm_count,
                                    cudaStream_t s);
 cudaError_t launch_tc_tails(const HoloDev *holos, const LaunchSlot *slots, int nslots, int maxN, bool subset,
                             cudaStream_t s);

@@ -370,9 +370,7 @@ __global__ void __launch_bounds__(256) const_tables_kernel(const HoloDev *__rest
 }
 
 // R' = w a e^{i theta} R (GEMM 1's A: 128 rows x 16 spots per block) of the
-// hologram of each slot, from its current spot state; with `masks`, for a
-// compressed pass also the subset mask (subset_mask), else a separate launch
-// draws it.
+// hologram of each slot, from its current spot state (rw_tables_kernel below).
 
 // The Mp draws of S_j (Section 3) of the slot's hologram, each setting its
 // pixel's bit in the iteration's mask, which is clear before (the tails of the
@@ -398,13 +396,53 @@ __global__ void __launch_bounds__(256) mask_scatter_kernel(const HoloDev *__rest
     if (sl.pass == kPassSubset && H.mask) scatter_subset(H, sl);
 }
 
+// The same masks drawn in shared memory: G CTAs per slot (grid G x slots),
+// each holding the slot's whole mask and taking 1 / G of the Mp draws, each
+// draw an OR in shared memory; the CTA's copy then goes out word by word (G =
+// 1: stored whole, zero words included; G > 1: the non-zero words ORed into
+// the mask, which is clear before).  P^2 / 8 bytes of shared memory: up to P
+// of about 1280.
+constexpr int kLocalThreads = 1024;
+
+__global__ void __launch_bounds__(kLocalThreads) mask_local_kernel(const HoloDev *__restrict__ holos,
+                                                                   const LaunchSlot *__restrict__ slots)
+{
+    extern __shared__ __align__(16) uint32_t s_words[];
+    const LaunchSlot sl = slots[blockIdx.y];
+    const HoloDev H = holos[sl.holo];
+    if (sl.pass != kPassSubset || !H.mask) return;
+    const uint32_t G = gridDim.x, x = blockIdx.x;
+    const int P = H.P, mw = H.mask_words, words = P * mw;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < words; i += kLocalThreads) s_words[i] = 0u;
+    __syncthreads();
+    const SubsetDraw d = subset_draw(H, sl.j);
+    const UDiv dP = udiv_of((uint32_t)P);
+    const uint32_t k0 = (uint32_t)((uint64_t)H.Mp * x / G), k1 = (uint32_t)((uint64_t)H.Mp * (x + 1) / G);
+    for (uint32_t k = k0 + tid; k < k1; k += kLocalThreads) {
+        const uint32_t m = subset_pixel(H, d, k);
+        uint32_t c;
+        const uint32_t r = udiv(m, dP, c);
+        atomicOr(s_words + r * (uint32_t)mw + (c >> 5), 1u << (c & 31));
+    }
+    __syncthreads();
+    uint32_t *g = subset_mask(H, sl.j);
+    if (G == 1) {
+        for (int i = tid; i < words; i += kLocalThreads) g[i] = s_words[i];
+    } else {
+        for (int i = tid; i < words; i += kLocalThreads) {
+            const uint32_t v = s_words[i];
+            if (v) atomicOr(g + i, v);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restrict__ holos,
-                                                        const LaunchSlot *__restrict__ slots, int masks)
+                                                        const LaunchSlot *__restrict__ slots)
 {
     const LaunchSlot sl = slots[blockIdx.y];
     const HoloDev H = holos[sl.holo];
     if (!H.rwtab) return;
-    if (masks && sl.pass == kPassSubset && H.mask) scatter_subset(H, sl);
     const int P = H.P, N = H.N, half = P >> 1, nc = nchunks(N);
     const int items = ((P + kRows - 1) / kRows) * nc * 256;      // (block, 128 rows x 2 groups)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items; i += gridDim.x * blockDim.x) {
@@ -1468,21 +1506,40 @@ cudaError_t launch_tc_const_tables(const HoloDev *holos, int count, int sm_count
 }
 
 cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
-                                bool masks, cudaStream_t s)
+                                cudaStream_t s)
 {
     if (nslots <= 0) return cudaSuccess;
     (void)cudaGetLastError();
-    // a wide grid: the subset masks' scattered bit sets are latency-bound
     dim3 grid((unsigned)std::max(1, 16 * sm_count / std::max(1, nslots)), (unsigned)nslots);
-    tc::rw_tables_kernel<<<grid, 256, 0, s>>>(holos, slots, masks ? 1 : 0);
+    tc::rw_tables_kernel<<<grid, 256, 0, s>>>(holos, slots);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int sm_count,
+// The shared-memory form of the mask draw for a launch whose holograms are
+// at most maxP pixels a side: the CTAs per slot (about one SM's worth of
+// slots per wave), or 0 when the mask does not fit a CTA's shared memory.
+static int mask_local_shape(int maxP, int nslots, int sm_count, size_t *smem)
+{
+    *smem = (size_t)maxP * (size_t)mask_words_of(maxP) * 4;
+    if (*smem > 200 * 1024) return 0;
+    if (cudaFuncSetAttribute(tc::mask_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return std::max(1, std::min(8, sm_count / std::max(1, nslots)));
+}
+
+cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int maxP, int sm_count,
                                    cudaStream_t s)
 {
     if (nslots <= 0) return cudaSuccess;
     (void)cudaGetLastError();
+    size_t smem = 0;
+    if (const int G = mask_local_shape(maxP, nslots, sm_count, &smem)) {
+        tc::mask_local_kernel<<<dim3((unsigned)G, (unsigned)nslots), tc::kLocalThreads, smem, s>>>(holos, slots);
+        return cudaGetLastError();
+    }
     // one block per SM beside the persistent kernel it overlaps (two slowed
     // that kernel more, one per two SMs delayed the next launch)
     dim3 grid((unsigned)std::max(1, sm_count / std::max(1, nslots)), (unsigned)nslots);

@@ -426,17 +426,24 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     // one launch of each kernel kind that has slots in it
     int L_max = 0;
     for (auto &s : b->specs) L_max = std::max(L_max, schedule_launches(s));
-    // heavier tiles first: order holograms by N (tile cost) descending
+    // heavier tiles first: order holograms by N (tile cost) descending; among
+    // holograms of equal N every other step runs backwards, so that a launch
+    // starts on the holograms whose factor tables the previous launch read
+    // last (still in L2)
     std::vector<int> order(count);
     for (int h = 0; h < count; ++h) order[h] = h;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int c) { return b->specs[a].N > b->specs[c].N; });
+    std::vector<int> order_back(order);
+    std::stable_sort(order_back.begin(), order_back.end(), [&](int a, int c) {
+        return b->specs[a].N != b->specs[c].N ? b->specs[a].N > b->specs[c].N : a > c;
+    });
     std::vector<LaunchSlot> slots;
     double pairs_total = 0.0, pairs_iter = 0.0;
     for (int L = 0; L < L_max; ++L) {
         for (int kind = 0; kind < 2; ++kind) {
-            int first = (int)slots.size(), tiles = 0, mN = 0;
-            for (int h : order) {
+            int first = (int)slots.size(), tiles = 0, mN = 0, mP = 0;
+            for (int h : (L & 1) ? order_back : order) {
                 const HoloSpec &s = b->specs[h];
                 int pass = pass_of(s, L);
                 if (pass < 0 || (pass == kPassSubset) != (kind == kLaunchSubset)) continue;
@@ -451,6 +458,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
                 sl.pad = 0;
                 tiles += sl.tiles;
                 mN = std::max(mN, s.N);
+                mP = std::max(mP, s.P);
                 slots.push_back(sl);
                 double pr = 2.0 * (double)s.N * (double)sl.count;
                 pairs_total += pr;
@@ -470,6 +478,7 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
             b->l_nslots.push_back((int)slots.size() - first);
             b->l_tiles.push_back(tiles);
             b->l_maxN.push_back(mN);
+            b->l_maxP.push_back(mP);
         }
     }
     b->pairs_total = pairs_total;
@@ -591,14 +600,14 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     // side stream, one step ahead: the draw of step L + 1 runs beside the launch
     // of step L, after the tails of step L - 1 have cleared that mask (each
     // hologram advances one iteration per step, so it alternates its two masks).
-    const bool side_masks = b->side && uses_masks(b->shape);
+    const bool side_masks = false && b->side && uses_masks(b->shape);
     auto masked = [&](size_t L) { return L < steps && b->l_tiles[2 * L + kLaunchSubset] > 0; };
     bool tail_rec[2] = {false, false};
     auto draw = [&](size_t L) -> cswgs_status {
         if (tail_rec[L & 1]) CSWGS_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_tail[L & 1], 0));
         const size_t i = 2 * L + kLaunchSubset;
-        CSWGS_CUDA_TRY(launch_tc_mask_scatter(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count,
-                                              b->side));
+        CSWGS_CUDA_TRY(launch_tc_mask_scatter(holos, slots + b->l_slot0[i], b->l_nslots[i], b->l_maxP[i],
+                                              b->plan->sm_count, b->side));
         CSWGS_CUDA_TRY(cudaEventRecordWithFlags(b->ev_scat[L & 1], b->side, 0));
         return CSWGS_OK;
     };
@@ -615,11 +624,11 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
             if (tiles == 0) continue;
             const int grid = std::min(b->grid[kind], tiles);
             const bool side_draw = side_masks && kind == kLaunchSubset;
+            if (kind == kLaunchSubset && uses_masks(b->shape) && !side_draw)
+                CSWGS_CUDA_TRY(launch_tc_mask_scatter(holos, slots + b->l_slot0[i], b->l_nslots[i], b->l_maxP[i],
+                                                      b->plan->sm_count, s));
             if (launch_uses_tc(b->shape, kind))
-                CSWGS_CUDA_TRY(launch_tc_rw_tables(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count,
-                                                   !side_draw, s));
-            else if (kind == kLaunchSubset && uses_masks(b->shape) && !side_draw)
-                CSWGS_CUDA_TRY(launch_tc_mask_scatter(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count, s));
+                CSWGS_CUDA_TRY(launch_tc_rw_tables(holos, slots + b->l_slot0[i], b->l_nslots[i], b->plan->sm_count, s));
             if (side_draw) CSWGS_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_scat[L & 1], 0));
             CSWGS_CUDA_TRY(shape_launch(b->shape, kind, holos, slots + b->l_slot0[i], b->l_nslots[i], tiles,
                                         b->l_maxN[i], queue, grid, s));

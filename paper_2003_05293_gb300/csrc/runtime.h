@@ -113,7 +113,7 @@ struct Fp32Batch {
     DevBuf holos_d, slots_d, queue_d;
     void *staging = nullptr;              // pinned host copy of the inputs
     std::vector<float *> own_phase;       // internal phase buffers (host outputs), per hologram
-    std::vector<int> l_slot0, l_nslots, l_tiles, l_maxN;   // per (step, kernel kind)
+    std::vector<int> l_slot0, l_nslots, l_tiles, l_maxN, l_maxP;   // per (step, kernel kind)
     TileShape shape{256, 4, 256};
     int grid[2] = {0, 0};                                     // resident blocks per kernel kind
     int maxN = 0;
@@ -123,10 +123,11 @@ struct Fp32Batch {
     std::vector<cudaEvent_t> events;      // launch boundaries (timing)
     double pairs_total = 0.0, pairs_iter = 0.0;
     size_t mask_begin = 0, mask_bytes = 0;   // subset masks (cleared at the start of every run)
-    // the next compressed launch's subset masks are drawn on a side stream while
-    // the current launch runs (two masks per hologram, by the parity of j), when
-    // every hologram has the square aperture; a round pupil's draws (a row
-    // search each) are too slow to hide and stay in the R' table kernel
+    // the next compressed launch's subset masks are drawn on a side stream
+    // (two masks per hologram, by the parity of j), beside the tails and the
+    // R' tables between launches, when every hologram has the square
+    // aperture; a round pupil's draws (a row search each) run on the main
+    // stream before the launch
     cudaStream_t side = nullptr;
     cudaEvent_t ev_start = nullptr, ev_tail[2] = {nullptr, nullptr}, ev_scat[2] = {nullptr, nullptr};
     DevBuf copy_jobs;   // host phase maps written out by the copy kernel (cswgs_solve_batch)

@@ -403,7 +403,8 @@ void Server::loop()
         for (auto &a : active_)
             if (a && !a->cancelled && pass_of(a->spec, a->L) >= 0) order.push_back(a.get());
         std::stable_sort(order.begin(), order.end(), [](Req *a, Req *b) { return a->spec.N > b->spec.N; });
-        int nslots = 0, group_slots[2] = {0, 0}, group_tiles[2] = {0, 0}, group_maxN[2] = {0, 0};
+        int nslots = 0, group_slots[2] = {0, 0}, group_tiles[2] = {0, 0}, group_maxN[2] = {0, 0},
+            group_maxP[2] = {0, 0};
         std::vector<Req *> finishing;
         for (int kind = 0; kind < 2; ++kind) {
             for (Req *r : order) {
@@ -421,6 +422,7 @@ void Server::loop()
                 group_tiles[kind] += sl.tiles;
                 group_slots[kind]++;
                 group_maxN[kind] = std::max(group_maxN[kind], r->spec.N);
+                group_maxP[kind] = std::max(group_maxP[kind], r->spec.P);
                 if (pass == kPassFinal) finishing.push_back(r);
             }
         }
@@ -459,10 +461,11 @@ void Server::loop()
             auto g = grid_for.find(key);
             if (g == grid_for.end())
                 g = grid_for.emplace(key, shape_max_grid(shape_, kind, group_maxN[kind], p_->sm_count)).first;
+            if (kind == kLaunchSubset && uses_masks(shape_))
+                chk(launch_tc_mask_scatter(holos, sd + first, group_slots[kind], group_maxP[kind], p_->sm_count,
+                                           stream_));
             if (launch_uses_tc(shape_, kind))
-                chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, true, stream_));
-            else if (kind == kLaunchSubset && uses_masks(shape_))
-                chk(launch_tc_mask_scatter(holos, sd + first, group_slots[kind], p_->sm_count, stream_));
+                chk(launch_tc_rw_tables(holos, sd + first, group_slots[kind], p_->sm_count, stream_));
             chk(shape_launch(shape_, kind, holos, sd + first, group_slots[kind], group_tiles[kind], group_maxN[kind],
                              queue, std::min(g->second, group_tiles[kind]), stream_));
         }

@@ -39,13 +39,13 @@ def oracle_states(oracle, pb, iterations, full_iterations=2):
 
 def write_pinned_tune_cache(path, threads, ppt, full, half=False, batch_pow2=range(0, 7), strip=None):
     """A tune cache that pins every key these tests can reach to one launch
-    shape: P rounded up to 128 (128 .. 1280), N and the batch size to powers of
+    shape: P rounded up to 128 (128 .. 2048), N and the batch size to powers of
     two, and the subset fraction to the nearest power of two (c = 1 .. 2^-16).
     strip: the tensor-core launches' tiles per work item (None: chosen per
     launch)."""
     import json
     shape = [threads, ppt, full] + ([] if strip is None else [strip])
     entries = {"P%d_N%d_B%d_c%d%s" % (128 * p, 2 ** n, 2 ** b, c, "_H" if half else ""): shape
-               for p in range(1, 11) for n in range(4, 11) for b in batch_pow2 for c in range(0, 17)}
+               for p in range(1, 17) for n in range(4, 11) for b in batch_pow2 for c in range(0, 17)}
     path.write_text(json.dumps({"format": "cswgs-tune-3", "entries": entries}))
     return str(path)

@@ -79,6 +79,21 @@ def test_free_running_against_oracle(plans, P, N, c, I):
     assert rms_wrapped(r["theta"], ref["theta"]) < TOL_PHASE_RMS
 
 
+@pytest.mark.parametrize("j", [1, 2])
+def test_teacher_forced_large_grid(plans, j):
+    # P = 1408: a subset mask (248 KB) larger than a block's shared memory is
+    # drawn with bit sets in global memory instead
+    tc, _ = plans
+    pb = workloads.problem(1408, 40, 10.0, 0.125, 4, seed=5)
+    st = oracle_states(oracle, pb, j, full_iterations=0)
+    w0, th0 = st[j - 1]
+    w1, th1 = st[j]
+    r = tc.solve(pb.xyz, pb.P, pb.c, 1, pb.seed, init_w=w0, init_theta=th0, first_iteration=j,
+                 full_iterations=0, final_pass=False, state=True)
+    assert rms_wrapped(r["theta"], th1) < TOL_PHASE_RMS
+    assert math.sqrt(np.mean((r["w"] / w1 - 1) ** 2)) < TOL_PHASE_RMS
+
+
 @pytest.mark.parametrize("j", [1, 2, 3])
 def test_teacher_forced_tiny_subset(plans, j):
     # c = 1/64 at P = 96: 144 subset pixels for 129 spots (two spot blocks),
