@@ -121,16 +121,22 @@ __device__ __forceinline__ void commit(uint32_t mbar)
                  : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false when it ran out.
+__device__ __forceinline__ bool try_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+    return ok != 0u;
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false when it ran out.  The
+// first poll does not wait for the poll limit's shared-memory load.
 __device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity)
 {
+    if (try_wait(mbar, parity)) return true;
     const uint32_t polls = s_wait_polls;
-    for (uint32_t it = 0; it < polls; ++it) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
-        if (ok) return true;
-    }
+    for (uint32_t it = 1; it < polls; ++it)
+        if (try_wait(mbar, parity)) return true;
     return false;
 }
 
