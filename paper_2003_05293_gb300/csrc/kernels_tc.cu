@@ -558,15 +558,11 @@ struct Info {
 
 
 // The epilogue warps: 4 u warps (epilogue 1, warps 0 .. 3) and 4 V warps
-// (epilogue 2, warps 4 .. 7), each group one warp per TMEM lane quadrant, each
-// with its own named barrier.
-// The epilogue warps: 4 u warps (epilogue 1, warps 0 .. 3) and 4 V warps
-// (epilogue 2, warps 4 .. 7), each group one warp per TMEM lane quadrant, each
-// with its own named barrier.  (Eight warps sharing both epilogues were
-// measured: 5 % slower, and 12 % at more than one GEMM 2 spot block, where
-// epilogue 2 of every tile no longer overlaps epilogue 1 of the next.)
+// (epilogue 2, warps 4 .. 7), each group one warp per TMEM lane quadrant.
+// (Eight warps sharing both epilogues were measured: 5 % slower, and 12 % at
+// more than one GEMM 2 spot block, where epilogue 2 of every tile no longer
+// overlaps epilogue 1 of the next.)
 constexpr int kUWarps = 4, kVWarps = 4;
-constexpr int kBarU = 1, kBarV = 2;
 
 template <int W>
 struct Cfg {
@@ -610,16 +606,11 @@ __device__ __forceinline__ void arrive(uint32_t mbar)
 
 __device__ __forceinline__ bool wait_newest(uint32_t mbar, uint32_t given) { return wait(mbar, (given - 1u) & 1u); }
 
-// A group's vote over named barrier Id (Threads threads): true when every
-// thread's p is.
-template <int Id, int Threads>
-__device__ __forceinline__ bool group_and(bool p)
-{
-    uint32_t r;
-    asm volatile("{\n .reg .pred pin, pout;\n setp.ne.u32 pin, %1, 0;\n bar.red.and.pred pout, %2, %3, pin;\n"
-                 " selp.u32 %0, 1, 0, pout;\n}\n" : "=r"(r) : "r"((uint32_t)p), "n"(Id), "n"(Threads) : "memory");
-    return r != 0;
-}
+// A warp's vote: true when every lane's p is.  The epilogue warps wait each
+// on its own; the hand-over barriers keep them within a tile of each other,
+// and a wait that runs out in one warp runs out in the others too, since the
+// pipeline behind it has stopped.
+__device__ __forceinline__ bool warp_and(bool p) { return __all_sync(0xffffffffu, p) != 0; }
 
 // Tile t of hologram H lies wholly outside the round pupil.
 __device__ __forceinline__ bool tile_outside(const HoloDev &H, int t)
@@ -1044,12 +1035,12 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
-        ok = group_and<kBarU, kT>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
+        ok = warp_and(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
         if (!ok) break;
         if (info[j].done) {
             // the GEMM 2 warp has read the last published operands once it has
             // issued that tile's first K-step
-            if (n_p > 0u) ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kUFree0), n_p));
+            if (n_p > 0u) ok = warp_and(wait_newest(mbar_at(mb, kUFree0), n_p));
             if (ok && tid == 0) {
                 g2->done = 1;
                 arrive(mbar_at(mb, kG2Info));
@@ -1104,7 +1095,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
         // the single GEMM 2 operand slot is free once GEMM 2 has issued the
         // previous tile's first K-step
         if (n_p > 0u) {
-            ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kUFree0), n_p));
+            ok = warp_and(wait_newest(mbar_at(mb, kUFree0), n_p));
             if (!ok) break;
         }
         if (tid == 0) {
@@ -1119,7 +1110,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
         }
         n_p++;
         n_s += 1u << (16 * j);
-        ok = group_and<kBarU, kT>(wait_newest(mbar_at(mb, kSFull0 + j), (n_s >> (16 * j)) & 0xFFFFu));
+        ok = warp_and(wait_newest(mbar_at(mb, kSFull0 + j), (n_s >> (16 * j)) & 0xFFFFu));
         if (!ok) break;
         fence_after();
         {
@@ -1208,12 +1199,12 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                     // u's slot of this K-step is free once GEMM 2 has read its last
                     // K-step (US earlier in GEMM 2's order: of this tile, or of the
                     // previous tile with products); K-step 0's was waited for above
-                    // (the condition is the same in every thread of the group, so
-                    // the named barrier of the vote stays matched)
+                    // (the condition is the same in every lane of the warp, so
+                    // the warp's vote stays matched)
                     const int pks = (ks + kKSteps - US) % kKSteps;
                     const uint32_t pcount = ks >= US ? n_p : n_p - 1u;
                     if (pcount > 0u && !(ks == 0 && US == kKSteps) &&
-                        !group_and<kBarU, kT>(wait_newest(mbar_at(mb, kUFree0 + pks), pcount)))
+                        !warp_and(wait_newest(mbar_at(mb, kUFree0 + pks), pcount)))
                         return false;
                     unsigned char *slot = m.u + (ks % US) * kUSlot;
                     store8<F16>(slot, kUc, core_off(row, 0, 16), pk[0]);
@@ -1232,7 +1223,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
         __syncwarp();
         if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
     }
-    if (!ok && tid == 0) atomicOr(status, 1u);
+    if (!ok && lane == 0) atomicOr(status, 1u);
 }
 
 // The V warps (epilogue 2): per strip (after the GEMM 2 of its last tile with
@@ -1248,7 +1239,7 @@ __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
-        ok = group_and<kBarV, kT>(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
+        ok = warp_and(wait(mbar_at(mb, kReady0 + j), (k >> 1) & 1u));
         if (!ok) break;
         if (info[j].done) break;
         const int item = info[j].item, empty = info[j].empty, t = info[j].tile, last = info[j].last;
@@ -1265,7 +1256,7 @@ __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32
         const int y0 = (t / ((P + kCols - 1) / kCols)) * kRows;
         for (int sb = 0; sb * kSpotBlock < N; ++sb) {
             n_z++;
-            ok = group_and<kBarV, kT>(wait_newest(mbar_at(mb, kZFull), n_z));
+            ok = warp_and(wait_newest(mbar_at(mb, kZFull), n_z));
             if (!ok) break;
             fence_after();
             const int n = sb * kSpotBlock + 32 * q + lane;
@@ -1281,7 +1272,7 @@ __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32
         }
         if (!ok) break;
     }
-    if (!ok && tid == 0) atomicOr(status, 1u);
+    if (!ok && lane == 0) atomicOr(status, 1u);
 }
 
 }  // namespace ws
