@@ -425,11 +425,29 @@ __global__ void __launch_bounds__(kLocalThreads) mask_local_kernel(const HoloDev
     const SubsetDraw d = subset_draw(H, sl.j);
     const UDiv dP = udiv_of((uint32_t)P);
     const uint32_t k0 = (uint32_t)((uint64_t)H.Mp * x / G), k1 = (uint32_t)((uint64_t)H.Mp * (x + 1) / G);
-    for (uint32_t k = k0 + tid; k < k1; k += kLocalThreads) {
-        const uint32_t m = subset_pixel(H, d, k);
-        uint32_t c;
-        const uint32_t r = udiv(m, dP, c);
-        atomicOr(s_words + r * (uint32_t)mw + (c >> 5), 1u << (c & 31));
+    if (H.aperture == 0 && H.fa == (uint32_t)P && H.fb == (uint32_t)P && H.D == P * P) {
+        // the square grid: the permutation's rectangle is the grid, so its
+        // final halves (L, R) are the pixel's row and column (subset_pixel
+        // without the cycle walk, the pupil map and the division by P)
+        const uint32_t D = (uint32_t)H.D;
+        for (uint32_t k = k0 + tid; k < k1; k += kLocalThreads) {
+            uint32_t kk = k + d.off;
+            kk = kk >= D ? kk - D : kk;
+            uint32_t R;
+            uint32_t L = udiv(kk, dP, R);
+            feistel_round(L, R, d.K.k0, (uint32_t)P);
+            feistel_round(L, R, d.K.k1, (uint32_t)P);
+            feistel_round(L, R, d.K.k2, (uint32_t)P);
+            feistel_round(L, R, d.K.k3, (uint32_t)P);
+            atomicOr(s_words + L * (uint32_t)mw + (R >> 5), 1u << (R & 31));
+        }
+    } else {
+        for (uint32_t k = k0 + tid; k < k1; k += kLocalThreads) {
+            const uint32_t m = subset_pixel(H, d, k);
+            uint32_t c;
+            const uint32_t r = udiv(m, dP, c);
+            atomicOr(s_words + r * (uint32_t)mw + (c >> 5), 1u << (c & 31));
+        }
     }
     __syncthreads();
     uint32_t *g = subset_mask(H, sl.j);
