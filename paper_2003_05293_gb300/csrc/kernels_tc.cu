@@ -1531,10 +1531,16 @@ cudaError_t launch_tc_rw_tables(const HoloDev *holos, const LaunchSlot *slots, i
 }
 
 // The shared-memory form of the mask draw for a launch whose holograms are
-// at most maxP pixels a side: the CTAs per slot (about one SM's worth of
-// slots per wave), or 0 when the mask does not fit a CTA's shared memory.
+// at most maxP pixels a side: the CTAs per slot (about one wave over the
+// SMs), or 0 when the mask does not fit a CTA's shared memory or the launch
+// has too few holograms for it: every CTA also clears and writes out a whole
+// mask, so past 8 CTAs per hologram the global bit sets of
+// mask_scatter_kernel (a few hundred thousand draws spread over every SM)
+// cost less.
 static int mask_local_shape(int maxP, int nslots, int sm_count, size_t *smem)
 {
+    const int G = std::max(1, sm_count / std::max(1, nslots));
+    if (G > 8) return 0;
     *smem = (size_t)maxP * (size_t)mask_words_of(maxP) * 4;
     if (*smem > 200 * 1024) return 0;
     if (cudaFuncSetAttribute(tc::mask_local_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) !=
@@ -1542,7 +1548,7 @@ static int mask_local_shape(int maxP, int nslots, int sm_count, size_t *smem)
         (void)cudaGetLastError();
         return 0;
     }
-    return std::max(1, std::min(8, sm_count / std::max(1, nslots)));
+    return G;
 }
 
 cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots, int nslots, int maxP, int sm_count,
@@ -1555,9 +1561,9 @@ cudaError_t launch_tc_mask_scatter(const HoloDev *holos, const LaunchSlot *slots
         tc::mask_local_kernel<<<dim3((unsigned)G, (unsigned)nslots), tc::kLocalThreads, smem, s>>>(holos, slots);
         return cudaGetLastError();
     }
-    // one block per SM beside the persistent kernel it overlaps (two slowed
-    // that kernel more, one per two SMs delayed the next launch)
-    dim3 grid((unsigned)std::max(1, sm_count / std::max(1, nslots)), (unsigned)nslots);
+    // a launch of few holograms (or holograms too large for the shared-memory
+    // form): four blocks per SM over the launch, the draws' latency spread wide
+    dim3 grid((unsigned)std::max(1, 4 * sm_count / std::max(1, nslots)), (unsigned)nslots);
     tc::mask_scatter_kernel<<<grid, 256, 0, s>>>(holos, slots);
     return cudaGetLastError();
 }
