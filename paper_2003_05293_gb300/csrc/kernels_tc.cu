@@ -1033,10 +1033,73 @@ __device__ __forceinline__ float2 strip_dot(uint32_t z_re, uint32_t z_im, const 
     return make_float2(vr0 + vr1, vi0 + vi1);
 }
 
-// The u warps (epilogue 1): per tile, u = A S / |S| (with Phi and the gray
-// level in the final pass) into GEMM 2's B operand, K-step by K-step: K-step
-// ks goes to u's slot ks % US once GEMM 2 has read that slot's last K-step
-// (computed first, stored after the wait).  A tile outside the pupil gets, in
+// The columns xl .. xr of grid row gy that lie in the pupil: the grid's, within
+// the round pupil (|x - half|^2 + (gy - half)^2 <= half^2) unless the aperture
+// is square; xr < xl for a row outside.
+__device__ __forceinline__ void row_span(int P, int aperture, int gy, int &xl, int &xr)
+{
+    const int half = P >> 1, yq = gy - half;
+    const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
+    xl = 0;
+    xr = gy < P ? P - 1 : -1;
+    if (aperture != 0) {
+        const int D = R2 - yq2;
+        int wr = -1;
+        if (D >= 0) {
+            wr = (int)sqrtf((float)D);   // within 1 of floor(sqrt(D))
+            if ((wr + 1) * (wr + 1) <= D) ++wr;
+            if (wr * wr > D) --wr;
+        }
+        xl = max(xl, half - wr);
+        xr = min(xr, half + wr);
+    }
+}
+
+// The final pass's phase map Phi = arg S (Eq. 1) and SLM gray levels of one
+// tile row (grid row gy, columns x0 .. x0 + 63), from S in tensor memory, K-step
+// by K-step: 0 outside the pupil.  Every lane of the warp runs the tensor-memory
+// loads (they are warp-collective); a row past the grid stores nothing.
+__device__ __forceinline__ void final_phases(const HoloDev &H, uint32_t s_re, uint32_t s_im, int gy, int x0)
+{
+    const int P = H.P;
+    int xl, xr;
+    row_span(P, H.aperture, gy, xl, xr);
+#pragma unroll 1
+    for (int ks = 0; ks < kKSteps; ++ks) {
+        const int gx0 = x0 + 16 * ks;
+        float sr[16], si[16], o[16];
+        __syncwarp();   // converged for the warp-collective loads
+        ld16(s_re + 16 * ks, sr);
+        ld16(s_im + 16 * ks, si);
+        ld_wait();
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int x = gx0 + jj;
+            float ph = atan2f(si[jj], sr[jj]);
+            ph = ph < 0.f ? ph + kTwoPiF : ph;
+            o[jj] = (ph >= kTwoPiF || x < xl || x > xr) ? 0.f : ph;
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int col = gx0 + 4 * g;
+            if (gy >= P || col >= P) break;
+            if (H.phase_out) {
+                float *dst = H.phase_out + (size_t)gy * P + col;
+                if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
+                } else {
+                    for (int e = 0; e < 4; ++e)
+                        if (col + e < P) dst[e] = o[4 * g + e];
+                }
+            }
+            if (H.slm) write_gray4(H, gy, col, o + 4 * g);
+        }
+    }
+}
+
+// The u warps (epilogue 1): per tile, u = A S / |S| into GEMM 2's B operand,
+// K-step by K-step: K-step ks goes to u's slot ks % US once GEMM 2 has read
+// that slot's last K-step (computed first, stored after the wait).  A tile outside the pupil gets, in
 // the final pass, phase 0 and gray lut[0] here, and a strip with no tile
 // inside the pupil its zero partials.
 template <bool F16, int US>
@@ -1133,22 +1196,9 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
         fence_after();
         {
             const uint32_t s_re = tmem + kS0 + 2 * kCols * j, s_im = s_re + kCols;
-            const int yq = gy - half;
-            const int R2 = half * half, yq2 = yq * yq;   // P <= 32768: squares stay below 2^30
-            // the row's pixels are columns xl..xr: the grid's, within the round
-            // pupil (|x - half|^2 + yq^2 <= half^2) unless the aperture is square
-            int xl = 0, xr = gy < P ? P - 1 : -1;
-            if (H.aperture != 0) {
-                const int D = R2 - yq2;
-                int wr = -1;
-                if (D >= 0) {
-                    wr = (int)sqrtf((float)D);   // within 1 of floor(sqrt(D))
-                    if ((wr + 1) * (wr + 1) <= D) ++wr;
-                    if (wr * wr > D) --wr;
-                }
-                xl = max(xl, half - wr);
-                xr = min(xr, half + wr);
-            }
+            const int yq = gy - half, yq2 = yq * yq;
+            int xl, xr;
+            row_span(P, H.aperture, gy, xl, xr);
             const float kA = H.kA;
             // the row's 16 columns of each K-step, with the Gaussian beam's
             // amplitude or the uniform one (a uniform branch outside the loop)
@@ -1163,7 +1213,7 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                     uint32_t bits = 0u;
                     if (lo <= hi) bits = (0xFFFFu >> (15 - hi + lo)) << lo;
                     bits &= (uint32_t)(mword >> xs);
-                    float sr[16], si[16], o[16];
+                    float sr[16], si[16];
                     ld16(s_re + lanes + xs, sr);
                     ld16(s_im + lanes + xs, si);
                     ld_wait();
@@ -1179,11 +1229,6 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                             const bool valid = ((bits >> jj) & 1u) != 0u;
                             const float a = sr[jj], b = si[jj];
                             const float n2 = a * a + b * b;
-                            if (pass == kPassFinal) {
-                                float ph = atan2f(b, a);
-                                ph = ph < 0.f ? ph + kTwoPiF : ph;
-                                o[jj] = (ph >= kTwoPiF || !valid) ? 0.f : ph;
-                            }
                             float amp = 1.f;   // Eq. 3's A
                             if constexpr (kGauss) {
                                 const int xq = gx0 + jj - half;
@@ -1195,24 +1240,6 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
                             u[e] = make_float2(valid ? ur : 0.f, valid ? ui : 0.f);
                         }
                         pk[g] = pack8<F16>(u);
-                    }
-                    if (pass == kPassFinal && gy < P) {
-#pragma unroll
-                        for (int g = 0; g < 4; ++g) {
-                            const int col = gx0 + 4 * g;
-                            if (col >= P) break;
-                            if (H.phase_out) {
-                                float *dst = H.phase_out + (size_t)gy * P + col;
-                                if (col + 3 < P && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-                                    *reinterpret_cast<float4 *>(dst) =
-                                        make_float4(o[4 * g], o[4 * g + 1], o[4 * g + 2], o[4 * g + 3]);
-                                } else {
-                                    for (int e = 0; e < 4; ++e)
-                                        if (col + e < P) dst[e] = o[4 * g + e];
-                                }
-                            }
-                            if (H.slm) write_gray4(H, gy, col, o + 4 * g);
-                        }
                     }
                     // u's slot of this K-step is free once GEMM 2 has read its last
                     // K-step (US earlier in GEMM 2's order: of this tile, or of the
@@ -1247,13 +1274,14 @@ __device__ __forceinline__ void epilogue_u(const SmemWs &m, const Info *info, G2
 // The V warps (epilogue 2): per strip (after the GEMM 2 of its last tile with
 // products) and spot block, the strip's partial V_n = sum_y conj(R_n(y))
 // Z(n, y), one spot per thread over all 128 rows, while the u warps go on with
-// the next tiles.
+// the next tiles.  In the final pass they also write each tile's phase map
+// (and gray levels) from S, beside the u warps' work on u.
 __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32_t tmem, unsigned *status)
 {
-    constexpr int kT = 32 * kVWarps;
     const int tid = threadIdx.x - 32 * kUWarps, lane = tid & 31, q = tid >> 5;   // TMEM lane quadrant q
     const uint32_t lanes = (uint32_t)(32 * q) << 16;
     uint32_t n_z = 0u;   // Z accumulations reduced
+    uint32_t n_s = 0u;   // tiles with products seen, per S buffer (low half: j = 0, high half: j = 1)
     bool ok = true;
     for (uint32_t k = 0;; ++k) {
         const int j = k & 1;
@@ -1266,12 +1294,24 @@ __device__ __forceinline__ void epilogue_v(const Info *info, uint32_t mb, uint32
         const int4 *coef = info[j].H.coef;
         float2 *part = info[j].H.part;
         double2 *part64 = info[j].H.part64;
-        // the info slot is read: it goes back with this group's arrival
+        const int y0 = (t / ((P + kCols - 1) / kCols)) * kRows;
+        if (!empty) n_s += 1u << (16 * j);
+        if (!empty && pass == kPassFinal) {
+            // the final pass's phase map, from S beside the u warps (S buffer j
+            // goes back once both groups have read it)
+            const HoloDev H = info[j].H;
+            ok = warp_and(wait_newest(mbar_at(mb, kSFull0 + j), (n_s >> (16 * j)) & 0xFFFFu));
+            if (!ok) break;
+            fence_after();
+            const uint32_t s_re = tmem + kS0 + 2 * kCols * j + lanes;
+            final_phases(H, s_re, s_re + kCols, y0 + 32 * q + lane, (t % ((P + kCols - 1) / kCols)) * kCols);
+            fence_before();
+        }
+        // the info slot (and S buffer) is read: it goes back with this group's arrival
         __syncwarp();
         if (lane == 0) arrive(mbar_at(mb, kSEmpty0 + j));
         if (empty || !last) continue;
         const int s_loc = item - tile_begin, half = P >> 1;
-        const int y0 = (t / ((P + kCols - 1) / kCols)) * kRows;
         for (int sb = 0; sb * kSpotBlock < N; ++sb) {
             n_z++;
             ok = warp_and(wait_newest(mbar_at(mb, kZFull), n_z));

@@ -290,7 +290,6 @@ static cswgs_status batch_build_shape(cswgs_plan_s *p, std::vector<HoloSpec> spe
     b->shape = shape;
     b->timing = timing;
     const int count = (int)b->specs.size();
-    const int tp = shape.threads * shape.ppt;
 
     // inputs block (mirrored in pinned staging)
     size_t in = 0;
