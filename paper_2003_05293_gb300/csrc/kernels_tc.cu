@@ -42,6 +42,8 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <functional>
+#include <vector>
 #include <type_traits>
 
 #include "tile.cuh"
@@ -1508,21 +1510,36 @@ int full_tc_assign_strips(LaunchSlot *slots, int nslots, const int *P, const int
     auto cols = [&](int i) { return (P[i] + kCols - 1) / kCols; };
     auto rows = [&](int i) { return (P[i] + kRows - 1) / kRows; };
     auto strip_of = [&](int i, int S) { return nspotblocks(N[i]) == 1 ? std::min(S, cols(i)) : 1; };
-    double tiles = 0.0;
     int smax = 1;
-    for (int i = 0; i < nslots; ++i) {
-        tiles += (double)rows(i) * cols(i);
+    for (int i = 0; i < nslots; ++i)
         if (nspotblocks(N[i]) == 1) smax = std::max(smax, cols(i));
-    }
+    // The launch's finish time for strip length S, in tiles: the persistent
+    // blocks take the work items in queue order, each the next free block
+    // (simulated with a heap of the blocks' finish times); an item costs its
+    // tiles plus a hand-over of ~0.15 tile, and 0.1 tile per unit of S stands
+    // for the wider spread of holograms (and of their tables in L2) that long
+    // strips keep in flight (fitted to strips of 1, 2, 3, 4, 6, 9, 12 and 18 at
+    // 64 holograms of P = 1152, where 3 is fastest).
+    constexpr double kItemCost = 0.15, kStripCost = 0.1;
+    std::vector<double> heap;
+    auto finish = [&](int S) {
+        heap.assign((size_t)grid, 0.0);   // all zero: a valid min-heap
+        auto take = [&](double w) {
+            std::pop_heap(heap.begin(), heap.end(), std::greater<double>());
+            heap.back() += w + kItemCost;
+            std::push_heap(heap.begin(), heap.end(), std::greater<double>());
+        };
+        for (int i = 0; i < nslots; ++i) {
+            const int st = strip_of(i, S), c = cols(i);
+            for (int r = 0; r < rows(i); ++r)
+                for (int c0 = 0; c0 < c; c0 += st) take((double)std::min(st, c - c0));
+        }
+        return *std::max_element(heap.begin(), heap.end());
+    };
     int best = forced > 0 ? forced : 1;
     double best_cost = 1e300;
     for (int S = 1; S <= smax && forced <= 0; ++S) {
-        double items = 0.0;
-        for (int i = 0; i < nslots; ++i) {
-            const int st = strip_of(i, S);
-            items += (double)rows(i) * ((cols(i) + st - 1) / st);
-        }
-        const double cost = (tiles + 0.5 * items) / grid + 0.5 * S;
+        const double cost = finish(S) + kStripCost * S;
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
             best = S;
