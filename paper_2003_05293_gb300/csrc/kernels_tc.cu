@@ -466,27 +466,40 @@ __global__ void __launch_bounds__(kLocalThreads) mask_local_kernel(const HoloDev
 __global__ void __launch_bounds__(256) rw_tables_kernel(const HoloDev *__restrict__ holos,
                                                         const LaunchSlot *__restrict__ slots)
 {
+    // one block (128 rows x 16 spots) per pass of the loop: its 16 spots' row
+    // coefficients and state are read once into shared memory
+    __shared__ int4 s_cf[kChunk];      // {B, Gh, gl, theta + rounding}
+    __shared__ float s_wa[kChunk];     // w a
     const LaunchSlot sl = slots[blockIdx.y];
     const HoloDev H = holos[sl.holo];
     if (!H.rwtab) return;
     const int P = H.P, N = H.N, half = P >> 1, nc = nchunks(N);
-    const int items = ((P + kRows - 1) / kRows) * nc * 256;      // (block, 128 rows x 2 groups)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < items; i += gridDim.x * blockDim.x) {
-        const int blk = i >> 8, j = i & 255;
+    const int blocks = ((P + kRows - 1) / kRows) * nc;   // (128 rows, 16 spots) blocks, 256 threads each
+    const int j = threadIdx.x;
+    const int row = (j & 7) + 8 * (j >> 4), g = (j >> 3) & 1;
+    for (int blk = blockIdx.x; blk < blocks; blk += gridDim.x) {
         const int rb = blk / nc, c = blk % nc;
-        const int row = (j & 7) + 8 * (j >> 4), g = (j >> 3) & 1;
+        __syncthreads();   // the previous block's spots are read
+        if (j < kChunk) {
+            const int n = c * kChunk + j;
+            int4 v = make_int4(0, 0, 0, 0);
+            float wa = 0.f;
+            if (n < N) {
+                const int4 cf = H.coef[n];
+                const SpotState st = H.state[n];
+                v = make_int4(cf.y, cf.z, cf.w, (int)(st.theta + kFixRound));
+                wa = st.w * st.a0;
+            }
+            s_cf[j] = v;
+            s_wa[j] = wa;
+        }
+        __syncthreads();
         float2 v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int n = c * kChunk + 8 * g + e;
-            if (n < N) {
-                const int4 cf = H.coef[n];
-                const SpotState s = H.state[n];
-                v[e] = spot_factor(cf.y, cf.z, __int_as_float(cf.w), rb * kRows + row - half, s.theta + kFixRound,
-                                   s.w * s.a0);
-            } else {
-                v[e] = make_float2(0.f, 0.f);
-            }
+            const int4 cf = s_cf[8 * g + e];
+            v[e] = spot_factor(cf.x, cf.y, __int_as_float(cf.z), rb * kRows + row - half, (uint32_t)cf.w,
+                               s_wa[8 * g + e]);
         }
         put8(H.rwtab + (size_t)blk * (4 * kA1), kA1, core_off(row, 8 * g, kChunk), v);
     }
