@@ -596,10 +596,12 @@ cswgs_status batch_enqueue_direct(Fp32Batch *b, cudaStream_t s, bool capturing)
     if (uses_tc(b->shape)) CSWGS_CUDA_TRY(launch_tc_const_tables(holos, count, b->plan->sm_count, s));
     const size_t steps = b->l_tiles.size() / 2;
     // Compressed launches on the tensor cores draw their subset masks on the
-    // side stream, one step ahead: the draw of step L + 1 runs beside the launch
-    // of step L, after the tails of step L - 1 have cleared that mask (each
-    // hologram advances one iteration per step, so it alternates its two masks).
-    const bool side_masks = false && b->side && uses_masks(b->shape);
+    // side stream, one step ahead: the draw of step L + 1 is queued beside the
+    // launch of step L, after the tails of step L - 1 have cleared that mask
+    // (each hologram advances one iteration per step, so it alternates its two
+    // masks); it runs as the launch's blocks leave, beside its tails and the
+    // next R' tables.
+    const bool side_masks = b->side && uses_masks(b->shape);
     auto masked = [&](size_t L) { return L < steps && b->l_tiles[2 * L + kLaunchSubset] > 0; };
     bool tail_rec[2] = {false, false};
     auto draw = [&](size_t L) -> cswgs_status {
