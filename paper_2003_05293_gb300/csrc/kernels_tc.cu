@@ -36,8 +36,9 @@
 // a ring; a producer warp issues GEMM 1's copies, two issuing warps (GEMM 1,
 // GEMM 2) issue the MMAs and commit them to mbarriers, and eight epilogue
 // warps run the CUDA-core stages: four turn S into u (epilogue 1), four reduce
-// Z to the spot fields (epilogue 2) once per strip of tiles along a row block.  Every wait is bounded and a timeout is recorded in the launch's status
-// word instead of hanging.
+// Z to the spot fields (epilogue 2) once per strip of tiles along a row block
+// and, in the final pass, write the phase map from S.  Every wait is bounded
+// and a timeout is recorded in the launch's status word instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
